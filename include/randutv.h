@@ -1,0 +1,173 @@
+/*
+ * randutv.h -- C ABI of the GB300 (sm_103a) randUTV engine.
+ *
+ * randUTV (Martinsson, Quintana-Orti, Heavner, arXiv 1703.00998) factors an
+ * m x n matrix A = U T V^T with U (m x m) and V (n x n) orthogonal and T
+ * upper triangular (Section 1, eq. defUTVpre), working on b columns per step
+ * (Fig. 4, Section 5.2).  Each step draws a Gaussian G, forms the sample
+ * Y = (X^T X)^q X^T G of the active block X (Section 4.3), applies the
+ * Householder reflector product of QR(Y) from the right, the one of the new
+ * b-column panel from the left (Remark 1), and diagonalizes the b x b block
+ * with a small SVD rotated into U, T and V (Fig. 4).
+ *
+ * Conventions for every entry point below:
+ *   - matrices are column-major: element (i, j) of X is X[i + j * ldx];
+ *   - pointers are DEVICE pointers unless a comment says otherwise, and
+ *     the caller keeps ownership of every buffer it passes in;
+ *   - work is queued on the stream set by randutv_set_stream (default: the
+ *     legacy default stream) and calls return after the result is complete
+ *     (they synchronize that stream before returning);
+ *   - the return value is a status: 0 success, -i when argument i (1-based)
+ *     is invalid (LAPACK info convention, nothing is computed), or one of
+ *     the positive RANDUTV_E* codes.  No call aborts the process and no
+ *     kernel traps; device-side failures (a bounded wait that ran out, a
+ *     non-finite value) are reported through the status.
+ */
+#ifndef RANDUTV_H
+#define RANDUTV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RANDUTV_OK            0
+#define RANDUTV_ENOMEM        1  /* device allocation failed                    */
+#define RANDUTV_ENOCONV       2  /* small SVD hit max_sweeps (outputs written)  */
+#define RANDUTV_ENAN          3  /* non-finite input or trailing norm           */
+#define RANDUTV_EUNSUPPORTED  4  /* valid but not supported by this build       */
+#define RANDUTV_ECUDA         5  /* a CUDA runtime call failed                  */
+#define RANDUTV_ETIMEOUT      6  /* a device grid barrier gave up waiting       */
+
+#define RANDUTV_FP64   0  /* every step in FP64                                */
+
+/* Options of randutv_factor_ex.  Fill with randutv_opts_default first. */
+typedef struct randutv_opts {
+  int precision;        /* RANDUTV_FP64                                        */
+  int form_uv;          /* 1: form U and V (Table 1); 0: T only (Table 4),
+                           U and V may then be NULL                            */
+  int max_sweeps;       /* cap on cyclic Jacobi sweeps of each small SVD (30)  */
+  int p;                /* over-sampling (Remark "Oversampling"); must be 0    */
+  uint64_t seed;        /* Philox4x32-10 key of the Gaussian matrices G        */
+  const double* g_inject; /* NULL, or a device buffer holding every randomized
+                           step's G, concatenated: step i (1-based, b*i <
+                           min(m,n)) stores its (m - b(i-1)) x b matrix
+                           column-major (ld = m - b(i-1)) right after step
+                           i-1's.  Used instead of the Philox stream.          */
+} randutv_opts;
+
+/* Defaults: FP64, form_uv = 1, max_sweeps = 30, p = 0, seed = 998, no g_inject. */
+void randutv_opts_default(randutv_opts* opts);
+
+/* Stream used by all later calls in this process (a cudaStream_t; NULL =
+   legacy default stream).  Always returns RANDUTV_OK. */
+int randutv_set_stream(void* cuda_stream);
+
+/* Factor A (m x n, lda >= m, FP64) as A = U T V^T (Fig. 4).  The library
+ * allocates T (m x n, ld m), U (m x m, ld m) and V (n x n, ld n) and returns
+ * them through *T, *U, *V; release each with randutv_free.  A is not
+ * modified.  b >= 1 is the block size (values above min(m,n) give one full
+ * SVD), q >= 0 the number of power steps, tol >= 0 the early-stop tolerance:
+ * before step i the factorization stops when ||T(I2 u I3, J2 u J3)||_F <=
+ * tol * ||A||_F, and *k_reached receives b(i-1) (min(m,n) when it runs to the
+ * end; tol = 0 never stops early).  Gaussians from the Philox stream with seed
+ * 998.  Argument order for the -i codes: m=1 n=2 A=3 lda=4 b=5 q=6 tol=7 U=8
+ * T=9 V=10 k_reached=11. */
+int randutv_factor(int64_t m, int64_t n, const double* A, int64_t lda, int b, int q,
+                   double tol, double** U, double** T, double** V, int64_t* k_reached);
+
+/* Same with caller-owned outputs: T (ldt >= m), U (ldu >= m), V (ldv >= n).
+ * T may equal A (in place, Section 5.2: T overwrites A) when ldt == lda.
+ * opts may be NULL (defaults).  Argument order: m=1 n=2 A=3 lda=4 b=5 q=6
+ * tol=7 U=8 ldu=9 T=10 ldt=11 V=12 ldv=13 k_reached=14 opts=15. */
+int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b, int q,
+                      double tol, double* U, int64_t ldu, double* T, int64_t ldt,
+                      double* V, int64_t ldv, int64_t* k_reached, const randutv_opts* opts);
+
+/* randutv_factor_ex on HOST buffers: A (lda >= m), U (ldu >= m), T (ldt >= m)
+ * and V (ldv >= n) are host pointers (page-locked memory gives the fastest
+ * copies; A and T must not overlap).  The library allocates device memory,
+ * copies A in, factors in place on the device, copies T (and U, V when
+ * form_uv) back, and frees the device memory before returning.  Same
+ * argument numbering and status codes as randutv_factor_ex. */
+int randutv_factor_host(int64_t m, int64_t n, const double* A, int64_t lda, int b, int q,
+                        double tol, double* U, int64_t ldu, double* T, int64_t ldt,
+                        double* V, int64_t ldv, int64_t* k_reached, const randutv_opts* opts);
+
+/* Release a buffer returned by randutv_factor (NULL is ignored). */
+void randutv_free(void* p);
+
+/* Static description of a status code. */
+const char* randutv_strerror(int status);
+
+/* Detail of the last RANDUTV_ECUDA / RANDUTV_ETIMEOUT / RANDUTV_EUNSUPPORTED
+ * status raised in the calling thread (empty string if none). */
+const char* randutv_last_error(void);
+
+/* ---- Diagnostics ---- */
+
+/* Kernel classes of randutv_profile_read. */
+#define RANDUTV_PROF_GEMM     0  /* FP64 GEMM (sketch, block-reflector applications, rotations) */
+#define RANDUTV_PROF_PANEL    1  /* Householder panel QR                              */
+#define RANDUTV_PROF_TFACTOR  2  /* compact-WY factor S                               */
+#define RANDUTV_PROF_JACOBI   3  /* small SVD (sweeps + ordering)                     */
+#define RANDUTV_PROF_GAUSS    4  /* Philox Gaussian                                   */
+#define RANDUTV_PROF_OTHER    5  /* copies, fills, norms                              */
+
+/* Turn per-kernel-class timing on (1) or off (0).  While on, each launch of a
+ * class is bracketed by CUDA events on its stream and its algorithmic flops
+ * and bytes are recorded; nothing synchronises the host until a read. */
+int randutv_profile_enable(int on);
+/* Zero the accumulated totals. */
+int randutv_profile_reset(void);
+/* Totals of class cls since the last reset: summed event time (ms), number
+ * of timed launches, algorithmic flops and bytes.  Synchronises pending
+ * events.  Any output pointer may be NULL.  Returns -1 for an unknown cls. */
+int randutv_profile_read(int cls, double* ms, int64_t* launches, double* flops, double* bytes);
+/* Number of kernels this library has launched since it was loaded. */
+uint64_t randutv_launch_count(void);
+
+/* ---- Building blocks of one step, exposed so each kernel can be tested on
+ * its own against the CPU oracle.  Same conventions as above. ---- */
+
+/* G (k x b, ld ldg >= k): the Gaussian matrix of global step `step` (1-based)
+ * from Philox4x32-10 with key (seed mod 2^32, seed div 2^32) and counter
+ * (r div 2, c, step, 0) for row r, column c; Box-Muller of two open-interval
+ * uniforms u = (floor(w / 2^12) + 1/2) 2^-52 from words (x0, x1) and (x2, x3):
+ * row 2p gets sqrt(-2 ln u1) cos(2 pi u2), row 2p+1 the sine (randn of Fig. 4). */
+int randutv_gaussian(uint64_t seed, int64_t step, int64_t k, int64_t b, double* G, int64_t ldg);
+
+/* Raw Philox4x32-10 words of the same counters: W holds ceil(k/2) x b x 4
+ * uint32 values, word t of counter (p, c) at W[4 * (p + c * ceil(k/2)) + t]. */
+int randutv_philox_words(uint64_t seed, int64_t step, int64_t k, int64_t b, uint32_t* W);
+
+/* C = alpha op(A) op(B) + beta C with op(X) = X ('N') or X^T ('T'); op(A) is
+ * m x k, op(B) k x n, C m x n.  beta = 0 never reads C.  The FP64 GEMM every
+ * block-reflector application and sketch product of the step runs on. */
+int randutv_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+                  const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                  double* C, int64_t ldc);
+
+/* Unpivoted Householder QR of the k x w panel P (k >= w >= 1, ldp >= k), in
+ * place (eq. unpivQR; LAPACK dlarfg convention: beta = -sign(alpha)||x||,
+ * tau = 0 when the part below the diagonal is zero).  On return P holds R on
+ * and above the diagonal and the Householder vectors below it; tau (w) the
+ * scalars; Vexp (k x w, ld k) the explicit unit-lower vectors (column j zero
+ * when tau_j = 0); S (w x w, ld w) the upper triangular factor with
+ * H_1 ... H_w = I - Vexp S Vexp^T (eq. WYrepresentation with W = -Vexp S). */
+int randutv_panel_qr(int64_t k, int64_t w, double* P, int64_t ldp, double* tau,
+                     double* Vexp, double* S);
+
+/* SVD of a p x p block M (ldm >= p): M = Us diag(d) Vs^T by one-sided cyclic
+ * Jacobi in FP64; d descending and >= 0, the largest-|.| entry of each Vs
+ * column positive (lowest index on ties).  Us, Vs are p x p with ld p.
+ * Returns RANDUTV_ENOCONV (outputs still written) after max_sweeps sweeps. */
+int randutv_small_svd(int64_t p, const double* M, int64_t ldm, double* Us, double* d,
+                      double* Vs, int max_sweeps);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RANDUTV_H */

@@ -1,0 +1,620 @@
+// The randUTV step loop (Fig. 4, Section 5.2) and the C ABI of include/randutv.h.
+//
+// The host walks the steps and queues kernels on one stream; T, U, V and
+// every intermediate stay in device memory for the whole factorization, and
+// each transform is applied as soon as it is formed (Section 5.2, first
+// modification).  There is no host synchronisation inside the loop unless a
+// tolerance asks for the trailing norm.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include "common.cuh"
+#include "internal.h"
+
+namespace rutv {
+
+static cudaStream_t g_stream = nullptr;
+cudaStream_t current_stream() { return g_stream; }
+
+static thread_local char g_detail[256] = "";
+
+static int cuda_status(cudaError_t e, const char* where) {
+  snprintf(g_detail, sizeof(g_detail), "%s: %s", where, cudaGetErrorString(e));
+  return RANDUTV_ECUDA;
+}
+
+#define RUTV_CK(call)                                            \
+  do {                                                           \
+    cudaError_t e_ = (call);                                     \
+    if (e_ != cudaSuccess) { st = cuda_status(e_, #call); goto done; } \
+  } while (0)
+
+// ---------------------------------------------------------------- utilities
+__global__ void set_identity_kernel(int64_t n, double* X, int64_t ldx) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= n * n) return;
+  const int64_t i = t % n, j = t / n;
+  X[i + j * ldx] = (i == j) ? 1.0 : 0.0;
+}
+
+cudaError_t set_identity(cudaStream_t s, int64_t n, double* X, int64_t ldx) {
+  if (n <= 0) return cudaSuccess;
+  set_identity_kernel<<<static_cast<unsigned>((n * n + 255) / 256), 256, 0, s>>>(n, X, ldx);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t copy_matrix(cudaStream_t s, int64_t m, int64_t n, const double* A, int64_t lda, double* B,
+                        int64_t ldb) {
+  if (m <= 0 || n <= 0 || A == B) return cudaSuccess;
+  return cudaMemcpy2DAsync(B, ldb * sizeof(double), A, lda * sizeof(double), m * sizeof(double), n,
+                           cudaMemcpyDeviceToDevice, s);
+}
+
+__global__ void fill_kernel(int64_t m, int64_t n, double* X, int64_t ldx, double v) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= m * n) return;
+  X[t % m + (t / m) * ldx] = v;
+}
+
+static cudaError_t fill(cudaStream_t s, int64_t m, int64_t n, double* X, int64_t ldx, double v) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  fill_kernel<<<static_cast<unsigned>((m * n + 255) / 256), 256, 0, s>>>(m, n, X, ldx, v);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void set_diag_kernel(int64_t p, const double* d, double* X, int64_t ldx) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t < p) X[t + t * ldx] = d[t];
+}
+
+__global__ void transpose_kernel(int64_t m, int64_t n, const double* A, int64_t lda, double* B, int64_t ldb) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= m * n) return;
+  const int64_t i = t % m, j = t / m;
+  B[j + i * ldb] = A[i + j * lda];
+}
+
+static cudaError_t transpose(cudaStream_t s, int64_t m, int64_t n, const double* A, int64_t lda, double* B,
+                             int64_t ldb) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  transpose_kernel<<<static_cast<unsigned>((m * n + 255) / 256), 256, 0, s>>>(m, n, A, lda, B, ldb);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// Sum of squares of an m x n strided matrix: block partials, then one block.
+__global__ void sumsq_partial_kernel(int64_t m, int64_t n, const double* X, int64_t ldx, double* part) {
+  __shared__ double red[8];
+  double s = 0.0;
+  const int64_t tot = m * n;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < tot;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double v = X[t % m + (t / m) * ldx];
+    s = fma(v, v, s);
+  }
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int w = 0; w < static_cast<int>(blockDim.x) / 32; ++w) a += red[w];
+    part[blockIdx.x] = a;
+  }
+}
+
+__global__ void sumsq_final_kernel(int nparts, const double* part, double* out) {
+  __shared__ double red[8];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int w = 0; w < static_cast<int>(blockDim.x) / 32; ++w) a += red[w];
+    *out = a;
+  }
+}
+
+constexpr int kSumsqBlocks = 2 * kNumSMs;
+
+static cudaError_t sumsq(cudaStream_t s, int64_t m, int64_t n, const double* X, int64_t ldx, double* part,
+                         double* out) {
+  sumsq_partial_kernel<<<kSumsqBlocks, 256, 0, s>>>(m, n, X, ldx, part);
+  note_launch();
+  sumsq_final_kernel<<<1, 256, 0, s>>>(kSumsqBlocks, part, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------- block reflectors
+// C (rows x cols) <- C (I - Vx S Vx^T), Vx cols x w.
+static cudaError_t wy_right(cudaStream_t s, int64_t rows, int64_t cols, double* C, int64_t ldc,
+                            const double* Vx, const double* S, int w, double* W1, double* W2,
+                            double* gws, int64_t gws_elems) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  cudaError_t e;
+  if ((e = gemm_f64(s, false, false, rows, w, cols, 1.0, C, ldc, Vx, cols, 0.0, W1, rows, gws, gws_elems))) return e;
+  if ((e = gemm_f64(s, false, false, rows, w, w, 1.0, W1, rows, S, w, 0.0, W2, rows, gws, gws_elems))) return e;
+  return gemm_f64(s, false, true, rows, cols, w, -1.0, W2, rows, Vx, cols, 1.0, C, ldc, gws, gws_elems);
+}
+
+// C (rows x cols) <- (I - Vx S Vx^T)^T C, Vx rows x w.
+static cudaError_t wy_left_t(cudaStream_t s, int64_t rows, int64_t cols, double* C, int64_t ldc,
+                             const double* Vx, const double* S, int w, double* W1, double* W2,
+                             double* gws, int64_t gws_elems) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  cudaError_t e;
+  if ((e = gemm_f64(s, true, false, w, cols, rows, 1.0, Vx, rows, C, ldc, 0.0, W1, w, gws, gws_elems))) return e;
+  if ((e = gemm_f64(s, true, false, w, cols, w, 1.0, S, w, W1, w, 0.0, W2, w, gws, gws_elems))) return e;
+  return gemm_f64(s, false, false, rows, cols, w, -1.0, Vx, rows, W2, w, 1.0, C, ldc, gws, gws_elems);
+}
+
+// X (rows x w) <- X Q with Q w x w (through tmp).
+static cudaError_t rot_right(cudaStream_t s, int64_t rows, int w, double* X, int64_t ldx, const double* Q,
+                             double* tmp, double* gws, int64_t gws_elems) {
+  if (rows <= 0 || w <= 0) return cudaSuccess;
+  cudaError_t e;
+  if ((e = gemm_f64(s, false, false, rows, w, w, 1.0, X, ldx, Q, w, 0.0, tmp, rows, gws, gws_elems))) return e;
+  return copy_matrix(s, rows, w, tmp, rows, X, ldx);
+}
+
+// X (w x cols) <- Q^T X with Q w x w (through tmp).
+static cudaError_t rot_left_t(cudaStream_t s, int w, int64_t cols, double* X, int64_t ldx, const double* Q,
+                              double* tmp, double* gws, int64_t gws_elems) {
+  if (cols <= 0 || w <= 0) return cudaSuccess;
+  cudaError_t e;
+  if ((e = gemm_f64(s, true, false, w, cols, w, 1.0, Q, w, X, ldx, 0.0, tmp, w, gws, gws_elems))) return e;
+  return copy_matrix(s, w, cols, tmp, w, X, ldx);
+}
+
+// ------------------------------------------------------------- workspace
+struct Work {
+  double *G, *Y, *Z, *Vv, *Vu, *tau, *R, *Rt, *gram, *S, *W1, *W2, *Us, *Vs, *d, *tmp;
+  double *gws, *part, *jws, *red, *scal;
+  int64_t gws_elems;
+  unsigned* flags;
+  void* base;
+  size_t bytes;
+};
+
+static size_t align_up(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+static int64_t gemm_budget(int64_t mx, int b) {
+  return std::max<int64_t>(24 * mx * b, 64ll * b * b);
+}
+
+static cudaError_t work_alloc(cudaStream_t s, int64_t m, int64_t n, int b, Work* w) {
+  const int64_t mx = std::max(m, n);
+  const int64_t bb = static_cast<int64_t>(b) * b;
+  struct Item { double** p; int64_t n; };
+  w->gws_elems = gemm_budget(mx, b);
+  Item items[] = {
+      {&w->G, m * b}, {&w->Y, n * b}, {&w->Z, m * b}, {&w->Vv, mx * b}, {&w->Vu, mx * b},
+      {&w->tau, b}, {&w->R, bb}, {&w->Rt, bb}, {&w->gram, bb}, {&w->S, bb}, {&w->W1, mx * b},
+      {&w->W2, mx * b}, {&w->Us, bb}, {&w->Vs, bb}, {&w->d, b}, {&w->tmp, mx * b},
+      {&w->gws, w->gws_elems}, {&w->part, panel_qr_part_elems(mx, b)}, {&w->jws, jacobi_work_elems(b)},
+      {&w->red, kSumsqBlocks}, {&w->scal, 8},
+  };
+  size_t total = 0;
+  for (auto& it : items) total += align_up(static_cast<size_t>(it.n) * sizeof(double));
+  total += align_up(4 * kFlagSlots * sizeof(unsigned));
+  cudaError_t e = cudaMallocAsync(&w->base, total, s);
+  if (e != cudaSuccess) return e;
+  w->bytes = total;
+  char* p = static_cast<char*>(w->base);
+  for (auto& it : items) {
+    *it.p = reinterpret_cast<double*>(p);
+    p += align_up(static_cast<size_t>(it.n) * sizeof(double));
+  }
+  w->flags = reinterpret_cast<unsigned*>(p);
+  return cudaMemsetAsync(w->flags, 0, 4 * kFlagSlots * sizeof(unsigned), s);
+}
+
+static unsigned* slot(Work& w, int i) { return w.flags + 4 * i; }
+
+// Read the error words of every barrier slot (after a stream sync).
+static int device_status(Work& w) {
+  unsigned h[4 * kFlagSlots];
+  if (cudaMemcpy(h, w.flags, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return RANDUTV_ECUDA;
+  unsigned err = 0;
+  for (int i = 0; i < kFlagSlots; ++i) err |= h[4 * i + 2];
+  if (err & kDevErrTimeout) { snprintf(g_detail, sizeof(g_detail), "device grid barrier timed out"); return RANDUTV_ETIMEOUT; }
+  if (err & kDevErrNaN) return RANDUTV_ENAN;
+  if (err & kDevErrNoConv) return RANDUTV_ENOCONV;
+  return RANDUTV_OK;
+}
+
+}  // namespace rutv
+
+using namespace rutv;
+
+// ================================================================== C ABI
+extern "C" {
+
+void randutv_opts_default(randutv_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = RANDUTV_FP64;
+  o->form_uv = 1;
+  o->max_sweeps = 30;
+  o->p = 0;
+  o->seed = 998;
+  o->g_inject = nullptr;
+}
+
+int randutv_set_stream(void* s) {
+  g_stream = static_cast<cudaStream_t>(s);
+  return RANDUTV_OK;
+}
+
+const char* randutv_strerror(int st) {
+  if (st < 0) return "invalid argument (the code is minus its 1-based position)";
+  switch (st) {
+    case RANDUTV_OK: return "success";
+    case RANDUTV_ENOMEM: return "device allocation failed";
+    case RANDUTV_ENOCONV: return "small SVD did not converge within max_sweeps";
+    case RANDUTV_ENAN: return "non-finite value in the input or the trailing block";
+    case RANDUTV_EUNSUPPORTED: return "valid arguments outside what this build supports";
+    case RANDUTV_ECUDA: return "a CUDA runtime call failed";
+    case RANDUTV_ETIMEOUT: return "a device-side grid barrier gave up waiting";
+    default: return "unknown status";
+  }
+}
+
+const char* randutv_last_error(void) { return g_detail; }
+
+void randutv_free(void* p) {
+  if (p) cudaFree(p);
+}
+
+int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b, int q, double tol,
+                      double* U, int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv,
+                      int64_t* k_reached, const randutv_opts* opts_in) {
+  randutv_opts opts;
+  if (opts_in) opts = *opts_in; else randutv_opts_default(&opts);
+  if (m < 1) return -1;
+  if (n < 1) return -2;
+  if (!A) return -3;
+  if (lda < m) return -4;
+  if (b < 1) return -5;
+  if (q < 0) return -6;
+  if (!(tol >= 0.0) || std::isinf(tol)) return -7;
+  if (opts.form_uv && !U) return -8;
+  if (opts.form_uv && ldu < m) return -9;
+  if (!T) return -10;
+  if (ldt < m || (T == A && ldt != lda)) return -11;
+  if (opts.form_uv && !V) return -12;
+  if (opts.form_uv && ldv < n) return -13;
+  if (!k_reached) return -14;
+  if (opts.precision != RANDUTV_FP64 || opts.p != 0 || opts.max_sweeps < 1) return -15;
+
+  const int64_t mn = std::min(m, n);
+  if (b > mn) b = static_cast<int>(mn);
+  if (b > 256) { snprintf(g_detail, sizeof(g_detail), "block size above 256"); return RANDUTV_EUNSUPPORTED; }
+  const bool uv = opts.form_uv != 0;
+  cudaStream_t s = g_stream;
+  Work w{};
+  int st = RANDUTV_OK;
+  double h_norm2 = 0.0, normA = 0.0;
+  int64_t g_off = 0;
+  *k_reached = mn;
+  const int64_t nsteps = std::min((m + b - 1) / b, (n + b - 1) / b);
+
+  {
+    cudaError_t e = work_alloc(s, m, n, b, &w);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      snprintf(g_detail, sizeof(g_detail), "workspace: %s", cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? RANDUTV_ENOMEM : RANDUTV_ECUDA;
+    }
+  }
+  RUTV_CK(copy_matrix(s, m, n, A, lda, T, ldt));
+  if (uv) {
+    RUTV_CK(set_identity(s, m, U, ldu));
+    RUTV_CK(set_identity(s, n, V, ldv));
+  }
+  RUTV_CK(sumsq(s, m, n, T, ldt, w.red, w.scal));
+  RUTV_CK(cudaMemcpyAsync(&h_norm2, w.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  RUTV_CK(cudaStreamSynchronize(s));
+  if (!std::isfinite(h_norm2)) { st = RANDUTV_ENAN; goto done; }
+  normA = std::sqrt(h_norm2);
+
+  for (int64_t i = 1; i <= nsteps; ++i) {
+    const int64_t r0 = b * (i - 1);
+    const int64_t r1 = std::min<int64_t>(r0 + b, m), c1 = std::min<int64_t>(r0 + b, n);
+    const int64_t kr = m - r0, kc = n - r0;
+    double* X = T + r0 + r0 * ldt;
+    if (tol > 0.0) {
+      double t2 = 0.0;
+      RUTV_CK(sumsq(s, kr, kc, X, ldt, w.red, w.scal));
+      RUTV_CK(cudaMemcpyAsync(&t2, w.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+      RUTV_CK(cudaStreamSynchronize(s));
+      if (!std::isfinite(t2)) { st = RANDUTV_ENAN; goto done; }
+      if (std::sqrt(t2) <= tol * normA) { *k_reached = r0; break; }
+    }
+    if (r1 < m && c1 < n) {
+      // ---- randomized step: sketch, QR(Y) -> VV, QR(panel) -> UU, small SVD
+      const double* G = w.G;
+      if (opts.g_inject) {
+        G = opts.g_inject + g_off;
+      } else {
+        RUTV_CK(launch_gaussian(s, opts.seed, i, kr, b, w.G, kr));
+      }
+      g_off += kr * b;
+      RUTV_CK(gemm_f64(s, true, false, kc, b, kr, 1.0, X, ldt, G, kr, 0.0, w.Y, kc, w.gws, w.gws_elems));
+      for (int j = 0; j < q; ++j) {
+        RUTV_CK(gemm_f64(s, false, false, kr, b, kc, 1.0, X, ldt, w.Y, kc, 0.0, w.Z, kr, w.gws, w.gws_elems));
+        RUTV_CK(gemm_f64(s, true, false, kc, b, kr, 1.0, X, ldt, w.Z, kr, 0.0, w.Y, kc, w.gws, w.gws_elems));
+      }
+      RUTV_CK(panel_qr(s, kc, b, w.Y, kc, w.tau, w.Vv, w.Rt, w.part, slot(w, 0)));
+      RUTV_CK(gemm_f64(s, true, false, b, b, kc, 1.0, w.Vv, kc, w.Vv, kc, 0.0, w.gram, b, w.gws, w.gws_elems));
+      RUTV_CK(tfactor_from_gram(s, b, w.gram, w.tau, w.S));
+      RUTV_CK(wy_right(s, m, kc, T + r0 * ldt, ldt, w.Vv, w.S, b, w.W1, w.W2, w.gws, w.gws_elems));
+      if (uv) RUTV_CK(wy_right(s, n, kc, V + r0 * ldv, ldv, w.Vv, w.S, b, w.W1, w.W2, w.gws, w.gws_elems));
+
+      RUTV_CK(panel_qr(s, kr, b, X, ldt, w.tau, w.Vu, w.R, w.part, slot(w, 1)));
+      RUTV_CK(gemm_f64(s, true, false, b, b, kr, 1.0, w.Vu, kr, w.Vu, kr, 0.0, w.gram, b, w.gws, w.gws_elems));
+      RUTV_CK(tfactor_from_gram(s, b, w.gram, w.tau, w.S));
+      if (uv) RUTV_CK(wy_right(s, m, kr, U + r0 * ldu, ldu, w.Vu, w.S, b, w.W1, w.W2, w.gws, w.gws_elems));
+      RUTV_CK(wy_left_t(s, kr, kc - b, T + r0 + c1 * ldt, ldt, w.Vu, w.S, b, w.W1, w.W2, w.gws, w.gws_elems));
+      RUTV_CK(fill(s, kr, b, X, ldt, 0.0));
+
+      RUTV_CK(jacobi_svd(s, b, w.R, b, w.Us, w.d, w.Vs, opts.max_sweeps, w.jws, slot(w, 2)));
+      set_diag_kernel<<<(b + 127) / 128, 128, 0, s>>>(b, w.d, X, ldt);
+      note_launch();
+      RUTV_CK(cudaGetLastError());
+      RUTV_CK(rot_left_t(s, b, kc - b, T + r0 + c1 * ldt, ldt, w.Us, w.tmp, w.gws, w.gws_elems));
+      RUTV_CK(rot_right(s, r0, b, T + r0 * ldt, ldt, w.Vs, w.tmp, w.gws, w.gws_elems));
+      if (uv) {
+        RUTV_CK(rot_right(s, m, b, U + r0 * ldu, ldu, w.Us, w.tmp, w.gws, w.gws_elems));
+        RUTV_CK(rot_right(s, n, b, V + r0 * ldv, ldv, w.Vs, w.tmp, w.gws, w.gws_elems));
+      }
+    } else {
+      // ---- last block: full SVD, economically through a QR when not square
+      int p;
+      const double* core;
+      int64_t ldcore;
+      if (kr == kc) {
+        p = static_cast<int>(kr);
+        core = X;
+        ldcore = ldt;
+      } else if (kr > kc) {
+        p = static_cast<int>(kc);
+        RUTV_CK(panel_qr(s, kr, p, X, ldt, w.tau, w.Vu, w.R, w.part, slot(w, 1)));
+        RUTV_CK(gemm_f64(s, true, false, p, p, kr, 1.0, w.Vu, kr, w.Vu, kr, 0.0, w.gram, p, w.gws, w.gws_elems));
+        RUTV_CK(tfactor_from_gram(s, p, w.gram, w.tau, w.S));
+        if (uv) RUTV_CK(wy_right(s, m, kr, U + r0 * ldu, ldu, w.Vu, w.S, p, w.W1, w.W2, w.gws, w.gws_elems));
+        core = w.R;
+        ldcore = p;
+      } else {
+        p = static_cast<int>(kr);
+        RUTV_CK(transpose(s, kr, kc, X, ldt, w.W1, kc));
+        RUTV_CK(panel_qr(s, kc, p, w.W1, kc, w.tau, w.Vv, w.Rt, w.part, slot(w, 0)));
+        RUTV_CK(gemm_f64(s, true, false, p, p, kc, 1.0, w.Vv, kc, w.Vv, kc, 0.0, w.gram, p, w.gws, w.gws_elems));
+        RUTV_CK(tfactor_from_gram(s, p, w.gram, w.tau, w.S));
+        RUTV_CK(wy_right(s, m, kc, T + r0 * ldt, ldt, w.Vv, w.S, p, w.W2, w.tmp, w.gws, w.gws_elems));
+        if (uv) RUTV_CK(wy_right(s, n, kc, V + r0 * ldv, ldv, w.Vv, w.S, p, w.W2, w.tmp, w.gws, w.gws_elems));
+        RUTV_CK(transpose(s, p, p, w.Rt, p, w.R, p));
+        core = w.R;
+        ldcore = p;
+      }
+      RUTV_CK(jacobi_svd(s, p, core, ldcore, w.Us, w.d, w.Vs, opts.max_sweeps, w.jws, slot(w, 2)));
+      RUTV_CK(fill(s, kr, kc, X, ldt, 0.0));
+      set_diag_kernel<<<(p + 127) / 128, 128, 0, s>>>(p, w.d, X, ldt);
+      note_launch();
+      RUTV_CK(cudaGetLastError());
+      RUTV_CK(rot_right(s, r0, p, T + r0 * ldt, ldt, w.Vs, w.tmp, w.gws, w.gws_elems));
+      if (uv) {
+        RUTV_CK(rot_right(s, m, p, U + r0 * ldu, ldu, w.Us, w.tmp, w.gws, w.gws_elems));
+        RUTV_CK(rot_right(s, n, p, V + r0 * ldv, ldv, w.Vs, w.tmp, w.gws, w.gws_elems));
+      }
+    }
+  }
+  RUTV_CK(cudaStreamSynchronize(s));
+  st = device_status(w);
+  if (prof_enabled()) prof_flush();
+
+done:
+  if (w.base) {
+    cudaFreeAsync(w.base, s);
+    cudaStreamSynchronize(s);
+  }
+  return st;
+}
+
+int randutv_factor(int64_t m, int64_t n, const double* A, int64_t lda, int b, int q, double tol,
+                   double** U, double** T, double** V, int64_t* k_reached) {
+  if (m < 1) return -1;
+  if (n < 1) return -2;
+  if (!A) return -3;
+  if (lda < m) return -4;
+  if (b < 1) return -5;
+  if (q < 0) return -6;
+  if (!(tol >= 0.0) || std::isinf(tol)) return -7;
+  if (!U) return -8;
+  if (!T) return -9;
+  if (!V) return -10;
+  if (!k_reached) return -11;
+  *U = *T = *V = nullptr;
+  double *u = nullptr, *t = nullptr, *v = nullptr;
+  if (cudaMalloc(&u, m * m * sizeof(double)) != cudaSuccess || cudaMalloc(&t, m * n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&v, n * n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(u); cudaFree(t); cudaFree(v);
+    return RANDUTV_ENOMEM;
+  }
+  int st = randutv_factor_ex(m, n, A, lda, b, q, tol, u, m, t, m, v, n, k_reached, nullptr);
+  if (st != RANDUTV_OK && st != RANDUTV_ENOCONV) {
+    cudaFree(u); cudaFree(t); cudaFree(v);
+    return st;
+  }
+  *U = u; *T = t; *V = v;
+  return st;
+}
+
+int randutv_factor_host(int64_t m, int64_t n, const double* A, int64_t lda, int b, int q, double tol,
+                        double* U, int64_t ldu, double* T, int64_t ldt, double* V, int64_t ldv,
+                        int64_t* k_reached, const randutv_opts* opts_in) {
+  randutv_opts opts;
+  if (opts_in) opts = *opts_in; else randutv_opts_default(&opts);
+  if (m < 1) return -1;
+  if (n < 1) return -2;
+  if (!A) return -3;
+  if (lda < m) return -4;
+  if (b < 1) return -5;
+  if (q < 0) return -6;
+  if (!(tol >= 0.0) || std::isinf(tol)) return -7;
+  if (opts.form_uv && !U) return -8;
+  if (opts.form_uv && ldu < m) return -9;
+  if (!T || T == A) return -10;
+  if (ldt < m) return -11;
+  if (opts.form_uv && !V) return -12;
+  if (opts.form_uv && ldv < n) return -13;
+  if (!k_reached) return -14;
+  cudaStream_t s = g_stream;
+  const bool uv = opts.form_uv != 0;
+  double *dT = nullptr, *dU = nullptr, *dV = nullptr;
+  int st = RANDUTV_OK;
+  cudaError_t e = cudaMallocAsync(&dT, m * n * sizeof(double), s);
+  if (e == cudaSuccess && uv) e = cudaMallocAsync(&dU, m * m * sizeof(double), s);
+  if (e == cudaSuccess && uv) e = cudaMallocAsync(&dV, n * n * sizeof(double), s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    st = (e == cudaErrorMemoryAllocation) ? RANDUTV_ENOMEM : cuda_status(e, "randutv_factor_host alloc");
+    goto done;
+  }
+  RUTV_CK(cudaMemcpy2DAsync(dT, m * sizeof(double), A, lda * sizeof(double), m * sizeof(double), n,
+                            cudaMemcpyHostToDevice, s));
+  st = randutv_factor_ex(m, n, dT, m, b, q, tol, dU, m, dT, m, dV, n, k_reached, &opts);
+  if (st != RANDUTV_OK && st != RANDUTV_ENOCONV) goto done;
+  RUTV_CK(cudaMemcpy2DAsync(T, ldt * sizeof(double), dT, m * sizeof(double), m * sizeof(double), n,
+                            cudaMemcpyDeviceToHost, s));
+  if (uv) {
+    RUTV_CK(cudaMemcpy2DAsync(U, ldu * sizeof(double), dU, m * sizeof(double), m * sizeof(double), m,
+                              cudaMemcpyDeviceToHost, s));
+    RUTV_CK(cudaMemcpy2DAsync(V, ldv * sizeof(double), dV, n * sizeof(double), n * sizeof(double), n,
+                              cudaMemcpyDeviceToHost, s));
+  }
+  RUTV_CK(cudaStreamSynchronize(s));
+done:
+  if (dT) cudaFreeAsync(dT, s);
+  if (dU) cudaFreeAsync(dU, s);
+  if (dV) cudaFreeAsync(dV, s);
+  cudaStreamSynchronize(s);
+  return st;
+}
+
+// ------------------------------------------------------ building blocks
+int randutv_gaussian(uint64_t seed, int64_t step, int64_t k, int64_t b, double* G, int64_t ldg) {
+  if (step < 1) return -2;
+  if (k < 0) return -3;
+  if (b < 0) return -4;
+  if (!G && k * b > 0) return -5;
+  if (ldg < std::max<int64_t>(1, k)) return -6;
+  cudaError_t e = launch_gaussian(g_stream, seed, step, k, b, G, ldg);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+  return e == cudaSuccess ? RANDUTV_OK : cuda_status(e, "randutv_gaussian");
+}
+
+int randutv_philox_words(uint64_t seed, int64_t step, int64_t k, int64_t b, uint32_t* W) {
+  if (step < 1) return -2;
+  if (k < 0) return -3;
+  if (b < 0) return -4;
+  if (!W && k * b > 0) return -5;
+  cudaError_t e = launch_philox_words(g_stream, seed, step, k, b, W);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+  return e == cudaSuccess ? RANDUTV_OK : cuda_status(e, "randutv_philox_words");
+}
+
+int randutv_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
+                  int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc) {
+  const bool ta = (transa == 'T' || transa == 't'), tb = (transb == 'T' || transb == 't');
+  if (!ta && transa != 'N' && transa != 'n') return -1;
+  if (!tb && transb != 'N' && transb != 'n') return -2;
+  if (m < 0) return -3;
+  if (n < 0) return -4;
+  if (k < 0) return -5;
+  if (lda < std::max<int64_t>(1, ta ? k : m)) return -8;
+  if (ldb < std::max<int64_t>(1, tb ? n : k)) return -10;
+  if (ldc < std::max<int64_t>(1, m)) return -13;
+  cudaStream_t s = g_stream;
+  const int64_t we = gemm_f64_work_elems(m, n, k);
+  double* ws = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (we > 0) e = cudaMallocAsync(&ws, we * sizeof(double), s);
+  if (e == cudaSuccess) e = gemm_f64(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, we);
+  if (ws) cudaFreeAsync(ws, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = e2;
+  return e == cudaSuccess ? RANDUTV_OK : cuda_status(e, "randutv_dgemm");
+}
+
+int randutv_panel_qr(int64_t k, int64_t w, double* P, int64_t ldp, double* tau, double* Vexp, double* S) {
+  if (k < 1) return -1;
+  if (w < 1 || w > k || w > 256) return -2;
+  if (!P) return -3;
+  if (ldp < k) return -4;
+  if (!tau) return -5;
+  if (!Vexp) return -6;
+  if (!S) return -7;
+  cudaStream_t s = g_stream;
+  const int wi = static_cast<int>(w);
+  const int64_t part = panel_qr_part_elems(k, wi), gw = gemm_budget(k, wi);
+  const int64_t total = part + 2 * w * w + gw + 64;
+  double* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(&ws, total * sizeof(double), s);
+  if (e != cudaSuccess) { cudaGetLastError(); return RANDUTV_ENOMEM; }
+  double* R = ws + part;
+  double* gram = R + w * w;
+  double* gws = gram + w * w;
+  unsigned* flags = reinterpret_cast<unsigned*>(gws + gw);
+  int st = RANDUTV_OK;
+  unsigned herr[4] = {0, 0, 0, 0};
+  RUTV_CK(cudaMemsetAsync(flags, 0, 4 * sizeof(unsigned), s));
+  RUTV_CK(panel_qr(s, k, wi, P, ldp, tau, Vexp, R, ws, flags));
+  RUTV_CK(gemm_f64(s, true, false, w, w, k, 1.0, Vexp, k, Vexp, k, 0.0, gram, w, gws, gw));
+  RUTV_CK(tfactor_from_gram(s, wi, gram, tau, S));
+  RUTV_CK(cudaMemcpyAsync(herr, flags, sizeof(herr), cudaMemcpyDeviceToHost, s));
+  RUTV_CK(cudaStreamSynchronize(s));
+  if (herr[2] & kDevErrTimeout) st = RANDUTV_ETIMEOUT;
+done:
+  cudaFreeAsync(ws, s);
+  cudaStreamSynchronize(s);
+  return st;
+}
+
+int randutv_small_svd(int64_t p, const double* M, int64_t ldm, double* Us, double* d, double* Vs,
+                      int max_sweeps) {
+  if (p < 1 || p > 512) return -1;
+  if (!M) return -2;
+  if (ldm < p) return -3;
+  if (!Us) return -4;
+  if (!d) return -5;
+  if (!Vs) return -6;
+  if (max_sweeps < 1) return -7;
+  cudaStream_t s = g_stream;
+  const int pi = static_cast<int>(p);
+  const int64_t we = jacobi_work_elems(pi) + 8;
+  double* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(&ws, we * sizeof(double), s);
+  if (e != cudaSuccess) { cudaGetLastError(); return RANDUTV_ENOMEM; }
+  unsigned* flags = reinterpret_cast<unsigned*>(ws + jacobi_work_elems(pi));
+  int st = RANDUTV_OK;
+  unsigned herr[4] = {0, 0, 0, 0};
+  RUTV_CK(cudaMemsetAsync(flags, 0, 4 * sizeof(unsigned), s));
+  RUTV_CK(jacobi_svd(s, pi, M, ldm, Us, d, Vs, max_sweeps, ws, flags));
+  RUTV_CK(cudaMemcpyAsync(herr, flags, sizeof(herr), cudaMemcpyDeviceToHost, s));
+  RUTV_CK(cudaStreamSynchronize(s));
+  if (herr[2] & kDevErrTimeout) st = RANDUTV_ETIMEOUT;
+  else if (herr[2] & kDevErrNoConv) st = RANDUTV_ENOCONV;
+done:
+  cudaFreeAsync(ws, s);
+  cudaStreamSynchronize(s);
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+// Host-side interfaces between the engine and its kernels (not exported).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rutv {
+
+// Process-wide stream used by every entry point.
+cudaStream_t current_stream();
+
+// Device scratch for the barrier and error words: {count, gen, err, pad} x slots.
+struct DevFlags {
+  unsigned* words = nullptr;  // 4 * kFlagSlots unsigned
+};
+constexpr int kFlagSlots = 8;
+
+// ---- prof.cu ----
+enum ProfClass { kProfGemm = 0, kProfPanel = 1, kProfTfactor = 2, kProfJacobi = 3, kProfGauss = 4,
+                 kProfOther = 5, kProfClasses = 6 };
+struct ProfTotals { double ms = 0.0; int64_t launches = 0; double flops = 0.0; double bytes = 0.0; };
+struct ProfToken { int idx; };
+void note_launch(int n = 1);
+unsigned long long launch_count();
+bool prof_enabled();
+ProfToken prof_begin(cudaStream_t s, int cls);
+void prof_end(cudaStream_t s, ProfToken t, double flops, double bytes);
+void prof_flush();
+
+// ---- gemm_f64.cu ----
+// C = alpha op(A) op(B) + beta C (column-major, FP64 DFMA).  `work` (device,
+// `work_elems` doubles) holds split-K partial sums; may be null (no split).
+cudaError_t gemm_f64(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k,
+                     double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+                     double beta, double* C, int64_t ldc, double* work, int64_t work_elems);
+// Split-K workspace (doubles) that gemm_f64 may use for an m x n x k product.
+int64_t gemm_f64_work_elems(int64_t m, int64_t n, int64_t k);
+
+// ---- philox.cu ----
+cudaError_t launch_gaussian(cudaStream_t s, uint64_t seed, int64_t step, int64_t k, int64_t b,
+                            double* G, int64_t ldg);
+cudaError_t launch_philox_words(cudaStream_t s, uint64_t seed, int64_t step, int64_t k, int64_t b,
+                                uint32_t* W);
+
+// ---- panel_qr.cu ----
+// Householder QR of the k x w panel P in place; writes tau (w), Vexp (k x w,
+// ld k, explicit unit-lower, zero columns where tau = 0) and R (w x w, ld w,
+// upper).  `part` needs panel_qr_part_elems(k, w) doubles.  `bar` points at
+// one barrier slot {count, gen, err}.
+cudaError_t panel_qr(cudaStream_t s, int64_t k, int w, double* P, int64_t ldp, double* tau,
+                     double* Vexp, double* R, double* part, unsigned* bar);
+int64_t panel_qr_part_elems(int64_t k, int w);
+// S (w x w, ld w) with H_1...H_w = I - Vexp S Vexp^T from the Gram matrix
+// Vexp^T Vexp (w x w, ld w) and tau: S = (striu(Gram) + diag(1/tau))^-1.
+cudaError_t tfactor_from_gram(cudaStream_t s, int w, const double* gram, const double* tau,
+                              double* S);
+
+// ---- jacobi.cu ----
+// SVD of a p x p matrix M (ld ldm): Us, Vs (p x p, ld p), d (p).  `work`
+// needs jacobi_work_elems(p) doubles; `bar` one barrier slot; returns after
+// queueing (status through the error word of the slot).
+cudaError_t jacobi_svd(cudaStream_t s, int p, const double* M, int64_t ldm, double* Us, double* d,
+                       double* Vs, int max_sweeps, double* work, unsigned* bar);
+int64_t jacobi_work_elems(int p);
+
+// ---- util kernels (engine.cu) ----
+cudaError_t set_identity(cudaStream_t s, int64_t n, double* X, int64_t ldx);
+cudaError_t copy_matrix(cudaStream_t s, int64_t m, int64_t n, const double* A, int64_t lda,
+                        double* B, int64_t ldb);
+
+}  // namespace rutv

@@ -1,0 +1,79 @@
+"""The C ABI library loads, exports every symbol include/randutv.h declares,
+and rejects invalid arguments before touching the GPU (no GPU needed)."""
+import ctypes
+import os
+import re
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "randutv.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(randutv_[a-z0-9_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1703_00998_gb300 import native
+    return native.lib()
+
+
+def test_header_lists_entry_points():
+    names = declared_functions()
+    for must in ("randutv_factor", "randutv_factor_ex", "randutv_set_stream", "randutv_free",
+                 "randutv_strerror", "randutv_factor_host"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1703_00998_gb300 import native
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in native.SIGNATURES, f"binding misses {name}"
+
+
+def test_strerror_and_defaults(lib):
+    from paper_1703_00998_gb300 import native
+    assert lib.randutv_strerror(0) == b"success"
+    assert b"max_sweeps" in lib.randutv_strerror(2)
+    o = native.default_opts()
+    assert (o.precision, o.form_uv, o.max_sweeps, o.p, o.seed) == (0, 1, 30, 0, 998)
+    assert o.g_inject is None
+
+
+def test_argument_validation(lib):
+    k = ctypes.c_int64(0)
+    dummy = ctypes.c_void_p(16)
+    f = lib.randutv_factor_ex
+    assert f(0, 4, dummy, 4, 2, 1, 0.0, dummy, 4, dummy, 4, dummy, 4, ctypes.byref(k), None) == -1
+    assert f(4, 0, dummy, 4, 2, 1, 0.0, dummy, 4, dummy, 4, dummy, 4, ctypes.byref(k), None) == -2
+    assert f(4, 4, None, 4, 2, 1, 0.0, dummy, 4, dummy, 4, dummy, 4, ctypes.byref(k), None) == -3
+    assert f(4, 4, dummy, 3, 2, 1, 0.0, dummy, 4, dummy, 4, dummy, 4, ctypes.byref(k), None) == -4
+    assert f(4, 4, dummy, 4, 0, 1, 0.0, dummy, 4, dummy, 4, dummy, 4, ctypes.byref(k), None) == -5
+    assert f(4, 4, dummy, 4, 2, -1, 0.0, dummy, 4, dummy, 4, dummy, 4, ctypes.byref(k), None) == -6
+    assert f(4, 4, dummy, 4, 2, 1, -1.0, dummy, 4, dummy, 4, dummy, 4, ctypes.byref(k), None) == -7
+    assert f(4, 4, dummy, 4, 2, 1, float("nan"), dummy, 4, dummy, 4, dummy, 4, ctypes.byref(k), None) == -7
+    assert f(4, 4, dummy, 4, 2, 1, 0.0, None, 4, dummy, 4, dummy, 4, ctypes.byref(k), None) == -8
+    assert f(4, 4, dummy, 4, 2, 1, 0.0, dummy, 4, dummy, 3, dummy, 4, ctypes.byref(k), None) == -11
+    assert f(4, 4, dummy, 4, 2, 1, 0.0, dummy, 4, dummy, 4, dummy, 4, None, None) == -14
+    assert lib.randutv_factor(4, 4, dummy, 4, 2, 1, 0.0, None, None, None, ctypes.byref(k)) == -8
+    assert lib.randutv_dgemm(b"X", b"N", 1, 1, 1, 1.0, dummy, 1, dummy, 1, 0.0, dummy, 1) == -1
+    assert lib.randutv_panel_qr(4, 5, dummy, 4, dummy, dummy, dummy) == -2
+    assert lib.randutv_small_svd(0, dummy, 1, dummy, dummy, dummy, 30) == -1
+    assert lib.randutv_gaussian(1, 0, 4, 4, dummy, 4) == -2
+
+
+def test_opts_validation(lib):
+    from paper_1703_00998_gb300 import native
+    k = ctypes.c_int64(0)
+    dummy = ctypes.c_void_p(16)
+    o = native.default_opts()
+    o.p = 5
+    assert lib.randutv_factor_ex(4, 4, dummy, 4, 2, 1, 0.0, dummy, 4, dummy, 4, dummy, 4, ctypes.byref(k),
+                                 ctypes.byref(o)) == -15

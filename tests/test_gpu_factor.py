@@ -1,0 +1,171 @@
+"""Whole-path parity: the CUDA randUTV through the C ABI against the oracle
+(same matrices, same Gaussian matrices), plus the closed-form properties at
+the full benchmark size."""
+import math
+import numpy as np
+import pytest
+import synth
+import oracle
+from oracle import checks
+from gpu_util import require_gpu, dev, host
+
+pytestmark = pytest.mark.gpu
+SEED = 998
+
+
+@pytest.fixture(scope="module")
+def R():
+    require_gpu()
+    import paper_1703_00998_gb300 as R
+    return R
+
+
+def gauss(i, k, b):
+    return synth.step_gaussian(SEED, i, k, b)
+
+
+def run_gpu(R, A, b, q, inject=True, **kw):
+    m, n = A.shape
+    g = dev(synth.gaussian_stream(SEED, m, n, b)) if inject and synth.stream_layout(m, n, b)[1] > 0 else None
+    out = R.factor(dev(A), b=b, q=q, g_inject=g, seed=SEED, **kw)
+    U = host(out.U) if out.U is not None else None
+    V = host(out.V) if out.V is not None else None
+    return U, host(out.T), V, out.k_reached
+
+
+def assert_valid_utv(A, U, T, V, b, k=None):
+    assert checks.residual(A, U, T, V) <= 1e-13
+    assert checks.orth_err(U) <= 1e-13 and checks.orth_err(V) <= 1e-13
+    kk = min(A.shape) if k is None else k
+    assert checks.lower_max(T[:, :kk]) == 0.0
+    assert checks.block_offdiag_max(T, b, kk) == 0.0
+    assert np.all(np.diag(T)[:kk] >= 0)
+
+
+def diag_rel(T, To):
+    d, do = np.abs(np.diag(T)), np.abs(np.diag(To))
+    scale = np.maximum(do, 1e-300)
+    return float(np.max(np.abs(d - do) / scale))
+
+
+def test_config_500_b32_q1_injected(R):
+    A = synth.make_matrix("exp50", 500, 500, 1703001)
+    U, T, V, kr = run_gpu(R, A, 32, 1)
+    Uo, To, Vo, kro = oracle.randutv(A, 32, 1, gauss)
+    assert kr == kro == 500
+    assert diag_rel(T, To) <= 1e-10
+    assert_valid_utv(A, U, T, V, 32)
+    # with the same order/sign conventions the factors agree entry by entry
+    assert np.max(np.abs(T - To)) <= 1e-9
+    assert np.max(np.abs(U - Uo)) <= 1e-9
+    assert np.max(np.abs(V - Vo)) <= 1e-9
+
+
+def test_config_500_philox_stream(R):
+    # the device Philox/Box-Muller stream instead of injected G
+    A = synth.make_matrix("exp50", 500, 500, 1703001)
+    U, T, V, _ = run_gpu(R, A, 32, 1, inject=False)
+    _, To, _, _ = oracle.randutv(A, 32, 1, gauss)
+    assert diag_rel(T, To) <= 1e-10
+    assert_valid_utv(A, U, T, V, 32)
+
+
+@pytest.mark.parametrize("m,n,b,q", [
+    (300, 200, 32, 1), (200, 300, 32, 1), (333, 333, 64, 0), (257, 257, 32, 2), (100, 100, 128, 1),
+    (130, 130, 1, 1), (65, 33, 16, 1), (33, 65, 16, 1), (1, 1, 4, 1), (3, 2, 1, 1), (2, 3, 1, 1),
+    (129, 129, 64, 1), (64, 64, 64, 1),
+])
+def test_shapes_against_oracle(R, m, n, b, q):
+    A = synth.make_matrix("exp50", m, n, 7 + m + n)
+    U, T, V, kr = run_gpu(R, A, b, q)
+    Uo, To, Vo, kro = oracle.randutv(A, b, q, gauss)
+    assert kr == kro
+    assert diag_rel(T, To) <= 1e-10
+    assert_valid_utv(A, U, T, V, min(b, m, n))
+
+
+def test_full_svd_case_matches_spectrum(R):
+    A = synth.make_matrix("exp5", 48, 48, 3)
+    s = synth.spectrum("exp5", 48)
+    U, T, V, _ = run_gpu(R, A, 64, 1)
+    np.testing.assert_allclose(np.diag(T), s, rtol=1e-12)
+    _, sj, _ = oracle.jacobi_svd(A)
+    np.testing.assert_allclose(np.diag(T), sj, rtol=1e-12)
+
+
+def test_tolerance_stop(R):
+    A = synth.make_matrix("exp", 400, 400, 8, r=6.0)
+    U, T, V, kr = run_gpu(R, A, 32, 1, tol=1e-5)
+    Uo, To, Vo, kro = oracle.randutv(A, 32, 1, gauss, tol=1e-5)
+    assert kr == kro and 0 < kr < 400
+    assert checks.residual(A, U, T, V) <= 1e-13
+    assert diag_rel(T[:kr, :kr], To[:kr, :kr]) <= 1e-10
+
+
+def test_t_only(R):
+    A = synth.make_matrix("inv", 300, 300, 5)
+    _, T1, _, _ = run_gpu(R, A, 32, 1)
+    U, T2, V, _ = run_gpu(R, A, 32, 1, form_uv=False)
+    assert U is None and V is None
+    np.testing.assert_array_equal(T1, T2)
+
+
+def test_non_finite_input_is_reported(R):
+    from paper_1703_00998_gb300 import RandutvError, native
+    A = np.ones((40, 40))
+    A[3, 5] = np.nan
+    with pytest.raises(RandutvError) as e:
+        R.factor(dev(A), b=8, q=1)
+    assert e.value.status == native.ENAN
+
+
+def test_zero_matrix(R):
+    U, T, V, kr = run_gpu(R, np.zeros((70, 70)), 16, 1)
+    assert np.all(T == 0)
+    assert checks.orth_err(U) <= 1e-14 and checks.orth_err(V) <= 1e-14
+
+
+@pytest.mark.parametrize("kind", ["exp200", "inv", "gauss"])
+def test_n4000_b128_q1_against_oracle(R, kind):
+    n = 4000
+    A = synth.make_matrix(kind, n, n, 1703002 + ["exp200", "inv", "gauss"].index(kind))
+    U, T, V, kr = run_gpu(R, A, 128, 1)
+    _, To, _, _ = oracle.randutv(A, 128, 1, gauss, form_uv=False)
+    assert kr == n
+    assert diag_rel(T, To) <= 1e-10
+    import torch
+    At, Ut, Tt, Vt = (dev(x) for x in (A, U, T, V))
+    res = float(torch.linalg.norm(At - Ut @ Tt @ Vt.T) / torch.linalg.norm(At))
+    eye = torch.eye(n, dtype=torch.float64, device="cuda")
+    assert res <= 1e-13
+    assert float((Ut.T @ Ut - eye).abs().max()) <= 1e-13
+    assert float((Vt.T @ Vt - eye).abs().max()) <= 1e-13
+    assert float(torch.tril(Tt, -1).abs().max()) == 0.0
+
+
+def test_n8000_b128_q1_full_size(R):
+    """The benchmark workload: closed forms at full size and the first block
+    against the oracle's first step (the diagonal block of step 1 is final)."""
+    import torch
+    n, b = 8000, 128
+    A = synth.make_matrix("exp200", n, n, 1703002, device="cuda")
+    Ah = host(A)
+    out = R.factor(A, b=b, q=1, seed=SEED)
+    U, T, V = out.U, out.T, out.V
+    assert out.k_reached == n
+    res = float(torch.linalg.norm(A - U @ T @ V.T) / torch.linalg.norm(A))
+    eye = torch.eye(n, dtype=torch.float64, device="cuda")
+    assert res <= 1e-13
+    assert float((U.T @ U - eye).abs().max()) <= 1e-13
+    assert float((V.T @ V - eye).abs().max()) <= 1e-13
+    assert float(torch.tril(T, -1).abs().max()) == 0.0
+    d = torch.diagonal(T)
+    assert float(d.min()) >= 0
+    # log|det A| = sum log sigma_j = -n(n+1)/400 for sigma_j = exp(-j/200)
+    logdet = float(torch.log(d).sum())
+    assert abs(logdet + n * (n + 1) / 400.0) <= 1e-9 * n
+    s = synth.spectrum("exp200", n)
+    assert abs(float(torch.linalg.norm(T)) / np.linalg.norm(s) - 1) <= 1e-12
+    _, T1, _, _ = oracle.randutv(Ah, b, 1, gauss, form_uv=False, max_steps=1)
+    d1 = host(d[:b])
+    np.testing.assert_allclose(d1, np.diag(T1)[:b], rtol=1e-10)

@@ -1,0 +1,117 @@
+"""Per-kernel parity of the CUDA building blocks against the oracle and the
+shared input generators (same seeded inputs, element by element)."""
+import numpy as np
+import pytest
+import synth
+import oracle
+from gpu_util import require_gpu, dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    require_gpu()
+    import paper_1703_00998_gb300 as R
+    return R
+
+
+@pytest.mark.parametrize("step,k,b", [(1, 500, 32), (7, 37, 5), (3, 1, 1), (16, 8000, 128)])
+def test_philox_words_bit_exact(R, step, k, b):
+    w = host(R.philox_words(998, step, k, b))
+    x = synth.gauss.step_words(998, step, k, b)   # each (ceil(k/2), b)
+    for t in range(4):
+        np.testing.assert_array_equal(w[:, :, t].T, x[t].astype(np.int64))
+
+
+@pytest.mark.parametrize("seed", [998, 2 ** 40 + 17])
+@pytest.mark.parametrize("step,k,b", [(1, 500, 32), (2, 33, 7), (5, 4001, 128)])
+def test_gaussian_matches_generator(R, seed, step, k, b):
+    g = host(R.gaussian(seed, step, k, b))
+    ref = synth.step_gaussian(seed, step, k, b)
+    # log / sincospi on the device vs libm on the host: a few ulps
+    np.testing.assert_allclose(g, ref, rtol=1e-14, atol=1e-15)
+
+
+SHAPES = [(1, 1, 1), (63, 65, 17), (130, 129, 64), (1000, 128, 3000), (128, 1000, 3000), (257, 300, 5)]
+
+
+@pytest.mark.parametrize("ta", [False, True])
+@pytest.mark.parametrize("tb", [False, True])
+@pytest.mark.parametrize("m,n,k", SHAPES)
+def test_dgemm(R, ta, tb, m, n, k):
+    rng = np.random.default_rng(m * 7 + n * 3 + k)
+    A = rng.standard_normal((k, m) if ta else (m, k))
+    B = rng.standard_normal((n, k) if tb else (k, n))
+    C = rng.standard_normal((m, n))
+    ref = 1.5 * (A.T if ta else A) @ (B.T if tb else B) - 0.5 * C
+    out = host(R.dgemm(dev(A), dev(B), ta=ta, tb=tb, alpha=1.5, beta=-0.5, C=dev(C)))
+    bound = 4 * k * 2.0 ** -53 * (np.abs(A).max() * np.abs(B).max() * k + 1)
+    assert np.max(np.abs(out - ref)) <= bound
+    out0 = host(R.dgemm(dev(A), dev(B), ta=ta, tb=tb))
+    np.testing.assert_allclose(out0, (A.T if ta else A) @ (B.T if tb else B), atol=bound)
+
+
+@pytest.mark.parametrize("k,w", [(500, 32), (37, 37), (8000, 128), (300, 1), (1, 1), (4000, 128), (200, 64)])
+def test_panel_qr(R, k, w):
+    P = np.random.default_rng(k + w).standard_normal((k, w)) * np.logspace(0, -3, w)[None, :]
+    Pout, tau, Vexp, S = (host(x) for x in R.panel_qr(dev(P)))
+    Vo, to, Ro = oracle.householder_qr(P)
+    So = oracle.tfactor(Vo, to)
+    np.testing.assert_allclose(tau, to, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(np.triu(Pout[:w]), Ro, rtol=1e-11, atol=1e-13 * np.abs(Ro).max())
+    np.testing.assert_allclose(Vexp, Vo, atol=1e-11)
+    np.testing.assert_allclose(np.tril(Pout, -1), np.tril(Vo, -1), atol=1e-11)
+    np.testing.assert_allclose(S, So, rtol=1e-10, atol=1e-11)
+    Q = np.eye(k) - Vexp @ S @ Vexp.T if k <= 600 else None
+    if Q is not None:
+        assert np.max(np.abs(Q.T @ Q - np.eye(k))) < 1e-13
+
+
+def test_panel_qr_zero_and_dependent_columns(R):
+    P = np.random.default_rng(3).standard_normal((50, 6))
+    P[:, 2] = 0.0            # zero column -> tau = 0 there
+    P[:, 4] = P[:, 1]        # dependent column
+    Pout, tau, Vexp, S = (host(x) for x in R.panel_qr(dev(P)))
+    Vo, to, Ro = oracle.householder_qr(P)
+    np.testing.assert_allclose(tau, to, atol=1e-13)
+    assert tau[2] == 0.0 and np.all(Vexp[:, 2] == 0.0)
+    Q = np.eye(50) - Vexp @ S @ Vexp.T
+    np.testing.assert_allclose(Q.T @ P, np.vstack([np.triu(Pout[:6]), np.zeros((44, 6))]), atol=1e-13)
+    np.testing.assert_allclose(np.triu(Pout[:6]), Ro, atol=1e-13)
+
+
+@pytest.mark.parametrize("p", [1, 2, 5, 20, 32, 127, 128])
+def test_small_svd(R, p):
+    A = synth.make_matrix("exp5", p, p, 11 + p)
+    M = np.linalg.qr(A)[1] if p > 1 else A   # upper triangular like R11
+    Us, d, Vs = (host(x) for x in R.small_svd(dev(M)))
+    Uo, do, Vo = oracle.svd_small(M)
+    np.testing.assert_allclose(d, do, rtol=1e-12, atol=1e-15 * do[0])
+    assert np.all(np.diff(d) <= 0) and np.all(d >= 0)
+    assert np.max(np.abs(Us.T @ Us - np.eye(p))) < 1e-13
+    assert np.max(np.abs(Vs.T @ Vs - np.eye(p))) < 1e-13
+    np.testing.assert_allclose(Us @ np.diag(d) @ Vs.T, M, atol=1e-14 * p)
+    # same order and sign convention as the oracle (spectrum exp(-j/5) is well separated)
+    np.testing.assert_allclose(Vs, Vo, atol=1e-9)
+    np.testing.assert_allclose(Us, Uo, atol=1e-9)
+
+
+def test_small_svd_zero_and_rank_deficient(R):
+    Us, d, Vs = (host(x) for x in R.small_svd(dev(np.zeros((8, 8)))))
+    assert np.all(d == 0)
+    assert np.max(np.abs(Us.T @ Us - np.eye(8))) < 1e-15
+    M = np.outer(np.arange(1.0, 7.0), np.ones(6))
+    Us, d, Vs = (host(x) for x in R.small_svd(dev(M)))
+    np.testing.assert_allclose(d[0], np.linalg.norm(M, 2), rtol=1e-14)
+    assert np.all(d[1:] <= 1e-14 * d[0])
+    assert np.max(np.abs(Us.T @ Us - np.eye(6))) < 1e-13
+    np.testing.assert_allclose(Us @ np.diag(d) @ Vs.T, M, atol=1e-13)
+
+
+def test_small_svd_sweep_cap_reports_noconv(R):
+    from paper_1703_00998_gb300 import RandutvError, native
+    M = np.random.default_rng(1).standard_normal((64, 64))
+    with pytest.raises(RandutvError) as e:
+        R.small_svd(dev(M), max_sweeps=1)
+    assert e.value.status == native.ENOCONV
