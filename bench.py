@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-verify", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
@@ -262,32 +263,37 @@ def run_own(args):
 
     # end to end through the public host-buffer entry point
     e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(1, args.steps // 2)
-    Ah = Ast.cpu().pin_memory()
-    Uh = torch.empty((n, n), dtype=torch.float64).pin_memory()
-    Th = torch.empty((n, n), dtype=torch.float64).pin_memory()
-    Vh = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    if args.no_e2e:
+        e2e_steps = 0
+    if e2e_steps > 0:
+        Ah = Ast.cpu().pin_memory()
+        Uh = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        Th = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        Vh = torch.empty((n, n), dtype=torch.float64).pin_memory()
 
     def step_host():
         st = lib.randutv_factor_host(n, n, Ah.data_ptr(), n, b, q, 0.0, Uh.data_ptr(), n, Th.data_ptr(), n,
                                      Vh.data_ptr(), n, ctypes.byref(kr), ctypes.byref(opts))
         native.check(st, "randutv_factor_host")
 
-    step_host()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    e2e = None
+    if e2e_steps > 0:
         step_host()
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * total_flops(n, q) / e2e_s / 1e12, "unit": "TFLOP/s",
-           "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 3 * 8 * n * n,
-           "ms_per_step": e2e_s * 1e3, "steps": e2e_steps}
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            step_host()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        if dist:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * total_flops(n, q) / e2e_s / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 3 * 8 * n * n,
+               "ms_per_step": e2e_s * 1e3, "steps": e2e_steps}
 
     g = prof["gemm"]
     avg_ms = g["ms"] / max(1, g["launches"])

@@ -52,7 +52,7 @@ __device__ __forceinline__ bool grid_barrier(const GridBarrier& g, unsigned nblo
       const unsigned long long t0 = global_ns();
       unsigned spins = 0;
       while (ld_acquire_u32(g.gen) == my_gen) {
-        if (++spins > 64) __nanosleep(100);
+        if (++spins > 1024) __nanosleep(32);
         if ((spins & 255u) == 0 && global_ns() - t0 > 2000000000ull) {
           atomicOr(g.err, kDevErrTimeout);
           ok = 0;

@@ -2,19 +2,22 @@
 // the full SVD of the last block) by one-sided cyclic Jacobi (Hestenes) in
 // FP64.
 //
-// Columns i < j of the working copy W of M are rotated until
-// |w_i . w_j| <= tol ||w_i|| ||w_j|| for every pair; the rotations are
-// accumulated in V, and then sigma_j = ||w_j||, u_j = w_j / sigma_j.  The
-// p(p-1)/2 pairs of a sweep are ordered as a round-robin tournament: p-1
-// rounds of p/2 disjoint pairs, so one round rotates p/2 pairs at once.
+// The rotations act on the columns of W = M^T (the rows of M): pairs i < j
+// are rotated until |w_i . w_j| <= tol ||w_i|| ||w_j|| for all of them, the
+// rotations accumulate in Q, and then W = M^T Q = N diag(sigma) with unit
+// columns N, i.e. M = Q diag(sigma) N^T: Us = Q, Vs = N.  Working on the rows
+// matters for the upper triangular R11 of randUTV: its columns are graded
+// like its singular values and one-sided Jacobi on them converges several
+// times more slowly than on its rows.  The p(p-1)/2 pairs of a sweep are
+// ordered as a round-robin tournament: p-1 rounds of p/2 disjoint pairs.
 //
 // GB300 design: FP64 runs at ~4 flop/clk/SM, so one SM would need tens of
 // milliseconds for a 128 x 128 SVD; instead one cooperative launch gives each
 // pair of a round its own CTA (p/2 CTAs) and separates the rounds by a grid
-// barrier.  W and V live in global memory (L2-resident, 2 p^2 doubles).
+// barrier.  W and Q live in global memory (L2-resident, 2 p^2 doubles).
 // Order and signs: singular values descending (stable in the column index);
 // the largest-|.| entry of each Vs column positive (lowest index on ties),
-// Us flipped with it; columns with sigma = 0 get Us columns completing an
+// Us flipped with it; zero singular values get Vs columns that complete an
 // orthonormal basis (Gram-Schmidt of unit vectors).
 #include "common.cuh"
 #include "internal.h"
@@ -30,16 +33,7 @@ __device__ __forceinline__ void rr_pair(int pp, int r, int kpair, int* a, int* b
   *b = max(x, y);
 }
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = warp_sum(v);
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double s = 0.0;
-  for (int w = 0; w < JC_NT / 32; ++w) s += red[w];
-  return s;
-}
+constexpr int JC_MAXR = 4;   // rows per thread: p <= JC_NT * JC_MAXR = 512
 
 __global__ void __launch_bounds__(JC_NT)
 jacobi_sweeps_kernel(int p, int pp, double* __restrict__ W, double* __restrict__ V, int max_sweeps,
@@ -48,7 +42,7 @@ jacobi_sweeps_kernel(int p, int pp, double* __restrict__ W, double* __restrict__
   __shared__ double s_cs[2];
   __shared__ int s_rot;
   const int nb = gridDim.x;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int sw = 0; sw < max_sweeps; ++sw) {
     for (int r = 0; r < pp - 1; ++r) {
       int i, j;
@@ -56,15 +50,24 @@ jacobi_sweeps_kernel(int p, int pp, double* __restrict__ W, double* __restrict__
       if (j < p) {
         double* wi = W + static_cast<int64_t>(i) * p;
         double* wj = W + static_cast<int64_t>(j) * p;
+        double x[JC_MAXR], y[JC_MAXR];
         double a = 0.0, b = 0.0, g = 0.0;
-        for (int t = tid; t < p; t += JC_NT) {
-          const double x = wi[t], y = wj[t];
-          a = fma(x, x, a); b = fma(y, y, b); g = fma(x, y, g);
+#pragma unroll
+        for (int u = 0; u < JC_MAXR; ++u) {
+          const int t = tid + u * JC_NT;
+          x[u] = (t < p) ? __ldcg(wi + t) : 0.0;
+          y[u] = (t < p) ? __ldcg(wj + t) : 0.0;
         }
-        a = block_sum(a, red[0]);
-        b = block_sum(b, red[1]);
-        g = block_sum(g, red[2]);
+#pragma unroll
+        for (int u = 0; u < JC_MAXR; ++u) {
+          a = fma(x[u], x[u], a); b = fma(y[u], y[u], b); g = fma(x[u], y[u], g);
+        }
+        a = warp_sum(a); b = warp_sum(b); g = warp_sum(g);
+        if (lane == 0) { red[0][warp] = a; red[1][warp] = b; red[2][warp] = g; }
+        __syncthreads();
         if (tid == 0) {
+          a = b = g = 0.0;
+          for (int w = 0; w < JC_NT / 32; ++w) { a += red[0][w]; b += red[1][w]; g += red[2][w]; }
           int rot = 0;
           if (g != 0.0 && fabs(g) > tol * sqrt(a) * sqrt(b)) {
             const double zeta = (b - a) / (2.0 * g);
@@ -81,13 +84,16 @@ jacobi_sweeps_kernel(int p, int pp, double* __restrict__ W, double* __restrict__
           const double c = s_cs[0], s = s_cs[1];
           double* vi = V + static_cast<int64_t>(i) * p;
           double* vj = V + static_cast<int64_t>(j) * p;
-          for (int t = tid; t < p; t += JC_NT) {
-            const double x = wi[t], y = wj[t];
-            wi[t] = c * x - s * y;
-            wj[t] = s * x + c * y;
-            const double u = vi[t], z = vj[t];
-            vi[t] = c * u - s * z;
-            vj[t] = s * u + c * z;
+#pragma unroll
+          for (int u = 0; u < JC_MAXR; ++u) {
+            const int t = tid + u * JC_NT;
+            if (t < p) {
+              wi[t] = c * x[u] - s * y[u];
+              wj[t] = s * x[u] + c * y[u];
+              const double q1 = __ldcg(vi + t), q2 = __ldcg(vj + t);
+              vi[t] = c * q1 - s * q2;
+              vj[t] = s * q1 + c * q2;
+            }
           }
           if (tid == 0) atomicOr(sweep_flag + sw, 1u);
         }
@@ -122,8 +128,8 @@ jacobi_finish_kernel(int p, const double* __restrict__ W, const double* __restri
     const int t = static_cast<int>(e % p), r = static_cast<int>(e / p);
     const int c = perm[r];
     const double s = sig[c];
-    Us[t + static_cast<int64_t>(r) * p] = (s > 0.0) ? W[t + static_cast<int64_t>(c) * p] / s : 0.0;
-    Vs[t + static_cast<int64_t>(r) * p] = V[t + static_cast<int64_t>(c) * p];
+    Vs[t + static_cast<int64_t>(r) * p] = (s > 0.0) ? W[t + static_cast<int64_t>(c) * p] / s : 0.0;
+    Us[t + static_cast<int64_t>(r) * p] = V[t + static_cast<int64_t>(c) * p];
     if (t == 0) d[r] = s;
   }
   __syncthreads();
@@ -131,13 +137,13 @@ jacobi_finish_kernel(int p, const double* __restrict__ W, const double* __restri
   __shared__ double red[8];
   for (int r = 0; r < p; ++r) {
     if (sig[perm[r]] > 0.0) continue;
-    double* u = Us + static_cast<int64_t>(r) * p;
+    double* u = Vs + static_cast<int64_t>(r) * p;
     for (int e = 0; e < p; ++e) {
       for (int t = tid; t < p; t += blockDim.x) u[t] = (t == e) ? 1.0 : 0.0;
       __syncthreads();
       for (int pass = 0; pass < 2; ++pass) {
         for (int q = 0; q < r; ++q) {
-          const double* uq = Us + static_cast<int64_t>(q) * p;
+          const double* uq = Vs + static_cast<int64_t>(q) * p;
           double s = 0.0;
           for (int t = tid; t < p; t += blockDim.x) s = fma(uq[t], u[t], s);
           s = warp_sum(s);
@@ -188,7 +194,7 @@ __global__ void jacobi_init_kernel(int p, const double* __restrict__ M, int64_t 
   const int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (e >= static_cast<int64_t>(p) * p) return;
   const int t = static_cast<int>(e % p), c = static_cast<int>(e / p);
-  W[e] = M[t + c * ldm];
+  W[e] = M[c + t * ldm];   // W = M^T
   V[e] = (t == c) ? 1.0 : 0.0;
 }
 
@@ -200,6 +206,7 @@ int64_t jacobi_work_elems(int p) {
 cudaError_t jacobi_svd(cudaStream_t s, int p, const double* M, int64_t ldm, double* Us, double* d,
                        double* Vs, int max_sweeps, double* work, unsigned* bar) {
   if (p < 1) return cudaSuccess;
+  if (p > JC_NT * JC_MAXR) return cudaErrorInvalidValue;
   if (max_sweeps > 64) max_sweeps = 64;
   double* W = work;
   double* V = W + static_cast<int64_t>(p) * p;

@@ -29,8 +29,10 @@ def test_philox_words_bit_exact(R, step, k, b):
 def test_gaussian_matches_generator(R, seed, step, k, b):
     g = host(R.gaussian(seed, step, k, b))
     ref = synth.step_gaussian(seed, step, k, b)
-    # log / sincospi on the device vs libm on the host: a few ulps
-    np.testing.assert_allclose(g, ref, rtol=1e-14, atol=1e-15)
+    # Same uniforms (bit-exact words); the device takes sincospi(2 u2) and the
+    # host cos(fl(2 pi u2)): |dz| <= r |d theta| + |z| few ulps with
+    # |d theta| <= 2 pi 2^-52 and r = sqrt(-2 ln u1) <= sqrt(2 ln 2^53) < 8.6.
+    np.testing.assert_allclose(g, ref, rtol=1e-14, atol=8.6 * 2 * np.pi * 2.0 ** -52)
 
 
 SHAPES = [(1, 1, 1), (63, 65, 17), (130, 129, 64), (1000, 128, 3000), (128, 1000, 3000), (257, 300, 5)]
@@ -58,6 +60,7 @@ def test_panel_qr(R, k, w):
     Pout, tau, Vexp, S = (host(x) for x in R.panel_qr(dev(P)))
     Vo, to, Ro = oracle.householder_qr(P)
     So = oracle.tfactor(Vo, to)
+    Vo[:, to == 0.0] = 0.0   # the explicit vectors of an identity reflector are stored as zero
     np.testing.assert_allclose(tau, to, rtol=1e-12, atol=1e-14)
     np.testing.assert_allclose(np.triu(Pout[:w]), Ro, rtol=1e-11, atol=1e-13 * np.abs(Ro).max())
     np.testing.assert_allclose(Vexp, Vo, atol=1e-11)
@@ -75,6 +78,8 @@ def test_panel_qr_zero_and_dependent_columns(R):
     Pout, tau, Vexp, S = (host(x) for x in R.panel_qr(dev(P)))
     Vo, to, Ro = oracle.householder_qr(P)
     np.testing.assert_allclose(tau, to, atol=1e-13)
+    Vo[:, to == 0.0] = 0.0
+    np.testing.assert_allclose(Vexp, Vo, atol=1e-12)
     assert tau[2] == 0.0 and np.all(Vexp[:, 2] == 0.0)
     Q = np.eye(50) - Vexp @ S @ Vexp.T
     np.testing.assert_allclose(Q.T @ P, np.vstack([np.triu(Pout[:6]), np.zeros((44, 6))]), atol=1e-13)
