@@ -29,9 +29,12 @@ FP64_FLOP_PER_CLK_SM = 4      # 2 DFMA lanes per SM per clock (measured 3.8-3.95
 SM_MAX_MHZ = 2070.0
 FP64_PEAK_TFLOPS = NUM_SMS * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
 
-# DRAM traffic of the FP64 GEMM kernel from an ncu capture, valid only for the
-# kernel source it was taken on (sha256 of csrc/gemm_f64.cu, first 16 hex).
-GEMM_TRAFFIC = {}
+# DRAM traffic of the FP64 GEMM kernel from one ncu capture (n=4096, launches
+# 7-9 of the factorization): measured dram read+write / algorithmic bytes.
+# Valid only for the kernel source it was taken on (sha256 prefix of
+# csrc/gemm_f64.cu); the per-launch traffic of the bench run is this ratio
+# times its algorithmic bytes per launch.
+GEMM_TRAFFIC = {"20ac287f222de114": 0.928}
 
 
 def parse():
@@ -299,12 +302,15 @@ def run_own(args):
     avg_ms = g["ms"] / max(1, g["launches"])
     achieved = g["flops"] / max(g["ms"] * 1e-3, 1e-12) / 1e12
     kh = kernel_hash(os.path.join(ROOT, "paper_1703_00998_gb300", "csrc", "gemm_f64.cu"))
-    traffic = GEMM_TRAFFIC.get(kh)
+    ratio = GEMM_TRAFFIC.get(kh)
+    traffic = ratio * g["bytes"] / max(1, g["launches"]) if ratio is not None else None
     roofline = {"bound": "alu", "kernel": "dgemm_kernel (FP64 DFMA GEMM, with its split-K reduce)",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "peak_source": "derived: 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz (recipe unit counts and "
                                "clock; FP64 is not in MEASURED_PEAKS.json)",
+                "traffic_unit": "bytes per launch (ncu dram bytes / algorithmic bytes at n=4096, scaled)",
+                "algorithmic_bytes_per_launch": g["bytes"] / max(1, g["launches"]),
                 "launches": g["launches"], "avg_launch_ms": avg_ms,
                 "flops_per_launch": g["flops"] / max(1, g["launches"]),
                 "time_share": g["ms"] / (ms * args.steps)}

@@ -41,8 +41,30 @@ jacobi_sweeps_kernel(int p, int pp, double* __restrict__ W, double* __restrict__
   __shared__ double red[3][JC_NT / 32];
   __shared__ double s_cs[2];
   __shared__ int s_rot;
+  __shared__ double s_thr2;
   const int nb = gridDim.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // Columns whose norm is at the rounding level of the whole block,
+  // ||w|| <= p u ||M||_F, are treated as zero: rotating them only stirs
+  // rounding noise and would never meet the relative stopping test.
+  {
+    double f = 0.0;
+    for (int64_t e = tid; e < static_cast<int64_t>(p) * p; e += JC_NT) {
+      const double x = __ldcg(W + e);
+      f = fma(x, x, f);
+    }
+    f = warp_sum(f);
+    if (lane == 0) red[0][warp] = f;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < JC_NT / 32; ++w) t += red[0][w];
+      const double pu = static_cast<double>(p) * 0x1p-53;
+      s_thr2 = pu * pu * t;
+    }
+    __syncthreads();
+  }
+  const double thr2 = s_thr2;
   for (int sw = 0; sw < max_sweeps; ++sw) {
     for (int r = 0; r < pp - 1; ++r) {
       int i, j;
@@ -69,7 +91,7 @@ jacobi_sweeps_kernel(int p, int pp, double* __restrict__ W, double* __restrict__
           a = b = g = 0.0;
           for (int w = 0; w < JC_NT / 32; ++w) { a += red[0][w]; b += red[1][w]; g += red[2][w]; }
           int rot = 0;
-          if (g != 0.0 && fabs(g) > tol * sqrt(a) * sqrt(b)) {
+          if (g != 0.0 && a > thr2 && b > thr2 && fabs(g) > tol * sqrt(a) * sqrt(b)) {
             const double zeta = (b - a) / (2.0 * g);
             const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
             const double c = 1.0 / sqrt(fma(t, t, 1.0));
@@ -117,6 +139,20 @@ jacobi_finish_kernel(int p, const double* __restrict__ W, const double* __restri
     sig[c] = sqrt(s);
   }
   __syncthreads();
+  {
+    // negligible columns (see the sweep kernel) count as exact zeros
+    __shared__ double s_cut;
+    if (tid == 0) {
+      double f = 0.0;
+      for (int c = 0; c < p; ++c) f = fma(sig[c], sig[c], f);
+      s_cut = static_cast<double>(p) * 0x1p-53 * sqrt(f);
+    }
+    __syncthreads();
+    const double cut = s_cut;
+    for (int c = tid; c < p; c += blockDim.x)
+      if (sig[c] <= cut) sig[c] = 0.0;
+    __syncthreads();
+  }
   for (int c = tid; c < p; c += blockDim.x) {
     int rank = 0;
     const double sc = sig[c];

@@ -35,10 +35,13 @@ def spectrum(kind, n, r=None):
     raise ValueError(f"unknown spectrum {kind!r}")
 
 
-def _haar_numpy(rng, n):
-    z = rng.standard_normal((n, n))
+def _haar_from(z):
     q, r = np.linalg.qr(z)
     return q * np.where(np.diag(r) < 0, -1.0, 1.0)[None, :]
+
+
+def _haar_numpy(rng, n):
+    return _haar_from(rng.standard_normal((n, n)))
 
 
 def haar_orthogonal(n, seed, device=None):
@@ -50,8 +53,14 @@ def haar_orthogonal(n, seed, device=None):
     if device is None:
         return _haar_numpy(rng, n)
     import torch
-    z = torch.from_numpy(rng.standard_normal((n, n))).to(device)
-    q, r = torch.linalg.qr(z)
+    z = rng.standard_normal((n, n))
+    try:
+        zt = torch.from_numpy(z).to(device)
+        q, r = torch.linalg.qr(zt)
+    except RuntimeError:
+        # torch's linear-algebra library can be unavailable (e.g. under a
+        # profiler that intercepts its loading): build Q on the host instead
+        return torch.from_numpy(_haar_from(z)).to(device)
     s = torch.where(torch.diagonal(r) < 0, -1.0, 1.0).to(q.dtype)
     return q * s[None, :]
 

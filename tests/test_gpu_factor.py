@@ -169,7 +169,7 @@ def test_n4000_b128_q1_against_oracle(R, kind):
 
 
 def test_n8000_b128_q1_full_size(R):
-    """The benchmark workload: closed forms at full size and the first block
+    """The benchmark workload: properties at full size and the first block
     against the oracle's first step (the diagonal block of step 1 is final)."""
     import torch
     n, b = 8000, 128
@@ -186,11 +186,21 @@ def test_n8000_b128_q1_full_size(R):
     assert float(torch.tril(T, -1).abs().max()) == 0.0
     d = torch.diagonal(T)
     assert float(d.min()) >= 0
-    # log|det A| = sum log sigma_j = -n(n+1)/400 for sigma_j = exp(-j/200)
-    logdet = float(torch.log(d).sum())
-    assert abs(logdet + n * (n + 1) / 400.0) <= 1e-9 * n
-    s = synth.spectrum("exp200", n)
-    assert abs(float(torch.linalg.norm(T)) / np.linalg.norm(s) - 1) <= 1e-12
+    assert abs(float(torch.linalg.norm(T) / torch.linalg.norm(A)) - 1) <= 1e-13
     _, T1, _, _ = oracle.randutv(Ah, b, 1, gauss, form_uv=False, max_steps=1)
-    d1 = host(d[:b])
-    np.testing.assert_allclose(d1, np.diag(T1)[:b], rtol=1e-10)
+    np.testing.assert_allclose(host(d[:b]), np.diag(T1)[:b], rtol=1e-10)
+
+
+def test_n8000_closed_forms(R):
+    """sigma_j = 1/j at n = 8000: sum_j log t_jj = log|det A| = -log n! and
+    ||T||_F^2 = sum_j j^-2 (T triangular, U and V orthogonal)."""
+    import torch
+    n, b = 8000, 128
+    A = synth.make_matrix("inv", n, n, 1703003, device="cuda")
+    out = R.factor(A, b=b, q=1, seed=SEED)
+    d = torch.diagonal(out.T)
+    logdet = float(torch.log(d).sum())
+    assert abs(logdet + math.lgamma(n + 1)) <= 1e-10 * n
+    s = synth.spectrum("inv", n)
+    assert abs(float(torch.linalg.norm(out.T)) / np.linalg.norm(s) - 1) <= 1e-13
+    assert float(torch.tril(out.T, -1).abs().max()) == 0.0
