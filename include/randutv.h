@@ -160,7 +160,8 @@ int randutv_panel_qr(int64_t k, int64_t w, double* P, int64_t ldp, double* tau,
                      double* Vexp, double* S);
 
 /* SVD of a p x p block M (ldm >= p): M = Us diag(d) Vs^T by one-sided cyclic
- * Jacobi in FP64; d descending and >= 0, the largest-|.| entry of each Vs
+ * Jacobi in FP64 on the rows of M (fastest for a triangular M such as the R
+ * factor of a QR, which is what the factorization passes); d descending and >= 0, the largest-|.| entry of each Vs
  * column positive (lowest index on ties).  Us, Vs are p x p with ld p.
  * Returns RANDUTV_ENOCONV (outputs still written) after max_sweeps sweeps. */
 int randutv_small_svd(int64_t p, const double* M, int64_t ldm, double* Us, double* d,

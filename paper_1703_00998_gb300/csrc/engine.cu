@@ -378,11 +378,10 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
       int p;
       const double* core;
       int64_t ldcore;
-      if (kr == kc) {
-        p = static_cast<int>(kr);
-        core = X;
-        ldcore = ldt;
-      } else if (kr > kc) {
+      if (kr >= kc) {
+        // QR first, also for a square block: one-sided Jacobi converges in a
+        // few sweeps on the rows of a triangular R, far more slowly on a
+        // general dense block of high condition number
         p = static_cast<int>(kc);
         RUTV_CK(panel_qr(s, kr, p, X, ldt, w.tau, w.Vu, w.R, w.part, slot(w, 1)));
         RUTV_CK(gemm_f64(s, true, false, p, p, kr, 1.0, w.Vu, kr, w.Vu, kr, 0.0, w.gram, p, w.gws, w.gws_elems));
