@@ -167,6 +167,24 @@ int randutv_panel_qr(int64_t k, int64_t w, double* P, int64_t ldp, double* tau,
 int randutv_small_svd(int64_t p, const double* M, int64_t ldm, double* Us, double* d,
                       double* Vs, int max_sweeps);
 
+/* randutv_small_svd without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that may not allocate
+ * device memory themselves or through the library (for example code whose
+ * host framework owns all device memory through its own allocator, code on
+ * a latency-critical path where an allocation could synchronise or fail,
+ * or a plugin that is not allowed to call the CUDA allocator).  Its scratch
+ * is one array in device global memory declared by the library (about 1 MB,
+ * held on every GPU that loads the library until the process exits), so p is
+ * limited to 256; larger p returns RANDUTV_EUNSUPPORTED with a message in
+ * randutv_last_error.  The caller passes M, Us, d and Vs exactly as for
+ * randutv_small_svd and gets the same results.  All calls on a device share
+ * the array and it keeps the last call's contents: calls whose work overlaps
+ * on the GPU (other streams or host threads) race on it and must be
+ * serialised.  The first call on each device looks up the array's device
+ * address (with that device current); make it before any stream capture. */
+int randutv_small_svd_noalloc(int64_t p, const double* M, int64_t ldm, double* Us, double* d,
+                              double* Vs, int max_sweeps);
+
 #ifdef __cplusplus
 }
 #endif

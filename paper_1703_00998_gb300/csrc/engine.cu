@@ -19,6 +19,8 @@ cudaStream_t current_stream() { return g_stream; }
 
 static thread_local char g_detail[256] = "";
 
+void set_last_error(const char* msg) { snprintf(g_detail, sizeof(g_detail), "%s", msg); }
+
 static int cuda_status(cudaError_t e, const char* where) {
   snprintf(g_detail, sizeof(g_detail), "%s: %s", where, cudaGetErrorString(e));
   return RANDUTV_ECUDA;

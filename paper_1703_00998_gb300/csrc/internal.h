@@ -7,6 +7,8 @@ namespace rutv {
 
 // Process-wide stream used by every entry point.
 cudaStream_t current_stream();
+// Set the calling thread's detail message returned by randutv_last_error.
+void set_last_error(const char* msg);
 
 // Device scratch for the barrier and error words: {count, gen, err, pad} x slots.
 struct DevFlags {

@@ -60,6 +60,7 @@ SIGNATURES = {
     "randutv_profile_read": (_i32, [_i32, ctypes.POINTER(_f64), ctypes.POINTER(_i64), ctypes.POINTER(_f64),
                                     ctypes.POINTER(_f64)]),
     "randutv_launch_count": (ctypes.c_uint64, []),
+    "randutv_small_svd_noalloc": (_i32, [_i64, _vp, _i64, _vp, _vp, _vp, _i32]),
 }
 
 PROF_GEMM, PROF_PANEL, PROF_TFACTOR, PROF_JACOBI, PROF_GAUSS, PROF_OTHER = range(6)
