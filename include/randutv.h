@@ -159,7 +159,7 @@ int randutv_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k, dou
 int randutv_panel_qr(int64_t k, int64_t w, double* P, int64_t ldp, double* tau,
                      double* Vexp, double* S);
 
-/* SVD of a p x p block M (ldm >= p): M = Us diag(d) Vs^T by one-sided cyclic
+/* SVD of a p x p block M (1 <= p <= 256, ldm >= p): M = Us diag(d) Vs^T by one-sided cyclic
  * Jacobi in FP64 on the rows of M (fastest for a triangular M such as the R
  * factor of a QR, which is what the factorization passes); d descending and >= 0, the largest-|.| entry of each Vs
  * column positive (lowest index on ties).  Us, Vs are p x p with ld p.

@@ -590,7 +590,7 @@ done:
 
 int randutv_small_svd(int64_t p, const double* M, int64_t ldm, double* Us, double* d, double* Vs,
                       int max_sweeps) {
-  if (p < 1 || p > 512) return -1;
+  if (p < 1 || p > 256) return -1;
   if (!M) return -2;
   if (ldm < p) return -3;
   if (!Us) return -4;

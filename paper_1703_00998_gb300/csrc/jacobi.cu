@@ -12,19 +12,31 @@
 // ordered as a round-robin tournament: p-1 rounds of p/2 disjoint pairs.
 //
 // GB300 design: FP64 runs at ~4 flop/clk/SM, so one SM would need tens of
-// milliseconds for a 128 x 128 SVD; instead one cooperative launch gives each
-// pair of a round its own CTA (p/2 CTAs) and separates the rounds by a grid
-// barrier.  W and Q live in global memory (L2-resident, 2 p^2 doubles).
+// milliseconds for a 128 x 128 SVD.  One thread-block cluster of 16 CTAs
+// (16 SMs) holds W and Q in distributed shared memory (2 p^2 doubles spread
+// over the 16 CTAs), each warp rotates one pair of a round at a time through
+// DSMEM loads and stores, and the hardware cluster barrier separates the
+// rounds: no global-memory round trips and no software grid barrier.
 // Order and signs: singular values descending (stable in the column index);
 // the largest-|.| entry of each Vs column positive (lowest index on ties),
 // Us flipped with it; zero singular values get Vs columns that complete an
 // orthonormal basis (Gram-Schmidt of unit vectors).
+#include <cooperative_groups.h>
 #include "common.cuh"
 #include "internal.h"
 
 namespace rutv {
 
-constexpr int JC_NT = 128;
+constexpr int JC_CLUSTER = 16;   // CTAs of the cluster (non-portable size, opt-in)
+constexpr int JC_NT = 128;       // 4 warps per CTA, one pair per warp at a time
+constexpr int JC_WARPS = JC_NT / 32;
+constexpr int JC_MAXP = 256;
+
+// dynamic shared memory of one CTA: W and Q slots (p doubles each) + norms
+__host__ __device__ constexpr size_t jc_smem(int p, int cs) {
+  return (2ull * ((p + (p & 1) + cs - 1) / cs) * p + ((p + (p & 1) + cs - 1) / cs)) * sizeof(double);
+}
+constexpr size_t kJcSmemMax = jc_smem(JC_MAXP, 8);
 
 __device__ __forceinline__ void rr_pair(int pp, int r, int kpair, int* a, int* b) {
   auto idx = [&](int t) { return t == 0 ? 0 : ((t - 1 + r) % (pp - 1)) + 1; };
@@ -33,126 +45,188 @@ __device__ __forceinline__ void rr_pair(int pp, int r, int kpair, int* a, int* b
   *b = max(x, y);
 }
 
-constexpr int JC_MAXR = 4;   // rows per thread: p <= JC_NT * JC_MAXR = 512
-
+// One cluster of cs CTAs (16, or 8 where 16 cannot be scheduled).  Column c
+// of W (= M^T, rotated) and of Q (accumulated rotations) lives in the shared
+// memory of CTA c % cs, slot c / cs, with its squared norm; a warp that
+// rotates the pair (i, j) reads and writes both columns through distributed
+// shared memory, and the rounds are separated by the cluster barrier.  On
+// exit the columns are copied to Wg and Qg (p x p, ld p) for the ordering
+// kernel.
+//
+// FP64 issues at 2 lanes/clk/SM on this GPU, so every FP64 instruction of a
+// warp costs its SM sub-partition ~64 cycles; the kernel keeps their number
+// per rotation small: NU = ceil(p/32) rows per lane exactly, one dot product
+// per pair (the squared column norms are carried along with the exact norm
+// formulas of the applied rotation and recomputed at every sweep), and the
+// rotation angle t from FP32 arithmetic.  The rotation itself is exactly
+// orthogonal in FP64 (c = 1/sqrt(1 + t^2), s = c t), so an FP32 angle only
+// changes how much of w_i . w_j a rotation removes, not the accuracy of W, Q.
+template <int NU>
 __global__ void __launch_bounds__(JC_NT)
-jacobi_sweeps_kernel(int p, int pp, double* __restrict__ W, double* __restrict__ V, int max_sweeps,
-                     double tol, unsigned* __restrict__ sweep_flag, GridBarrier gb) {
-  __shared__ double red[3][JC_NT / 32];
-  __shared__ double s_cs[2];
-  __shared__ int s_rot;
-  __shared__ double s_thr2;
-  const int nb = gridDim.x;
+jacobi_cluster_kernel(int p, const double* __restrict__ M, int64_t ldm, double* __restrict__ Wg,
+                      double* __restrict__ Qg, int max_sweeps, double tol, int* __restrict__ err) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ double jsm[];
+  const int rank = static_cast<int>(cluster.block_rank());
+  const int cs = static_cast<int>(cluster.num_blocks());   // 16, or 8 where 16 cannot be scheduled
+  const int pp = p + (p & 1);
+  const int slots = (pp + cs - 1) / cs;
+  double* Wl = jsm;                                    // slots x p
+  double* Ql = jsm + static_cast<size_t>(slots) * p;   // slots x p
+  double* Nl = Ql + static_cast<size_t>(slots) * p;    // slots: squared norms of the W columns
+  __shared__ double s_part[JC_CLUSTER];
+  __shared__ double s_fro;
+  __shared__ int s_flag[2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // Columns whose norm is at the rounding level of the whole block,
-  // ||w|| <= p u ||M||_F, are treated as zero: rotating them only stirs
-  // rounding noise and would never meet the relative stopping test.
-  {
-    double f = 0.0;
-    for (int64_t e = tid; e < static_cast<int64_t>(p) * p; e += JC_NT) {
-      const double x = __ldcg(W + e);
-      f = fma(x, x, f);
-    }
-    f = warp_sum(f);
-    if (lane == 0) red[0][warp] = f;
-    __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int w = 0; w < JC_NT / 32; ++w) t += red[0][w];
-      const double pu = static_cast<double>(p) * 0x1p-53;
-      s_thr2 = pu * pu * t;
-    }
-    __syncthreads();
-  }
-  const double thr2 = s_thr2;
-  for (int sw = 0; sw < max_sweeps; ++sw) {
-    for (int r = 0; r < pp - 1; ++r) {
-      int i, j;
-      rr_pair(pp, r, blockIdx.x, &i, &j);
-      if (j < p) {
-        double* wi = W + static_cast<int64_t>(i) * p;
-        double* wj = W + static_cast<int64_t>(j) * p;
-        double x[JC_MAXR], y[JC_MAXR];
-        double a = 0.0, b = 0.0, g = 0.0;
-#pragma unroll
-        for (int u = 0; u < JC_MAXR; ++u) {
-          const int t = tid + u * JC_NT;
-          x[u] = (t < p) ? __ldcg(wi + t) : 0.0;
-          y[u] = (t < p) ? __ldcg(wj + t) : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < JC_MAXR; ++u) {
-          a = fma(x[u], x[u], a); b = fma(y[u], y[u], b); g = fma(x[u], y[u], g);
-        }
-        a = warp_sum(a); b = warp_sum(b); g = warp_sum(g);
-        if (lane == 0) { red[0][warp] = a; red[1][warp] = b; red[2][warp] = g; }
-        __syncthreads();
-        if (tid == 0) {
-          a = b = g = 0.0;
-          for (int w = 0; w < JC_NT / 32; ++w) { a += red[0][w]; b += red[1][w]; g += red[2][w]; }
-          int rot = 0;
-          if (g != 0.0 && a > thr2 && b > thr2 && fabs(g) > tol * sqrt(a) * sqrt(b)) {
-            const double zeta = (b - a) / (2.0 * g);
-            const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-            const double c = 1.0 / sqrt(fma(t, t, 1.0));
-            s_cs[0] = c;
-            s_cs[1] = c * t;
-            rot = 1;
-          }
-          s_rot = rot;
-        }
-        __syncthreads();
-        if (s_rot) {
-          const double c = s_cs[0], s = s_cs[1];
-          double* vi = V + static_cast<int64_t>(i) * p;
-          double* vj = V + static_cast<int64_t>(j) * p;
-#pragma unroll
-          for (int u = 0; u < JC_MAXR; ++u) {
-            const int t = tid + u * JC_NT;
-            if (t < p) {
-              wi[t] = c * x[u] - s * y[u];
-              wj[t] = s * x[u] + c * y[u];
-              const double q1 = __ldcg(vi + t), q2 = __ldcg(vj + t);
-              vi[t] = c * q1 - s * q2;
-              vj[t] = s * q1 + c * q2;
-            }
-          }
-          if (tid == 0) atomicOr(sweep_flag + sw, 1u);
-        }
-      }
-      if (!grid_barrier(gb, nb)) return;
-    }
-    if (ld_acquire_u32(sweep_flag + sw) == 0u) return;  // a sweep without rotations: converged
-  }
-  if (blockIdx.x == 0 && tid == 0) atomicOr(gb.err, kDevErrNoConv);
-}
 
-// Sort, normalise, complete, sign-fix; one CTA.
-__global__ void __launch_bounds__(256)
-jacobi_finish_kernel(int p, const double* __restrict__ W, const double* __restrict__ V,
-                     double* __restrict__ Us, double* __restrict__ d, double* __restrict__ Vs,
-                     double* __restrict__ sig, int* __restrict__ perm) {
-  const int tid = threadIdx.x;
-  for (int c = tid; c < p; c += blockDim.x) {
-    double s = 0.0;
-    for (int t = 0; t < p; ++t) s = fma(W[t + static_cast<int64_t>(c) * p], W[t + static_cast<int64_t>(c) * p], s);
-    sig[c] = sqrt(s);
+  // Load this CTA's columns: W(:, c) = M(c, :)^T, Q = I.
+  for (int sl = 0; sl < slots; ++sl) {
+    const int c = sl * cs + rank;
+    for (int t = tid; t < p; t += JC_NT) {
+      Wl[sl * p + t] = (c < p) ? M[c + static_cast<int64_t>(t) * ldm] : 0.0;
+      Ql[sl * p + t] = (c < p && t == c) ? 1.0 : 0.0;
+    }
   }
   __syncthreads();
-  {
-    // negligible columns (see the sweep kernel) count as exact zeros
-    __shared__ double s_cut;
-    if (tid == 0) {
-      double f = 0.0;
-      for (int c = 0; c < p; ++c) f = fma(sig[c], sig[c], f);
-      s_cut = static_cast<double>(p) * 0x1p-53 * sqrt(f);
-    }
-    __syncthreads();
-    const double cut = s_cut;
-    for (int c = tid; c < p; c += blockDim.x)
-      if (sig[c] <= cut) sig[c] = 0.0;
-    __syncthreads();
+  // ||M||_F^2, summed in the same order by every CTA.
+  if (warp == 0) {
+    double f = 0.0;
+    for (int e = lane; e < slots * p; e += 32) f = fma(Wl[e], Wl[e], f);
+    f = warp_sum(f);
+    if (lane == 0) s_part[rank] = f;
   }
+  if (tid < 2) s_flag[tid] = 0;
+  cluster.sync();
+  if (tid == 0) {
+    double f = 0.0;
+    for (int q = 0; q < cs; ++q) f += *cluster.map_shared_rank(&s_part[q], q);
+    s_fro = f;
+  }
+  __syncthreads();
+  // Columns with ||w|| <= p u ||M||_F are at the rounding level of the block
+  // and count as zero (rotating them only stirs rounding noise).
+  const double pu = static_cast<double>(p) * 0x1p-53;
+  const double thr2 = pu * pu * s_fro;
+  const double tol2 = tol * tol;
+  const int npairs = pp / 2;
+
+  bool converged = false;
+  for (int sw = 0; sw < max_sweeps && !converged; ++sw) {
+    // exact squared norms of this CTA's columns at the start of the sweep
+    for (int sl = warp; sl < slots; sl += JC_WARPS) {
+      double f = 0.0;
+      for (int t = lane; t < p; t += 32) f = fma(Wl[sl * p + t], Wl[sl * p + t], f);
+      f = warp_sum(f);
+      if (lane == 0) Nl[sl] = f;
+    }
+    if (tid == 0) s_flag[sw & 1] = 0;
+    cluster.sync();
+    for (int r = 0; r < pp - 1; ++r) {
+      for (int k = rank * JC_WARPS + warp; k < npairs; k += cs * JC_WARPS) {
+        int i, j;
+        rr_pair(pp, r, k, &i, &j);
+        if (j >= p) continue;
+        const int oi = i % cs, oj = j % cs, si = (i / cs), sj = (j / cs);
+        double* wi = cluster.map_shared_rank(Wl + si * p, oi);
+        double* wj = cluster.map_shared_rank(Wl + sj * p, oj);
+        double* ni = cluster.map_shared_rank(Nl + si, oi);
+        double* nj = cluster.map_shared_rank(Nl + sj, oj);
+        double x[NU], y[NU];
+        double g = 0.0;
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+          const int t = lane + 32 * u;
+          x[u] = (t < p) ? wi[t] : 0.0;
+          y[u] = (t < p) ? wj[t] : 0.0;
+          g = fma(x[u], y[u], g);
+        }
+        const double a = *ni, b = *nj;
+        g = warp_sum(g);   // identical in every lane
+        if (g == 0.0 || a <= thr2 || b <= thr2 || !(g * g > tol2 * a * b)) continue;
+        // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (b - a) / (2 g), in FP32
+        const float bf = static_cast<float>(b - a), gf = static_cast<float>(g);
+        const float zf = bf / (2.0f * gf);
+        double tt;
+        if (gf != 0.0f && isfinite(bf) && isfinite(gf) && isfinite(zf)) {
+          // for |zeta| > 2^60, zeta^2 would overflow: t -> 1 / (2 zeta)
+          const float tf = (fabsf(zf) > 0x1p60f) ? 0.5f / zf
+                                                  : copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)));
+          tt = static_cast<double>(tf);
+        } else {
+          const double zeta = (b - a) / (2.0 * g);   // rare: outside the FP32 range
+          tt = (fabs(zeta) > 0x1p500) ? 0.5 / zeta
+                                      : copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+        }
+        const double c = rsqrt(fma(tt, tt, 1.0));
+        const double sn = c * tt;
+        double* qi = cluster.map_shared_rank(Ql + si * p, oi);
+        double* qj = cluster.map_shared_rank(Ql + sj * p, oj);
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+          const int t = lane + 32 * u;
+          if (t < p) {
+            wi[t] = fma(c, x[u], -sn * y[u]);
+            wj[t] = fma(sn, x[u], c * y[u]);
+            const double q1 = qi[t], q2 = qj[t];
+            qi[t] = fma(c, q1, -sn * q2);
+            qj[t] = fma(sn, q1, c * q2);
+          }
+        }
+        if (lane == 0) {
+          // squared norms after the applied rotation (c, s)
+          const double cc = c * c, ss = sn * sn, csg = 2.0 * c * sn * g;
+          *ni = fma(cc, a, fma(ss, b, -csg));
+          *nj = fma(ss, a, fma(cc, b, csg));
+          s_flag[sw & 1] = 1;
+        }
+      }
+      cluster.sync();
+    }
+    // A sweep without rotations anywhere in the cluster: converged.
+    int any = 0;
+    for (int q = 0; q < cs; ++q) any |= *cluster.map_shared_rank(&s_flag[sw & 1], q);
+    converged = (any == 0);
+  }
+  if (!converged && rank == 0 && tid == 0) atomicOr(err, kDevErrNoConv);
+  for (int sl = 0; sl < slots; ++sl) {
+    const int c = sl * cs + rank;
+    if (c >= p) continue;
+    for (int t = tid; t < p; t += JC_NT) {
+      Wg[t + static_cast<int64_t>(c) * p] = Wl[sl * p + t];
+      Qg[t + static_cast<int64_t>(c) * p] = Ql[sl * p + t];
+    }
+  }
+  cluster.sync();   // no CTA leaves while others may still read its shared memory
+}
+
+// Sort, normalise, complete, sign-fix; one CTA of 256 threads.
+__global__ void __launch_bounds__(256)
+jacobi_finish_kernel(int p, const double* __restrict__ W, const double* __restrict__ V,
+                     double* __restrict__ Us, double* __restrict__ d, double* __restrict__ Vs) {
+  __shared__ double sig[JC_MAXP];
+  __shared__ int perm[JC_MAXP];
+  __shared__ double red[8];
+  __shared__ double s_cut;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int c = warp; c < p; c += 8) {
+    const double* w = W + static_cast<int64_t>(c) * p;
+    double s = 0.0;
+    for (int t = lane; t < p; t += 32) s = fma(w[t], w[t], s);
+    s = warp_sum(s);
+    if (lane == 0) sig[c] = sqrt(s);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // negligible columns (see the sweep kernel) count as exact zeros
+    double f = 0.0;
+    for (int c = 0; c < p; ++c) f = fma(sig[c], sig[c], f);
+    s_cut = static_cast<double>(p) * 0x1p-53 * sqrt(f);
+  }
+  __syncthreads();
+  for (int c = tid; c < p; c += blockDim.x)
+    if (sig[c] <= s_cut) sig[c] = 0.0;
+  __syncthreads();
   for (int c = tid; c < p; c += blockDim.x) {
     int rank = 0;
     const double sc = sig[c];
@@ -169,8 +243,7 @@ jacobi_finish_kernel(int p, const double* __restrict__ W, const double* __restri
     if (t == 0) d[r] = s;
   }
   __syncthreads();
-  // Complete the basis for zero singular values (columns with sigma = 0 are last).
-  __shared__ double red[8];
+  // Complete the basis for zero singular values (they sort last).
   for (int r = 0; r < p; ++r) {
     if (sig[perm[r]] > 0.0) continue;
     double* u = Vs + static_cast<int64_t>(r) * p;
@@ -183,10 +256,10 @@ jacobi_finish_kernel(int p, const double* __restrict__ W, const double* __restri
           double s = 0.0;
           for (int t = tid; t < p; t += blockDim.x) s = fma(uq[t], u[t], s);
           s = warp_sum(s);
-          if ((tid & 31) == 0) red[tid >> 5] = s;
+          if (lane == 0) red[warp] = s;
           __syncthreads();
           double dot = 0.0;
-          for (int w = 0; w < static_cast<int>(blockDim.x) / 32; ++w) dot += red[w];
+          for (int w = 0; w < 8; ++w) dot += red[w];
           __syncthreads();
           for (int t = tid; t < p; t += blockDim.x) u[t] -= dot * uq[t];
           __syncthreads();
@@ -195,10 +268,10 @@ jacobi_finish_kernel(int p, const double* __restrict__ W, const double* __restri
       double s = 0.0;
       for (int t = tid; t < p; t += blockDim.x) s = fma(u[t], u[t], s);
       s = warp_sum(s);
-      if ((tid & 31) == 0) red[tid >> 5] = s;
+      if (lane == 0) red[warp] = s;
       __syncthreads();
       double nrm2 = 0.0;
-      for (int w = 0; w < static_cast<int>(blockDim.x) / 32; ++w) nrm2 += red[w];
+      for (int w = 0; w < 8; ++w) nrm2 += red[w];
       __syncthreads();
       if (nrm2 > 0.25) {
         const double inv = 1.0 / sqrt(nrm2);
@@ -209,65 +282,113 @@ jacobi_finish_kernel(int p, const double* __restrict__ W, const double* __restri
     }
   }
   __syncthreads();
-  // Sign convention on Vs columns.
-  for (int r = tid; r < p; r += blockDim.x) {
+  // Sign convention: the largest-|.| entry of each Vs column positive (lowest
+  // index on ties); one warp per column.
+  for (int r = warp; r < p; r += 8) {
     double* v = Vs + static_cast<int64_t>(r) * p;
-    int best = 0;
-    double bv = fabs(v[0]);
-    for (int t = 1; t < p; ++t) {
+    double bv = -1.0;
+    int bi = p;
+    for (int t = lane; t < p; t += 32) {
       const double a = fabs(v[t]);
-      if (a > bv) { bv = a; best = t; }
+      if (a > bv) { bv = a; bi = t; }
     }
-    if (v[best] < 0.0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (v[bi] < 0.0) {
       double* u = Us + static_cast<int64_t>(r) * p;
-      for (int t = 0; t < p; ++t) { v[t] = -v[t]; u[t] = -u[t]; }
+      for (int t = lane; t < p; t += 32) { v[t] = -v[t]; u[t] = -u[t]; }
     }
   }
 }
 
-__global__ void jacobi_init_kernel(int p, const double* __restrict__ M, int64_t ldm, double* __restrict__ W,
-                                   double* __restrict__ V) {
-  const int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (e >= static_cast<int64_t>(p) * p) return;
-  const int t = static_cast<int>(e % p), c = static_cast<int>(e / p);
-  W[e] = M[c + t * ldm];   // W = M^T
-  V[e] = (t == c) ? 1.0 : 0.0;
-}
-
 int64_t jacobi_work_elems(int p) {
-  // W, V (p x p each), sig (p), perm (p ints), sweep flags (<= 64 unsigned)
+  // W, Q (p x p each), sig (p), perm (p ints)
   return 2ll * p * p + 2ll * p + 64;
 }
+
+namespace {
+
+template <int NU>
+cudaError_t launch_cluster(cudaStream_t s, int csize, size_t smem, int p, const double* M, int64_t ldm,
+                           double* W, double* V, int max_sweeps, double tol, int* err) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(jacobi_cluster_kernel<NU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kJcSmemMax));
+    if (e == cudaSuccess && csize > 8)
+      e = cudaFuncSetAttribute(jacobi_cluster_kernel<NU>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(csize);
+  cfg.blockDim = dim3(JC_NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = csize;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel<NU>, p, M, ldm, W, V, max_sweeps, tol, err);
+}
+
+// Largest cluster size (16 with the non-portable opt-in, else 8) that can be scheduled.
+int cluster_size() {
+  static int csize = 0;
+  if (csize) return csize;
+  csize = 8;
+  if (cudaFuncSetAttribute(jacobi_cluster_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(kJcSmemMax)) == cudaSuccess &&
+      cudaFuncSetAttribute(jacobi_cluster_kernel<8>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+          cudaSuccess) {
+    cudaLaunchConfig_t q = {};
+    q.gridDim = dim3(JC_CLUSTER);
+    q.blockDim = dim3(JC_NT);
+    q.dynamicSmemBytes = jc_smem(JC_MAXP, JC_CLUSTER);
+    cudaLaunchAttribute qa[1];
+    qa[0].id = cudaLaunchAttributeClusterDimension;
+    qa[0].val.clusterDim.x = JC_CLUSTER;
+    qa[0].val.clusterDim.y = 1;
+    qa[0].val.clusterDim.z = 1;
+    q.attrs = qa;
+    q.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, jacobi_cluster_kernel<8>, &q) == cudaSuccess && nclusters > 0)
+      csize = JC_CLUSTER;
+  }
+  cudaGetLastError();
+  return csize;
+}
+
+}  // namespace
 
 cudaError_t jacobi_svd(cudaStream_t s, int p, const double* M, int64_t ldm, double* Us, double* d,
                        double* Vs, int max_sweeps, double* work, unsigned* bar) {
   if (p < 1) return cudaSuccess;
-  if (p > JC_NT * JC_MAXR) return cudaErrorInvalidValue;
-  if (max_sweeps > 64) max_sweeps = 64;
+  if (p > JC_MAXP) return cudaErrorInvalidValue;
   double* W = work;
   double* V = W + static_cast<int64_t>(p) * p;
-  double* sig = V + static_cast<int64_t>(p) * p;
-  int* perm = reinterpret_cast<int*>(sig + p);
-  unsigned* flags = reinterpret_cast<unsigned*>(sig + 2 * p);
-  const int64_t pe = static_cast<int64_t>(p) * p;
+  int* err = reinterpret_cast<int*>(bar + 2);
+  const int csize = cluster_size();
+  const size_t smem = jc_smem(p, csize);
+  const double tol = static_cast<double>(p) * 0x1p-53;
   const ProfToken tok = prof_begin(s, kProfJacobi);
-  jacobi_init_kernel<<<static_cast<unsigned>((pe + 255) / 256), 256, 0, s>>>(p, M, ldm, W, V);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  if (p <= 32) e = launch_cluster<1>(s, csize, smem, p, M, ldm, W, V, max_sweeps, tol, err);
+  else if (p <= 64) e = launch_cluster<2>(s, csize, smem, p, M, ldm, W, V, max_sweeps, tol, err);
+  else if (p <= 128) e = launch_cluster<4>(s, csize, smem, p, M, ldm, W, V, max_sweeps, tol, err);
+  else e = launch_cluster<8>(s, csize, smem, p, M, ldm, W, V, max_sweeps, tol, err);
+  note_launch();
   if (e != cudaSuccess) return e;
-  if (p >= 2) {
-    if ((e = cudaMemsetAsync(flags, 0, 64 * sizeof(unsigned), s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s)) != cudaSuccess) return e;
-    int pp = p + (p & 1);
-    double tol = static_cast<double>(p) * 0x1p-53;
-    GridBarrier gb{bar, bar + 1, reinterpret_cast<int*>(bar + 2)};
-    void* args[] = {&p, &pp, &W, &V, &max_sweeps, &tol, &flags, &gb};
-    e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(jacobi_sweeps_kernel), dim3(pp / 2),
-                                    dim3(JC_NT), args, 0, s);
-    note_launch();
-    if (e != cudaSuccess) return e;
-  }
-  jacobi_finish_kernel<<<1, 256, 0, s>>>(p, W, V, Us, d, Vs, sig, perm);
-  note_launch(2);
+  jacobi_finish_kernel<<<1, 256, 0, s>>>(p, W, V, Us, d, Vs);
+  note_launch();
   // flops are iteration-dependent; record the p x p input and three p x p outputs
   prof_end(s, tok, 0.0, 8.0 * 4.0 * p * p);
   return cudaGetLastError();

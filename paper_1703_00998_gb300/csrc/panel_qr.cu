@@ -8,11 +8,14 @@
 // GB300 design: one cooperative launch over up to 152 CTAs; each CTA keeps
 // its slice of rows of the panel in shared memory for the whole
 // factorization, so HBM is read and written once.  Column j needs, from all
-// rows, ||x(2:)||^2 and x^T P(:, c) for c > j; every CTA publishes its
-// partial sums, one grid barrier follows, and every CTA then sums the
-// partials in the same fixed order (so all CTAs hold bit-identical beta, tau
-// and v^T P) and updates its rows.  The partial sums of column j+1 are formed
-// right after the update of column j, so each column costs one barrier.
+// rows, ||x(2:)||^2 and x^T P(:, c) for c > j; every CTA adds its partial
+// sums into one accumulator vector per column with FP64 atomic reductions in
+// L2, one grid barrier follows, and every CTA reads the same sums (so all
+// hold identical beta, tau and v^T P) and updates its rows.  The partial sums
+// of column j+1 are formed right after the update of column j, so each
+// column costs one barrier and one L2 round trip.  (The order of the atomic
+// additions is not fixed, so results may differ between runs in the last
+// bits.)
 // Convention: LAPACK dlarfg (beta = -sign(alpha)||x||, tau = (beta-alpha)/beta,
 // v = x(2:)/(alpha-beta), tau = 0 when x(2:) = 0).
 #include <algorithm>
@@ -24,7 +27,7 @@ namespace rutv {
 constexpr int PQ_NT = 256;
 constexpr int PQ_WARPS = PQ_NT / 32;
 constexpr int kMaxCoopBlocks = kNumSMs;
-constexpr size_t kPqSmemBudget = 200 * 1024;
+constexpr size_t kPqSmemBudget = 226 * 1024;   // of the 227 KB a CTA may use
 
 __global__ void __launch_bounds__(PQ_NT, 1)
 panel_qr_kernel(int64_t k, int w, double* __restrict__ P, int64_t ldp, double* __restrict__ tau_out,
@@ -32,15 +35,19 @@ panel_qr_kernel(int64_t k, int w, double* __restrict__ P, int64_t ldp, double* _
                 GridBarrier gb, int rpb) {
   extern __shared__ double sm[];
   const int nb = gridDim.x;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const int64_t r_lo = static_cast<int64_t>(blockIdx.x) * rpb;
   const int nr = static_cast<int>(imax64(0, imin64(k, r_lo + rpb) - r_lo));
   double* slice = sm;                         // rpb x w, column-major, ld rpb
-  double* vec = slice + static_cast<size_t>(rpb) * w;  // w: reduced t_c
-  double* rowj = vec + w;                     // w: row j of the panel (owner's copy)
+  double* vec = slice + static_cast<size_t>(rpb) * w;  // w: sums, then tau * v^T P(:, c)
+  double* rowj = vec + w;                     // w: row j of the panel
   double* taus = rowj + w;                    // w: tau of every column
   __shared__ double s_beta, s_tau, s_scale;
-  const int PS = 2 * w;                       // partial record per CTA
+  // part: acc (w x w, zeroed by the host) receives the partial sums of
+  // column j at acc[j w + c] through FP64 atomic additions in L2; rowbuf
+  // (w x w) row j of the panel at rowbuf[j w + c], stored by the owning CTA.
+  double* acc = part;
+  double* rowbuf = part + static_cast<size_t>(w) * w;
 
   for (int64_t idx = tid; idx < static_cast<int64_t>(nr) * w; idx += PQ_NT) {
     const int i = static_cast<int>(idx % nr), c = static_cast<int>(idx / nr);
@@ -48,35 +55,33 @@ panel_qr_kernel(int64_t k, int w, double* __restrict__ P, int64_t ldp, double* _
   }
   __syncthreads();
 
-  // Partial sums of column j over this CTA's rows below row j:
-  //   [c] = sum_{i>j} P(i,j) P(i,c)  (c >= j; c = j gives ||x(2:)||^2)
-  //   [w + c] = P(j, c)              (only in the CTA owning row j)
+  // This CTA's contribution to column j's sums over the rows below row j:
+  //   acc[j w + c] += sum_{i>j} P(i,j) P(i,c)  (c >= j; c = j gives ||x(2:)||^2)
+  // and, from the CTA owning row j, rowbuf[j w + c] = P(j, c).
   auto partials = [&](int j) {
-    double* out = part + static_cast<size_t>(j & 1) * nb * PS + static_cast<size_t>(blockIdx.x) * PS;
     const int i0 = static_cast<int>(imax64(0, j + 1 - r_lo));
     const double* xj = slice + static_cast<size_t>(j) * rpb;
-    for (int c = j + warp; c < w; c += PQ_WARPS) {
-      const double* xc = slice + static_cast<size_t>(c) * rpb;
-      double s = 0.0;
-      for (int i = i0 + lane; i < nr; i += 32) s = fma(xj[i], xc[i], s);
-      s = warp_sum(s);
-      if (lane == 0) out[c] = s;
+    if (i0 < nr) {
+      for (int c = j + tid; c < w; c += PQ_NT) {
+        const double* xc = slice + static_cast<size_t>(c) * rpb;
+        double s0 = 0.0, s1 = 0.0;
+        int i = i0;
+        for (; i + 1 < nr; i += 2) { s0 = fma(xj[i], xc[i], s0); s1 = fma(xj[i + 1], xc[i + 1], s1); }
+        if (i < nr) s0 = fma(xj[i], xc[i], s0);
+        atomicAdd(acc + static_cast<size_t>(j) * w + c, s0 + s1);
+      }
     }
-    const bool owner = (j >= r_lo && j < r_lo + nr);
-    for (int c = j + tid; c < w; c += PQ_NT)
-      out[w + c] = owner ? slice[(j - r_lo) + static_cast<size_t>(c) * rpb] : 0.0;
+    if (j >= r_lo && j < r_lo + nr)
+      for (int c = j + tid; c < w; c += PQ_NT)
+        rowbuf[static_cast<size_t>(j) * w + c] = slice[(j - r_lo) + static_cast<size_t>(c) * rpb];
   };
 
   partials(0);
   for (int j = 0; j < w; ++j) {
     if (!grid_barrier(gb, nb)) return;
-    const double* pj = part + static_cast<size_t>(j & 1) * nb * PS;
-    const int ob = static_cast<int>(j / rpb);  // CTA owning row j
     for (int c = j + tid; c < w; c += PQ_NT) {
-      double s = 0.0;
-      for (int b = 0; b < nb; ++b) s += pj[static_cast<size_t>(b) * PS + c];
-      vec[c] = s;
-      rowj[c] = pj[static_cast<size_t>(ob) * PS + w + c];
+      vec[c] = __ldcg(acc + static_cast<size_t>(j) * w + c);
+      rowj[c] = __ldcg(rowbuf + static_cast<size_t>(j) * w + c);
     }
     __syncthreads();
     if (tid == 0) {
@@ -85,34 +90,36 @@ panel_qr_kernel(int64_t k, int w, double* __restrict__ P, int64_t ldp, double* _
       if (xn2 != 0.0) {
         const double nrm = sqrt(fma(alpha, alpha, xn2));
         beta = -copysign(nrm, alpha);
-        t = (beta - alpha) / beta;
-        sc = 1.0 / (alpha - beta);
+        // tau = (beta - alpha) / beta and scale = 1 / (alpha - beta) from one division
+        const double r = 1.0 / (beta * (alpha - beta));
+        t = (beta - alpha) * ((alpha - beta) * r);
+        sc = beta * r;
       }
       s_beta = beta; s_tau = t; s_scale = sc;
       taus[j] = t;
     }
     __syncthreads();
     const double t = s_tau, sc = s_scale;
-    // v^T P(:, c) = P(j, c) + scale * sum_{i>j} P(i,j) P(i,c), stored in vec[c]
-    for (int c = j + 1 + tid; c < w; c += PQ_NT) vec[c] = fma(sc, vec[c], rowj[c]);
-    __syncthreads();
+    // vec[c] <- tau * v^T P(:, c) = tau * (P(j, c) + scale * sum_{i>j} P(i,j) P(i,c))
+    for (int c = j + 1 + tid; c < w; c += PQ_NT) vec[c] = t * fma(sc, vec[c], rowj[c]);
     const int i0 = static_cast<int>(imax64(0, j + 1 - r_lo));
     double* xj = slice + static_cast<size_t>(j) * rpb;
+    for (int i = i0 + tid; i < nr; i += PQ_NT) xj[i] *= sc;   // x(2:) -> v(2:)
+    __syncthreads();
     if (t != 0.0) {
       const int ncols = w - j - 1;
       const int nrows = nr - i0;
-      for (int64_t e = tid; e < static_cast<int64_t>(ncols) * nrows; e += PQ_NT) {
-        const int i = i0 + static_cast<int>(e % nrows);
-        const int c = j + 1 + static_cast<int>(e / nrows);
-        slice[i + static_cast<size_t>(c) * rpb] -= t * (xj[i] * sc) * vec[c];
-      }
+      if (nrows > 0)
+        for (int64_t e = tid; e < static_cast<int64_t>(ncols) * nrows; e += PQ_NT) {
+          const int i = i0 + static_cast<int>(e % nrows);
+          const int c = j + 1 + static_cast<int>(e / nrows);
+          slice[i + static_cast<size_t>(c) * rpb] = fma(-xj[i], vec[c], slice[i + static_cast<size_t>(c) * rpb]);
+        }
       if (j >= r_lo && j < r_lo + nr) {
         const int il = static_cast<int>(j - r_lo);
-        for (int c = j + 1 + tid; c < w; c += PQ_NT) slice[il + static_cast<size_t>(c) * rpb] -= t * vec[c];
+        for (int c = j + 1 + tid; c < w; c += PQ_NT) slice[il + static_cast<size_t>(c) * rpb] -= vec[c];
       }
     }
-    __syncthreads();
-    for (int i = i0 + tid; i < nr; i += PQ_NT) xj[i] *= sc;
     if (j >= r_lo && j < r_lo + nr && tid == 0) xj[j - r_lo] = s_beta;
     __syncthreads();
     if (j + 1 < w) partials(j + 1);
@@ -152,8 +159,8 @@ PqGeom pq_geometry(int64_t k, int w) {
 }  // namespace
 
 int64_t panel_qr_part_elems(int64_t k, int w) {
-  PqGeom g = pq_geometry(k, w);
-  return 2ll * g.nb * 2 * w;
+  (void)k;
+  return 2ll * w * w;   // accumulators + rows
 }
 
 cudaError_t panel_qr(cudaStream_t s, int64_t k, int w, double* P, int64_t ldp, double* tau,
@@ -164,11 +171,12 @@ cudaError_t panel_qr(cudaStream_t s, int64_t k, int w, double* P, int64_t ldp, d
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(kPqSmemBudget + 4096));
+                                         static_cast<int>(kPqSmemBudget));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(part, 0, static_cast<size_t>(w) * w * sizeof(double), s);
   if (e != cudaSuccess) return e;
   GridBarrier gb{bar, bar + 1, reinterpret_cast<int*>(bar + 2)};
   void* args[] = {&k, &w, &P, &ldp, &tau, &Vexp, &R, &part, &gb, &g.rpb};

@@ -128,11 +128,14 @@ def test_tolerance_stop(R):
 
 
 def test_t_only(R):
+    # T-only mode (Table 4) computes the same T; the panel QR adds its
+    # cross-CTA partial sums with atomics, so two runs agree to rounding level
     A = synth.make_matrix("inv", 300, 300, 5)
     _, T1, _, _ = run_gpu(R, A, 32, 1)
     U, T2, V, _ = run_gpu(R, A, 32, 1, form_uv=False)
     assert U is None and V is None
-    np.testing.assert_array_equal(T1, T2)
+    assert np.max(np.abs(T1 - T2)) <= 1e-12 * np.abs(T1).max()
+    assert diag_rel(T2, T1) <= 1e-10
 
 
 def test_non_finite_input_is_reported(R):
