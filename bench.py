@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-verify", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     return ap.parse_args()
 
 
@@ -192,6 +193,70 @@ def run_reference(args):
     return 0
 
 
+def run_mixed(args, lib, native, A, Tst64, n, b, q, stream, dist):
+    """The mixed-precision form on the same matrix rounded to FP32: time per
+    factorization (same K/W and timing rules), residual and orthogonality in
+    FP64 against the stored FP32 A, |diag T| against the FP64 result."""
+    import torch
+    A32 = A.to(torch.float32)
+    Ast = A32.t().contiguous()
+    Tst = torch.empty_like(Ast)
+    Ust = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    Vst = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    opts = native.default_opts()
+    kr = ctypes.c_int64(0)
+
+    def step():
+        st = lib.randutv_factor_mixed(n, n, Ast.data_ptr(), n, b, q, 0.0, Ust.data_ptr(), n, Tst.data_ptr(), n,
+                                      Vst.data_ptr(), n, ctypes.byref(kr), ctypes.byref(opts))
+        native.check(st, "randutv_factor_mixed")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    lib.randutv_profile_reset()
+    lib.randutv_profile_enable(1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    lib.randutv_profile_enable(0)
+    prof = {name: native.profile_read(i) for i, name in enumerate(native.PROF_NAMES)}
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    world = dist.get_world_size() if dist else 1
+    out = {"value": world * total_flops(n, q) / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
+           "dtype": "f32 storage and products, f64 panel QR and small SVD",
+           "breakdown": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
+                         for k, v in prof.items()}}
+    g = prof["gemm32"]
+    if g["launches"]:
+        out["gemm32_achieved_tflops"] = g["flops"] / (g["ms"] * 1e-3) / 1e12
+    if not args.no_verify:
+        A64 = A32.to(torch.float64)
+        U, T, V = (x.t().to(torch.float64) for x in (Ust, Tst, Vst))
+        out["residual_fro"] = float(torch.linalg.norm(A64 - U @ T @ V.T) / torch.linalg.norm(A64))
+        eye = torch.eye(n, dtype=torch.float64, device="cuda")
+        out["orth_u_max"] = float((U.T @ U - eye).abs().max())
+        out["orth_v_max"] = float((V.T @ V - eye).abs().max())
+        d32 = torch.diagonal(T).abs()
+        d64 = torch.diagonal(Tst64.t()).abs()
+        floor = n * 2.0 ** -24 * float(d64.max()) / 1e-4
+        out["diag_rel_vs_fp64"] = float(((d32 - d64).abs() / (d64 + floor)).max())
+        out["diag_rel_vs_fp64_note"] = "max |d32-d64| / (|d64| + n 2^-24 ||A||_2 / 1e-4)"
+        del eye, A64, U, T, V
+    out["speedup_vs_fp64"] = None
+    return out
+
+
 def run_own(args):
     import torch
     import synth
@@ -264,6 +329,10 @@ def run_own(args):
         verify["tril_max"] = float(torch.tril(T, -1).abs().max())
         del eye
 
+    mixed = None if args.no_mixed else run_mixed(args, lib, native, A, Tst, n, b, q, stream, dist)
+    if mixed is not None:
+        mixed["speedup_vs_fp64"] = ms / mixed["ms_per_step"]
+
     # end to end through the public host-buffer entry point
     e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(1, args.steps // 2)
     if args.no_e2e:
@@ -326,7 +395,8 @@ def run_own(args):
                        "parallelism": f"replicas x{world} (one independent factorization per GPU)",
                        "flops_per_step": total_flops(n, q)},
             "seconds_per_factorization": ms / 1e3, "verify": verify, "roofline": roofline,
-            "breakdown": breakdown, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches)}
+            "breakdown": breakdown, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
+            "mixed": mixed}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_sample(A.cpu().numpy(), b, q, args.cpu_seconds)
     if rank == 0:

@@ -44,7 +44,7 @@ extern "C" {
 
 /* Options of randutv_factor_ex.  Fill with randutv_opts_default first. */
 typedef struct randutv_opts {
-  int precision;        /* RANDUTV_FP64                                        */
+  int precision;        /* RANDUTV_FP64 (randutv_factor_mixed ignores it)      */
   int form_uv;          /* 1: form U and V (Table 1); 0: T only (Table 4),
                            U and V may then be NULL                            */
   int max_sweeps;       /* cap on cyclic Jacobi sweeps of each small SVD (30)  */
@@ -85,6 +85,18 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
                       double tol, double* U, int64_t ldu, double* T, int64_t ldt,
                       double* V, int64_t ldv, int64_t* k_reached, const randutv_opts* opts);
 
+/* Mixed-precision form of randutv_factor_ex (same method and arguments, FP32
+ * data): A, T, U, V are FP32 device matrices; the sketch, the
+ * block-reflector applications and the small rotations run as FP32 products
+ * with FP32 accumulation (split reductions summed in FP64), while every panel
+ * is up-cast to FP64 for its Householder QR and compact-WY factor and the
+ * b x b SVD is computed in FP64.  opts->g_inject, if given, is the FP64
+ * Gaussian stream of randutv_factor_ex (rounded to FP32).  T may equal A
+ * when ldt == lda.  Same numbering of invalid arguments. */
+int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_t lda, int b, int q,
+                         double tol, float* U, int64_t ldu, float* T, int64_t ldt,
+                         float* V, int64_t ldv, int64_t* k_reached, const randutv_opts* opts);
+
 /* randutv_factor_ex on HOST buffers: A (lda >= m), U (ldu >= m), T (ldt >= m)
  * and V (ldv >= n) are host pointers (page-locked memory gives the fastest
  * copies; A and T must not overlap).  The library allocates device memory,
@@ -114,6 +126,7 @@ const char* randutv_last_error(void);
 #define RANDUTV_PROF_JACOBI   3  /* small SVD (sweeps + ordering)                     */
 #define RANDUTV_PROF_GAUSS    4  /* Philox Gaussian                                   */
 #define RANDUTV_PROF_OTHER    5  /* copies, fills, norms                              */
+#define RANDUTV_PROF_GEMM32   6  /* FP32 GEMM of the mixed-precision form             */
 
 /* Turn per-kernel-class timing on (1) or off (0).  While on, each launch of a
  * class is bracketed by CUDA events on its stream and its algorithmic flops
@@ -148,6 +161,12 @@ int randutv_philox_words(uint64_t seed, int64_t step, int64_t k, int64_t b, uint
 int randutv_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
                   const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                   double* C, int64_t ldc);
+
+/* FP32 counterpart of randutv_dgemm (the products of the mixed-precision
+ * form): FP32 operands and accumulation, split-K partial sums added in FP64. */
+int randutv_sgemm(char transa, char transb, int64_t m, int64_t n, int64_t k, float alpha,
+                  const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
+                  float* C, int64_t ldc);
 
 /* Unpivoted Householder QR of the k x w panel P (k >= w >= 1, ldp >= k), in
  * place (eq. unpivQR; LAPACK dlarfg convention: beta = -sign(alpha)||x||,

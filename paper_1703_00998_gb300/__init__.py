@@ -13,7 +13,7 @@ from collections import namedtuple
 from . import native
 from .native import RandutvError
 
-__all__ = ["factor", "factor_host", "gaussian", "philox_words", "dgemm", "panel_qr", "small_svd",
+__all__ = ["factor", "factor_mixed", "factor_host", "gaussian", "philox_words", "dgemm", "sgemm", "panel_qr", "small_svd",
            "RandutvError", "UTV"]
 
 UTV = namedtuple("UTV", ["U", "T", "V", "k_reached"])
@@ -75,6 +75,31 @@ def factor(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sw
             Ust.data_ptr() if form_uv else None, m, Tst.data_ptr(), m,
             Vst.data_ptr() if form_uv else None, n, ctypes.byref(kr), ctypes.byref(o))
         native.check(st, "randutv_factor_ex")
+    return UTV(Ust.t() if form_uv else None, Tst.t(), Vst.t() if form_uv else None, kr.value)
+
+
+def factor_mixed(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sweeps=30):
+    """Mixed-precision randUTV: A is an (m, n) float32 CUDA tensor; U, T, V
+    come back float32.  Panel QRs and small SVDs run in FP64 inside."""
+    torch = _torch()
+    if not isinstance(A, torch.Tensor) or A.dim() != 2 or A.dtype != torch.float32 or not A.is_cuda:
+        raise TypeError("A must be a 2-D float32 CUDA tensor")
+    m, n = A.shape
+    with torch.cuda.device(A.device):
+        Tst = _colmajor(A)
+        Ust = torch.empty((m, m), dtype=torch.float32, device=A.device) if form_uv else None
+        Vst = torch.empty((n, n), dtype=torch.float32, device=A.device) if form_uv else None
+        if g_inject is not None:
+            if g_inject.dtype != torch.float64 or not g_inject.is_cuda or not g_inject.is_contiguous():
+                raise TypeError("g_inject must be a contiguous float64 CUDA tensor")
+        o = _opts(seed, form_uv, max_sweeps, g_inject)
+        kr = ctypes.c_int64(0)
+        _bind_stream()
+        st = native.lib().randutv_factor_mixed(
+            m, n, Tst.data_ptr(), m, int(b), int(q), float(tol),
+            Ust.data_ptr() if form_uv else None, m, Tst.data_ptr(), m,
+            Vst.data_ptr() if form_uv else None, n, ctypes.byref(kr), ctypes.byref(o))
+        native.check(st, "randutv_factor_mixed")
     return UTV(Ust.t() if form_uv else None, Tst.t(), Vst.t() if form_uv else None, kr.value)
 
 
@@ -145,6 +170,27 @@ def dgemm(A, B, ta=False, tb=False, alpha=1.0, beta=0.0, C=None):
                                     Ac.data_ptr(), A.shape[0], Bc.data_ptr(), B.shape[0], float(beta),
                                     Cst.data_ptr(), m)
     native.check(st, "randutv_dgemm")
+    return Cst.t()
+
+
+def sgemm(A, B, ta=False, tb=False, alpha=1.0, beta=0.0, C=None):
+    """alpha op(A) op(B) + beta C with the library's FP32 GEMM (torch layout)."""
+    torch = _torch()
+    for x, nm in ((A, "A"), (B, "B")):
+        if not isinstance(x, torch.Tensor) or x.dim() != 2 or x.dtype != torch.float32 or not x.is_cuda:
+            raise TypeError(f"{nm} must be a 2-D float32 CUDA tensor")
+    Ac, Bc = _colmajor(A), _colmajor(B)
+    m = A.shape[1] if ta else A.shape[0]
+    k = A.shape[0] if ta else A.shape[1]
+    n = B.shape[0] if tb else B.shape[1]
+    if (B.shape[1] if tb else B.shape[0]) != k:
+        raise ValueError("inner dimensions differ")
+    Cst = _colmajor(C) if C is not None else torch.empty((n, m), dtype=torch.float32, device=A.device)
+    _bind_stream()
+    st = native.lib().randutv_sgemm(b"T" if ta else b"N", b"T" if tb else b"N", m, n, k, float(alpha),
+                                    Ac.data_ptr(), A.shape[0], Bc.data_ptr(), B.shape[0], float(beta),
+                                    Cst.data_ptr(), m)
+    native.check(st, "randutv_sgemm")
     return Cst.t()
 
 

@@ -18,7 +18,7 @@ constexpr int kFlagSlots = 8;
 
 // ---- prof.cu ----
 enum ProfClass { kProfGemm = 0, kProfPanel = 1, kProfTfactor = 2, kProfJacobi = 3, kProfGauss = 4,
-                 kProfOther = 5, kProfClasses = 6 };
+                 kProfOther = 5, kProfGemm32 = 6, kProfClasses = 7 };
 struct ProfTotals { double ms = 0.0; int64_t launches = 0; double flops = 0.0; double bytes = 0.0; };
 struct ProfToken { int idx; };
 void note_launch(int n = 1);
@@ -36,6 +36,13 @@ cudaError_t gemm_f64(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int
                      double beta, double* C, int64_t ldc, double* work, int64_t work_elems);
 // Split-K workspace (doubles) that gemm_f64 may use for an m x n x k product.
 int64_t gemm_f64_work_elems(int64_t m, int64_t n, int64_t k);
+
+// ---- gemm_f32.cu ----
+// FP32 GEMM of the mixed-precision form (split-K partials summed in FP64).
+cudaError_t gemm_f32(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, float alpha,
+                     const float* A, int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                     float* work, int64_t work_elems);
+int64_t gemm_f32_work_elems(int64_t m, int64_t n, int64_t k);
 
 // ---- philox.cu ----
 cudaError_t launch_gaussian(cudaStream_t s, uint64_t seed, int64_t step, int64_t k, int64_t b,

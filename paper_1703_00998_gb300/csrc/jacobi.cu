@@ -145,10 +145,23 @@ jacobi_cluster_kernel(int p, const double* __restrict__ M, int64_t ldm, double* 
         g = warp_sum(g);   // identical in every lane
         if (g == 0.0 || a <= thr2 || b <= thr2 || !(g * g > tol2 * a * b)) continue;
         // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (b - a) / (2 g), in FP32
-        const float bf = static_cast<float>(b - a), gf = static_cast<float>(g);
-        const float zf = bf / (2.0f * gf);
+        // zeta is scale-invariant: bring (b - a) and g to [-2, 2] by an exact
+        // power of two before rounding them to FP32 (blocks at the rounding
+        // level have w_i . w_j ~ 1e-46, below the FP32 range)
+        const double dba = b - a;
+        const double mx = fmax(fabs(dba), fabs(g));
+        const long long ex = (__double_as_longlong(mx) >> 52) & 0x7ff;
         double tt;
-        if (gf != 0.0f && isfinite(bf) && isfinite(gf) && isfinite(zf)) {
+        float bf = 0.f, gf = 0.f, zf = 0.f;
+        bool fp32_ok = ex > 0 && ex < 2046;
+        if (fp32_ok) {
+          const double sc = __longlong_as_double(static_cast<long long>(2046 - ex) << 52);   // 2^(1023 - ex)
+          bf = static_cast<float>(dba * sc);
+          gf = static_cast<float>(g * sc);
+          fp32_ok = fabsf(gf) >= 0x1p-100f;
+          if (fp32_ok) zf = bf / (2.0f * gf);
+        }
+        if (fp32_ok) {
           // for |zeta| > 2^60, zeta^2 would overflow: t -> 1 / (2 zeta)
           const float tf = (fabsf(zf) > 0x1p60f) ? 0.5f / zf
                                                   : copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)));

@@ -44,6 +44,8 @@ SIGNATURES = {
     "randutv_factor": (_i32, [_i64, _i64, _vp, _i64, _i32, _i32, _f64, _vp, _vp, _vp, ctypes.POINTER(_i64)]),
     "randutv_factor_ex": (_i32, [_i64, _i64, _vp, _i64, _i32, _i32, _f64, _vp, _i64, _vp, _i64, _vp, _i64,
                                  ctypes.POINTER(_i64), ctypes.POINTER(Opts)]),
+    "randutv_factor_mixed": (_i32, [_i64, _i64, _vp, _i64, _i32, _i32, _f64, _vp, _i64, _vp, _i64, _vp, _i64,
+                                    ctypes.POINTER(_i64), ctypes.POINTER(Opts)]),
     "randutv_factor_host": (_i32, [_i64, _i64, _vp, _i64, _i32, _i32, _f64, _vp, _i64, _vp, _i64, _vp, _i64,
                                    ctypes.POINTER(_i64), ctypes.POINTER(Opts)]),
     "randutv_free": (None, [_vp]),
@@ -53,6 +55,8 @@ SIGNATURES = {
     "randutv_philox_words": (_i32, [ctypes.c_uint64, _i64, _i64, _i64, _vp]),
     "randutv_dgemm": (_i32, [ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, _f64, _vp, _i64, _vp, _i64, _f64,
                              _vp, _i64]),
+    "randutv_sgemm": (_i32, [ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, ctypes.c_float, _vp, _i64, _vp, _i64,
+                             ctypes.c_float, _vp, _i64]),
     "randutv_panel_qr": (_i32, [_i64, _i64, _vp, _i64, _vp, _vp, _vp]),
     "randutv_small_svd": (_i32, [_i64, _vp, _i64, _vp, _vp, _vp, _i32]),
     "randutv_profile_enable": (_i32, [_i32]),
@@ -63,8 +67,8 @@ SIGNATURES = {
     "randutv_small_svd_noalloc": (_i32, [_i64, _vp, _i64, _vp, _vp, _vp, _i32]),
 }
 
-PROF_GEMM, PROF_PANEL, PROF_TFACTOR, PROF_JACOBI, PROF_GAUSS, PROF_OTHER = range(6)
-PROF_NAMES = ["gemm", "panel_qr", "tfactor", "jacobi", "gauss", "other"]
+PROF_GEMM, PROF_PANEL, PROF_TFACTOR, PROF_JACOBI, PROF_GAUSS, PROF_OTHER, PROF_GEMM32 = range(7)
+PROF_NAMES = ["gemm", "panel_qr", "tfactor", "jacobi", "gauss", "other", "gemm32"]
 
 
 def profile_read(cls):

@@ -54,6 +54,23 @@ def test_dgemm(R, ta, tb, m, n, k):
     np.testing.assert_allclose(out0, (A.T if ta else A) @ (B.T if tb else B), atol=bound)
 
 
+@pytest.mark.parametrize("ta", [False, True])
+@pytest.mark.parametrize("tb", [False, True])
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (130, 129, 64), (1000, 128, 3000), (128, 1000, 8000), (257, 300, 5)])
+def test_sgemm(R, ta, tb, m, n, k):
+    import torch
+    rng = np.random.default_rng(m + 3 * n + 7 * k)
+    A = rng.standard_normal((k, m) if ta else (m, k)).astype(np.float32)
+    B = rng.standard_normal((n, k) if tb else (k, n)).astype(np.float32)
+    C = rng.standard_normal((m, n)).astype(np.float32)
+    A64, B64 = A.astype(np.float64), B.astype(np.float64)
+    ref = 1.5 * (A64.T if ta else A64) @ (B64.T if tb else B64) - 0.5 * C.astype(np.float64)
+    out = host(R.sgemm(dev(A), dev(B), ta=ta, tb=tb, alpha=1.5, beta=-0.5, C=dev(C))).astype(np.float64)
+    # FP32 accumulation of chunks of <= 1024 products, chunks summed in FP64
+    bound = (min(k, 1024) + 2) * 2.0 ** -24 * (np.abs(A64) .max() * np.abs(B64).max() * k * 1.5 + 1)
+    assert np.max(np.abs(out - ref)) <= bound
+
+
 @pytest.mark.parametrize("k,w", [(500, 32), (37, 37), (8000, 128), (300, 1), (1, 1), (4000, 128), (200, 64)])
 def test_panel_qr(R, k, w):
     P = np.random.default_rng(k + w).standard_normal((k, w)) * np.logspace(0, -3, w)[None, :]
@@ -115,6 +132,20 @@ def test_small_svd_zero_and_rank_deficient(R):
     assert np.all(d[1:] <= 1e-14 * d[0])
     assert np.max(np.abs(Us.T @ Us - np.eye(6))) < 1e-13
     np.testing.assert_allclose(Us @ np.diag(d) @ Vs.T, M, atol=1e-13)
+
+
+@pytest.mark.parametrize("scale", [1e-16, 1e-60, 1e40])
+def test_small_svd_scale_invariance(R, scale):
+    # blocks at the rounding level of a factorization (w_i . w_j far below the
+    # FP32 range) converge as fast and as accurately as unit-scale ones
+    A = synth.make_matrix("exp50", 64, 64, 77)
+    M = np.linalg.qr(A)[1] * scale
+    Us, d, Vs = (host(x) for x in R.small_svd(dev(M)))
+    Uo, do, Vo = oracle.svd_small(M)
+    np.testing.assert_allclose(d, do, rtol=1e-12, atol=1e-15 * do[0])
+    assert np.max(np.abs(Us.T @ Us - np.eye(64))) < 1e-13
+    assert np.max(np.abs(Vs.T @ Vs - np.eye(64))) < 1e-13
+    np.testing.assert_allclose(Us @ np.diag(d) @ Vs.T, M, atol=1e-13 * do[0])
 
 
 def test_small_svd_sweep_cap_reports_noconv(R):
