@@ -192,7 +192,7 @@ int randutv_small_svd(int64_t p, const double* M, int64_t ldm, double* Us, doubl
  * host framework owns all device memory through its own allocator, code on
  * a latency-critical path where an allocation could synchronise or fail,
  * or a plugin that is not allowed to call the CUDA allocator).  Its scratch
- * is one array in device global memory declared by the library (about 1 MB,
+ * is one array in device global memory declared by the library (about 4 MB,
  * held on every GPU that loads the library until the process exits), so p is
  * limited to 256; larger p returns RANDUTV_EUNSUPPORTED with a message in
  * randutv_last_error.  The caller passes M, Us, d and Vs exactly as for

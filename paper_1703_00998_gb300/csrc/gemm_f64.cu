@@ -6,7 +6,8 @@
 // about 4 flop/clk/SM on the CUDA cores (the FP64 mma.sync path measures
 // slower), so these products are bound by DFMA issue, not by HBM: a 64 x 64
 // register-blocked tile re-reads each operand element 64 times from shared
-// memory, far above what the 2-DFMA/clk/SM pipe needs.  What matters is
+// memory, far above what the 2-DFMA/clk/SM pipe needs (small products use
+// a 32 x 32 tile so that they still spread over many SMs).  What matters is
 // keeping every SM's DFMA pipe busy, so thin products are split along K until
 // the work divides evenly over the 152 SMs (partials reduced by a second,
 // memory-bound kernel).
@@ -16,13 +17,18 @@
 
 namespace rutv {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BK = 16, NT = 256;
 
-template <bool TA, bool TB>
+// Tile (16 TM) x (16 TM) per CTA, TM x TM outputs per thread: TM = 4 for the
+// large products, TM = 2 for small ones (p x p products of the small SVD),
+// which gives four times as many CTAs.
+template <bool TA, bool TB, int TM>
 __global__ void __launch_bounds__(NT, 2)
 dgemm_kernel(int64_t M, int64_t N, int64_t K, double alpha, const double* __restrict__ A, int64_t lda,
              const double* __restrict__ B, int64_t ldb, double beta, double* __restrict__ C, int64_t ldc,
              double* __restrict__ part, int64_t kchunk) {
+  constexpr int BM = 16 * TM, BN = 16 * TM;
+  constexpr int LA = BM * BK / NT;   // elements of A (and of B) each thread loads per tile
   __shared__ __align__(16) double As[BK][BM];
   __shared__ __align__(16) double Bs[BK][BN];
   const int tid = threadIdx.x;
@@ -32,27 +38,31 @@ dgemm_kernel(int64_t M, int64_t N, int64_t K, double alpha, const double* __rest
   const int64_t kbeg = static_cast<int64_t>(blockIdx.z) * kchunk;
   const int64_t kend = min(K, kbeg + kchunk);
 
-  double acc[4][4];
+  double acc[TM][TM];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < TM; ++j) acc[i][j] = 0.0;
 
-  double ra[4], rb[4];
+  // A tile BM x BK: untransposed, consecutive threads walk the BM rows;
+  // transposed, they walk the BK entries of one row of op(A).  B likewise.
+  double ra[LA], rb[LA];
   auto load = [&](int64_t k0) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < LA; ++r) {
+      const int e = tid + r * NT;
       int i, kk;
-      if (!TA) { i = tid % 64; kk = tid / 64 + 4 * r; } else { kk = tid % 16; i = tid / 16 + 16 * r; }
+      if (!TA) { i = e % BM; kk = e / BM; } else { kk = e % BK; i = e / BK; }
       const int64_t gi = m0 + i, gk = k0 + kk;
       double v = 0.0;
       if (gi < M && gk < kend) v = TA ? A[gk + gi * lda] : A[gi + gk * lda];
       ra[r] = v;
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < LA; ++r) {
+      const int e = tid + r * NT;
       int j, kk;
-      if (!TB) { kk = tid % 16; j = tid / 16 + 16 * r; } else { j = tid % 64; kk = tid / 64 + 4 * r; }
+      if (!TB) { kk = e % BK; j = e / BK; } else { j = e % BN; kk = e / BN; }
       const int64_t gj = n0 + j, gk = k0 + kk;
       double v = 0.0;
       if (gj < N && gk < kend) v = TB ? B[gj + gk * ldb] : B[gk + gj * ldb];
@@ -61,9 +71,10 @@ dgemm_kernel(int64_t M, int64_t N, int64_t K, double alpha, const double* __rest
   };
   auto store = [&]() {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      if (!TA) As[tid / 64 + 4 * r][tid % 64] = ra[r]; else As[tid % 16][tid / 16 + 16 * r] = ra[r];
-      if (!TB) Bs[tid % 16][tid / 16 + 16 * r] = rb[r]; else Bs[tid / 64 + 4 * r][tid % 64] = rb[r];
+    for (int r = 0; r < LA; ++r) {
+      const int e = tid + r * NT;
+      if (!TA) As[e / BM][e % BM] = ra[r]; else As[e % BK][e / BK] = ra[r];
+      if (!TB) Bs[e % BK][e / BK] = rb[r]; else Bs[e / BN][e % BN] = rb[r];
     }
   };
 
@@ -74,27 +85,29 @@ dgemm_kernel(int64_t M, int64_t N, int64_t K, double alpha, const double* __rest
     if (k0 + BK < kend) load(k0 + BK);  // prefetch the next tile into registers
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      const double2 a01 = *reinterpret_cast<const double2*>(&As[kk][tx * 4]);
-      const double2 a23 = *reinterpret_cast<const double2*>(&As[kk][tx * 4 + 2]);
-      const double2 b01 = *reinterpret_cast<const double2*>(&Bs[kk][ty * 4]);
-      const double2 b23 = *reinterpret_cast<const double2*>(&Bs[kk][ty * 4 + 2]);
-      const double a[4] = {a01.x, a01.y, a23.x, a23.y};
-      const double b[4] = {b01.x, b01.y, b23.x, b23.y};
+      double a[TM], b[TM];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int h = 0; h < TM; h += 2) {
+        const double2 av = *reinterpret_cast<const double2*>(&As[kk][tx * TM + h]);
+        const double2 bv = *reinterpret_cast<const double2*>(&Bs[kk][ty * TM + h]);
+        a[h] = av.x; a[h + 1] = av.y;
+        b[h] = bv.x; b[h + 1] = bv.y;
+      }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TM; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
 
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int64_t gj = n0 + ty * 4 + j;
+  for (int j = 0; j < TM; ++j) {
+    const int64_t gj = n0 + ty * TM + j;
     if (gj >= N) continue;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int64_t gi = m0 + tx * 4 + i;
+    for (int i = 0; i < TM; ++i) {
+      const int64_t gi = m0 + tx * TM + i;
       if (gi >= M) continue;
       if (part) {
         part[static_cast<int64_t>(blockIdx.z) * M * N + gi + gj * M] = acc[i][j];
@@ -127,27 +140,32 @@ __global__ void scale_kernel(int64_t M, int64_t N, double beta, double* __restri
 
 namespace {
 
-struct Plan { int splits; int64_t kchunk; };
+struct Plan { int splits; int64_t kchunk; int tm; };
 
-// Choose the K split: minimise the modelled time of the busiest SM (units of
-// BM x BN x kchunk handed out evenly over the SMs, FP64-bound) plus the
+// Choose the tile (64 or 32 square) and the K split: minimise the modelled
+// time of the busiest SM (units of tile x kchunk handed out evenly over the
+// SMs, FP64-bound; the 32 tile issues about 15 % more per flop) plus the
 // memory-bound reduction of the partial sums.
 Plan plan_gemm(int64_t M, int64_t N, int64_t K, int64_t work_elems) {
-  const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
-  Plan best{1, ((K + BK - 1) / BK) * BK};
+  Plan best{1, ((K + BK - 1) / BK) * BK, 4};
   double best_t = 1e300;
   const double fma_per_s = 2.0 * 1.9e9;   // one SM's DFMA rate
-  for (int s = 1; s <= 64; ++s) {
-    int64_t kc = (K + s - 1) / s;
-    kc = ((kc + BK - 1) / BK) * BK;
-    if (s > 1 && kc < 64) break;
-    const int se = static_cast<int>((K + kc - 1) / kc);
-    if (se > 1 && se * M * N > work_elems) break;
-    const int64_t units = tiles * se;
-    const int64_t per_sm = (units + kNumSMs - 1) / kNumSMs;
-    double t = per_sm * static_cast<double>(BM * BN) * kc / fma_per_s;
-    if (se > 1) t += 4e-6 + (se + 2.0) * M * N * 8.0 / 5.0e12;
-    if (t < best_t * 0.999) { best_t = t; best = Plan{se, kc}; }
+  for (int tm = 4; tm >= 2; tm -= 2) {
+    const int bm = 16 * tm;
+    const int64_t tiles = ((M + bm - 1) / bm) * ((N + bm - 1) / bm);
+    const double eff = (tm == 4) ? 1.0 : 1.15;
+    for (int s = 1; s <= 64; ++s) {
+      int64_t kc = (K + s - 1) / s;
+      kc = ((kc + BK - 1) / BK) * BK;
+      if (s > 1 && kc < 64) break;
+      const int se = static_cast<int>((K + kc - 1) / kc);
+      if (se > 1 && se * M * N > work_elems) break;
+      const int64_t units = tiles * se;
+      const int64_t per_sm = (units + kNumSMs - 1) / kNumSMs;
+      double t = eff * per_sm * static_cast<double>(bm * bm) * kc / fma_per_s + 2e-6;
+      if (se > 1) t += 4e-6 + (se + 2.0) * M * N * 8.0 / 5.0e12;
+      if (t < best_t * 0.999) { best_t = t; best = Plan{se, kc, tm}; }
+    }
   }
   return best;
 }
@@ -172,16 +190,24 @@ cudaError_t gemm_f64(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int
   }
   Plan p = plan_gemm(m, n, k, work ? work_elems : 0);
   const ProfToken tok = prof_begin(s, kProfGemm);
-  dim3 grid(static_cast<unsigned>((m + BM - 1) / BM), static_cast<unsigned>((n + BN - 1) / BN),
+  const int bm = 16 * p.tm;
+  dim3 grid(static_cast<unsigned>((m + bm - 1) / bm), static_cast<unsigned>((n + bm - 1) / bm),
             static_cast<unsigned>(p.splits));
   double* part = p.splits > 1 ? work : nullptr;
-#define RUTV_GEMM_LAUNCH(TA_, TB_)                                                            \
-  dgemm_kernel<TA_, TB_><<<grid, NT, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, part, \
-                                            p.kchunk)
-  if (!ta && !tb) RUTV_GEMM_LAUNCH(false, false);
-  else if (ta && !tb) RUTV_GEMM_LAUNCH(true, false);
-  else if (!ta && tb) RUTV_GEMM_LAUNCH(false, true);
-  else RUTV_GEMM_LAUNCH(true, true);
+#define RUTV_GEMM_LAUNCH(TA_, TB_, TM_)                                                              \
+  dgemm_kernel<TA_, TB_, TM_><<<grid, NT, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, part, \
+                                                 p.kchunk)
+  if (p.tm == 4) {
+    if (!ta && !tb) RUTV_GEMM_LAUNCH(false, false, 4);
+    else if (ta && !tb) RUTV_GEMM_LAUNCH(true, false, 4);
+    else if (!ta && tb) RUTV_GEMM_LAUNCH(false, true, 4);
+    else RUTV_GEMM_LAUNCH(true, true, 4);
+  } else {
+    if (!ta && !tb) RUTV_GEMM_LAUNCH(false, false, 2);
+    else if (ta && !tb) RUTV_GEMM_LAUNCH(true, false, 2);
+    else if (!ta && tb) RUTV_GEMM_LAUNCH(false, true, 2);
+    else RUTV_GEMM_LAUNCH(true, true, 2);
+  }
 #undef RUTV_GEMM_LAUNCH
   note_launch();
   cudaError_t e = cudaGetLastError();

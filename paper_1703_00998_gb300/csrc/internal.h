@@ -64,6 +64,9 @@ cudaError_t tfactor_from_gram(cudaStream_t s, int w, const double* gram, const d
                               double* S);
 
 // ---- jacobi.cu ----
+// Scratch of jacobi_svd for a p x p block: W, Q, two p x p temporaries and the
+// split-K partials of the p x p products (4 p^2), plus slack.
+constexpr int64_t jacobi_work_elems_for(int p) { return 8ll * p * p + 2ll * p + 64; }
 // SVD of a p x p matrix M (ld ldm): Us, Vs (p x p, ld p), d (p).  `work`
 // needs jacobi_work_elems(p) doubles; `bar` one barrier slot; returns after
 // queueing (status through the error word of the slot).

@@ -37,6 +37,9 @@ __host__ __device__ constexpr size_t jc_smem(int p, int cs) {
   return (2ull * ((p + (p & 1) + cs - 1) / cs) * p + ((p + (p & 1) + cs - 1) / cs)) * sizeof(double);
 }
 constexpr size_t kJcSmemMax = jc_smem(JC_MAXP, 8);
+__host__ __device__ constexpr size_t jc_smem32(int p, int cs) {
+  return (2ull * ((p + (p & 1) + cs - 1) / cs) * p + ((p + (p & 1) + cs - 1) / cs)) * sizeof(float);
+}
 
 __device__ __forceinline__ void rr_pair(int pp, int r, int kpair, int* a, int* b) {
   auto idx = [&](int t) { return t == 0 ? 0 : ((t - 1 + r) % (pp - 1)) + 1; };
@@ -63,8 +66,8 @@ __device__ __forceinline__ void rr_pair(int pp, int r, int kpair, int* a, int* b
 // changes how much of w_i . w_j a rotation removes, not the accuracy of W, Q.
 template <int NU>
 __global__ void __launch_bounds__(JC_NT)
-jacobi_cluster_kernel(int p, const double* __restrict__ M, int64_t ldm, double* __restrict__ Wg,
-                      double* __restrict__ Qg, int max_sweeps, double tol, int* __restrict__ err) {
+jacobi_cluster_kernel(int p, const double* __restrict__ M, int64_t ldm, const double* W0, const double* Q0,
+                      double* Wg, double* Qg, int max_sweeps, double tol, int* __restrict__ err) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ double jsm[];
@@ -80,12 +83,18 @@ jacobi_cluster_kernel(int p, const double* __restrict__ M, int64_t ldm, double* 
   __shared__ int s_flag[2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  // Load this CTA's columns: W(:, c) = M(c, :)^T, Q = I.
+  // Load this CTA's columns: W(:, c) = M(c, :)^T and Q = I, or the given
+  // starting point W0 = M^T Q0 (p x p, ld p) after the FP32 sweeps.
   for (int sl = 0; sl < slots; ++sl) {
     const int c = sl * cs + rank;
     for (int t = tid; t < p; t += JC_NT) {
-      Wl[sl * p + t] = (c < p) ? M[c + static_cast<int64_t>(t) * ldm] : 0.0;
-      Ql[sl * p + t] = (c < p && t == c) ? 1.0 : 0.0;
+      if (W0) {
+        Wl[sl * p + t] = (c < p) ? W0[t + static_cast<int64_t>(c) * p] : 0.0;
+        Ql[sl * p + t] = (c < p) ? Q0[t + static_cast<int64_t>(c) * p] : 0.0;
+      } else {
+        Wl[sl * p + t] = (c < p) ? M[c + static_cast<int64_t>(t) * ldm] : 0.0;
+        Ql[sl * p + t] = (c < p && t == c) ? 1.0 : 0.0;
+      }
     }
   }
   __syncthreads();
@@ -213,6 +222,158 @@ jacobi_cluster_kernel(int p, const double* __restrict__ M, int64_t ldm, double* 
   cluster.sync();   // no CTA leaves while others may still read its shared memory
 }
 
+// The same cyclic one-sided Jacobi on the rows of M in FP32 (the FFMA pipe
+// issues 64x faster than FP64 here): W = s M^T with s an exact power of two
+// that brings ||M||_F near 1 (so FP32 range limits do not bite), Q = I; the
+// sweeps stop at relative tolerance p 2^-24 or after max_sweeps.  The FP32
+// rotations accumulate in Q, written as FP64 to Qg (p x p, ld p); the FP64
+// sweeps then start from W0 = M^T Q after Q is made orthonormal in FP64.
+template <int NU>
+__global__ void __launch_bounds__(JC_NT)
+jacobi32_cluster_kernel(int p, const double* __restrict__ M, int64_t ldm, double* __restrict__ Qg,
+                        int max_sweeps) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ float jsm32[];
+  const int rank = static_cast<int>(cluster.block_rank());
+  const int cs = static_cast<int>(cluster.num_blocks());
+  const int pp = p + (p & 1);
+  const int slots = (pp + cs - 1) / cs;
+  float* Wl = jsm32;
+  float* Ql = jsm32 + static_cast<size_t>(slots) * p;
+  float* Nl = Ql + static_cast<size_t>(slots) * p;
+  __shared__ double s_part[JC_CLUSTER];
+  __shared__ double s_scale;
+  __shared__ int s_flag[2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  // ||M||_F^2 in FP64 over this CTA's rows of M, then the common scale.
+  if (warp == 0) {
+    double f = 0.0;
+    for (int sl = 0; sl < slots; ++sl) {
+      const int c = sl * cs + rank;
+      if (c >= p) continue;
+      for (int t = lane; t < p; t += 32) {
+        const double v = M[c + static_cast<int64_t>(t) * ldm];
+        f = fma(v, v, f);
+      }
+    }
+    f = warp_sum(f);
+    if (lane == 0) s_part[rank] = f;
+  }
+  if (tid < 2) s_flag[tid] = 0;
+  cluster.sync();
+  if (tid == 0) {
+    double f = 0.0;
+    for (int q = 0; q < cs; ++q) f += *cluster.map_shared_rank(&s_part[q], q);
+    int e = 0;
+    if (f > 0.0) frexp(sqrt(f), &e);
+    s_scale = ldexp(1.0, -e);
+  }
+  __syncthreads();
+  const double scale = s_scale;
+  for (int sl = 0; sl < slots; ++sl) {
+    const int c = sl * cs + rank;
+    for (int t = tid; t < p; t += JC_NT) {
+      Wl[sl * p + t] = (c < p) ? static_cast<float>(M[c + static_cast<int64_t>(t) * ldm] * scale) : 0.f;
+      Ql[sl * p + t] = (c < p && t == c) ? 1.f : 0.f;
+    }
+  }
+  __syncthreads();
+  // scaled ||W||_F^2 in FP32 terms (about 1), thresholds as in the FP64 sweeps
+  float fro = 0.f;
+  {
+    double f = 0.0;
+    for (int q = 0; q < cs; ++q) f += *cluster.map_shared_rank(&s_part[q], q);
+    fro = static_cast<float>(f * scale * scale);
+  }
+  const float pu = static_cast<float>(p) * 0x1p-24f;
+  const float thr2 = pu * pu * fro;
+  const float tol2 = pu * pu;
+  const int npairs = pp / 2;
+
+  bool converged = false;
+  for (int sw = 0; sw < max_sweeps && !converged; ++sw) {
+    for (int sl = warp; sl < slots; sl += JC_WARPS) {
+      float f = 0.f;
+      for (int t = lane; t < p; t += 32) f = fmaf(Wl[sl * p + t], Wl[sl * p + t], f);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+      if (lane == 0) Nl[sl] = f;
+    }
+    if (tid == 0) s_flag[sw & 1] = 0;
+    cluster.sync();
+    for (int r = 0; r < pp - 1; ++r) {
+      for (int k = rank * JC_WARPS + warp; k < npairs; k += cs * JC_WARPS) {
+        int i, j;
+        rr_pair(pp, r, k, &i, &j);
+        if (j >= p) continue;
+        const int oi = i % cs, oj = j % cs, si = i / cs, sj = j / cs;
+        float* wi = cluster.map_shared_rank(Wl + si * p, oi);
+        float* wj = cluster.map_shared_rank(Wl + sj * p, oj);
+        float* ni = cluster.map_shared_rank(Nl + si, oi);
+        float* nj = cluster.map_shared_rank(Nl + sj, oj);
+        float x[NU], y[NU];
+        float g = 0.f;
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+          const int t = lane + 32 * u;
+          x[u] = (t < p) ? wi[t] : 0.f;
+          y[u] = (t < p) ? wj[t] : 0.f;
+          g = fmaf(x[u], y[u], g);
+        }
+        const float a = *ni, b = *nj;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+        if (g == 0.f || a <= thr2 || b <= thr2 || !(g * g > tol2 * a * b)) continue;
+        const float zf = (b - a) / (2.0f * g);
+        const float tf = (fabsf(zf) > 0x1p60f) ? 0.5f / zf
+                                                : copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)));
+        const float c = rsqrtf(fmaf(tf, tf, 1.0f));
+        const float sn = c * tf;
+        float* qi = cluster.map_shared_rank(Ql + si * p, oi);
+        float* qj = cluster.map_shared_rank(Ql + sj * p, oj);
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+          const int t = lane + 32 * u;
+          if (t < p) {
+            wi[t] = fmaf(c, x[u], -sn * y[u]);
+            wj[t] = fmaf(sn, x[u], c * y[u]);
+            const float q1 = qi[t], q2 = qj[t];
+            qi[t] = fmaf(c, q1, -sn * q2);
+            qj[t] = fmaf(sn, q1, c * q2);
+          }
+        }
+        if (lane == 0) {
+          const float cc = c * c, ss = sn * sn, csg = 2.0f * c * sn * g;
+          *ni = fmaf(cc, a, fmaf(ss, b, -csg));
+          *nj = fmaf(ss, a, fmaf(cc, b, csg));
+          s_flag[sw & 1] = 1;
+        }
+      }
+      cluster.sync();
+    }
+    int any = 0;
+    for (int q = 0; q < cs; ++q) any |= *cluster.map_shared_rank(&s_flag[sw & 1], q);
+    converged = (any == 0);
+  }
+  for (int sl = 0; sl < slots; ++sl) {
+    const int c = sl * cs + rank;
+    if (c >= p) continue;
+    for (int t = tid; t < p; t += JC_NT) Qg[t + static_cast<int64_t>(c) * p] = static_cast<double>(Ql[sl * p + t]);
+  }
+  cluster.sync();
+}
+
+// F = 1.5 I - 0.5 E in place: one Newton-Schulz step Q <- Q F with E = Q^T Q
+// pulls Q to the nearest orthonormal matrix (error squared per step).
+__global__ void polar_step_kernel(int p, double* E) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= static_cast<int64_t>(p) * p) return;
+  const int i = static_cast<int>(t % p), j = static_cast<int>(t / p);
+  E[t] = (i == j ? 1.5 : 0.0) - 0.5 * E[t];
+}
+
 // Sort, normalise, complete, sign-fix; one CTA of 256 threads.
 __global__ void __launch_bounds__(256)
 jacobi_finish_kernel(int p, const double* __restrict__ W, const double* __restrict__ V,
@@ -318,38 +479,70 @@ jacobi_finish_kernel(int p, const double* __restrict__ W, const double* __restri
   }
 }
 
-int64_t jacobi_work_elems(int p) {
-  // W, Q (p x p each), sig (p), perm (p ints)
-  return 2ll * p * p + 2ll * p + 64;
-}
-
 namespace {
 
-template <int NU>
-cudaError_t launch_cluster(cudaStream_t s, int csize, size_t smem, int p, const double* M, int64_t ldm,
-                           double* W, double* V, int max_sweeps, double tol, int* err) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(jacobi_cluster_kernel<NU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(kJcSmemMax));
-    if (e == cudaSuccess && csize > 8)
-      e = cudaFuncSetAttribute(jacobi_cluster_kernel<NU>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+cudaLaunchConfig_t cluster_cfg(cudaStream_t s, int csize, size_t smem, cudaLaunchAttribute* at) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(csize);
   cfg.blockDim = dim3(JC_NT);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = csize;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel<NU>, p, M, ldm, W, V, max_sweeps, tol, err);
+  return cfg;
+}
+
+template <typename K>
+cudaError_t prepare(K kern, int csize, size_t smem_max) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_max));
+  if (e == cudaSuccess && csize > 8) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+template <int NU>
+cudaError_t launch64(cudaStream_t s, int csize, int p, const double* M, int64_t ldm, const double* W0,
+                     const double* Q0, double* W, double* V, int max_sweeps, double tol, int* err) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = prepare(jacobi_cluster_kernel<NU>, csize, kJcSmemMax);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  cudaLaunchAttribute at[1];
+  cudaLaunchConfig_t cfg = cluster_cfg(s, csize, jc_smem(p, csize), at);
+  return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel<NU>, p, M, ldm, W0, Q0, W, V, max_sweeps, tol, err);
+}
+
+template <int NU>
+cudaError_t launch32(cudaStream_t s, int csize, int p, const double* M, int64_t ldm, double* Qg, int sweeps) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = prepare(jacobi32_cluster_kernel<NU>, csize, jc_smem32(JC_MAXP, 8));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  cudaLaunchAttribute at[1];
+  cudaLaunchConfig_t cfg = cluster_cfg(s, csize, jc_smem32(p, csize), at);
+  return cudaLaunchKernelEx(&cfg, jacobi32_cluster_kernel<NU>, p, M, ldm, Qg, sweeps);
+}
+
+cudaError_t run64(cudaStream_t s, int csize, int p, const double* M, int64_t ldm, const double* W0, const double* Q0,
+                  double* W, double* V, int max_sweeps, double tol, int* err) {
+  if (p <= 32) return launch64<1>(s, csize, p, M, ldm, W0, Q0, W, V, max_sweeps, tol, err);
+  if (p <= 64) return launch64<2>(s, csize, p, M, ldm, W0, Q0, W, V, max_sweeps, tol, err);
+  if (p <= 128) return launch64<4>(s, csize, p, M, ldm, W0, Q0, W, V, max_sweeps, tol, err);
+  return launch64<8>(s, csize, p, M, ldm, W0, Q0, W, V, max_sweeps, tol, err);
+}
+
+cudaError_t run32(cudaStream_t s, int csize, int p, const double* M, int64_t ldm, double* Qg, int sweeps) {
+  if (p <= 32) return launch32<1>(s, csize, p, M, ldm, Qg, sweeps);
+  if (p <= 64) return launch32<2>(s, csize, p, M, ldm, Qg, sweeps);
+  if (p <= 128) return launch32<4>(s, csize, p, M, ldm, Qg, sweeps);
+  return launch32<8>(s, csize, p, M, ldm, Qg, sweeps);
 }
 
 // Largest cluster size (16 with the non-portable opt-in, else 8) that can be scheduled.
@@ -357,21 +550,9 @@ int cluster_size() {
   static int csize = 0;
   if (csize) return csize;
   csize = 8;
-  if (cudaFuncSetAttribute(jacobi_cluster_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(kJcSmemMax)) == cudaSuccess &&
-      cudaFuncSetAttribute(jacobi_cluster_kernel<8>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-          cudaSuccess) {
-    cudaLaunchConfig_t q = {};
-    q.gridDim = dim3(JC_CLUSTER);
-    q.blockDim = dim3(JC_NT);
-    q.dynamicSmemBytes = jc_smem(JC_MAXP, JC_CLUSTER);
+  if (prepare(jacobi_cluster_kernel<8>, JC_CLUSTER, kJcSmemMax) == cudaSuccess) {
     cudaLaunchAttribute qa[1];
-    qa[0].id = cudaLaunchAttributeClusterDimension;
-    qa[0].val.clusterDim.x = JC_CLUSTER;
-    qa[0].val.clusterDim.y = 1;
-    qa[0].val.clusterDim.z = 1;
-    q.attrs = qa;
-    q.numAttrs = 1;
+    cudaLaunchConfig_t q = cluster_cfg(nullptr, JC_CLUSTER, jc_smem(JC_MAXP, JC_CLUSTER), qa);
     int nclusters = 0;
     if (cudaOccupancyMaxActiveClusters(&nclusters, jacobi_cluster_kernel<8>, &q) == cudaSuccess && nclusters > 0)
       csize = JC_CLUSTER;
@@ -380,24 +561,49 @@ int cluster_size() {
   return csize;
 }
 
+constexpr int kPreconditionMinP = 32;   // below this the FP64 sweeps alone are cheaper
+constexpr int kFp32Sweeps = 20;
+
 }  // namespace
+
+int64_t jacobi_work_elems(int p) { return jacobi_work_elems_for(p); }
 
 cudaError_t jacobi_svd(cudaStream_t s, int p, const double* M, int64_t ldm, double* Us, double* d,
                        double* Vs, int max_sweeps, double* work, unsigned* bar) {
   if (p < 1) return cudaSuccess;
   if (p > JC_MAXP) return cudaErrorInvalidValue;
-  double* W = work;
-  double* V = W + static_cast<int64_t>(p) * p;
+  const int64_t pe = static_cast<int64_t>(p) * p;
+  double* W = work;        // W iterate
+  double* V = W + pe;      // accumulated rotations Q
+  double* X1 = V + pe;     // Q^T Q, then the Newton-Schulz factor
+  double* X2 = X1 + pe;    // intermediate Q
+  double* gw = X2 + pe;    // split-K partials of the p x p products (4 p^2)
+  const int64_t gwe = 4 * pe;
   int* err = reinterpret_cast<int*>(bar + 2);
   const int csize = cluster_size();
-  const size_t smem = jc_smem(p, csize);
   const double tol = static_cast<double>(p) * 0x1p-53;
   const ProfToken tok = prof_begin(s, kProfJacobi);
   cudaError_t e;
-  if (p <= 32) e = launch_cluster<1>(s, csize, smem, p, M, ldm, W, V, max_sweeps, tol, err);
-  else if (p <= 64) e = launch_cluster<2>(s, csize, smem, p, M, ldm, W, V, max_sweeps, tol, err);
-  else if (p <= 128) e = launch_cluster<4>(s, csize, smem, p, M, ldm, W, V, max_sweeps, tol, err);
-  else e = launch_cluster<8>(s, csize, smem, p, M, ldm, W, V, max_sweeps, tol, err);
+  if (p >= kPreconditionMinP) {
+    // FP32 sweeps, two FP64 Newton-Schulz steps on Q, W0 = M^T Q, FP64 sweeps
+    e = run32(s, csize, p, M, ldm, V, kFp32Sweeps);
+    note_launch();
+    for (int it = 0; it < 2 && e == cudaSuccess; ++it) {
+      double* Qin = (it == 0) ? V : X2;
+      double* Qout = (it == 0) ? X2 : V;
+      e = gemm_f64(s, true, false, p, p, p, 1.0, Qin, p, Qin, p, 0.0, X1, p, gw, gwe);
+      if (e == cudaSuccess) {
+        polar_step_kernel<<<static_cast<unsigned>((pe + 255) / 256), 256, 0, s>>>(p, X1);
+        note_launch();
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = gemm_f64(s, false, false, p, p, p, 1.0, Qin, p, X1, p, 0.0, Qout, p, gw, gwe);
+    }
+    if (e == cudaSuccess) e = gemm_f64(s, true, false, p, p, p, 1.0, M, ldm, V, p, 0.0, W, p, gw, gwe);
+    if (e == cudaSuccess) e = run64(s, csize, p, M, ldm, W, V, W, V, max_sweeps, tol, err);
+  } else {
+    e = run64(s, csize, p, M, ldm, nullptr, nullptr, W, V, max_sweeps, tol, err);
+  }
   note_launch();
   if (e != cudaSuccess) return e;
   jacobi_finish_kernel<<<1, 256, 0, s>>>(p, W, V, Us, d, Vs);

@@ -11,7 +11,7 @@
 // takes its scratch from one fixed array in device global memory that the
 // library declares at file scope; the caller still passes M, Us, d and Vs.
 //
-// Limits and sharing: p <= kNoAllocMaxP.  The array (about 1 MB) exists on
+// Limits and sharing: p <= kNoAllocMaxP.  The array (about 4 MB) exists on
 // every GPU that loads the library until the process exits.  All calls on a
 // device share it and it keeps the last call's contents, so two calls whose
 // work overlaps on the GPU (different streams, or different host threads)
@@ -28,7 +28,7 @@ namespace {
 constexpr int kNoAllocMaxP = 256;
 constexpr int kMaxDevices = 64;
 // jacobi_work_elems(256) doubles, then 8 doubles of barrier/error words
-constexpr int64_t kNoAllocElems = 2ll * kNoAllocMaxP * kNoAllocMaxP + 2ll * kNoAllocMaxP + 64 + 8;
+constexpr int64_t kNoAllocElems = jacobi_work_elems_for(kNoAllocMaxP) + 8;
 
 static __device__ __align__(256) double g_svd_scratch[kNoAllocElems];
 
