@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-verify", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--forms", default="fp64,mixed", help="fp64, mixed or both (the FP64 form carries the line)")
     return ap.parse_args()
 
 
@@ -289,6 +290,13 @@ def run_own(args):
                                    Vst.data_ptr(), n, ctypes.byref(kr), ctypes.byref(opts))
         native.check(st, "randutv_factor_ex")
 
+    if "fp64" not in args.forms:   # profiling aid: the mixed form alone, no FP64 timing
+        step()
+        torch.cuda.synchronize()
+        m = run_mixed(args, lib, native, A, Tst, n, b, q, stream, dist)
+        if rank == 0:
+            print(json.dumps({"forms": "mixed", "mixed": m}), flush=True)
+        return 0
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -329,7 +337,8 @@ def run_own(args):
         verify["tril_max"] = float(torch.tril(T, -1).abs().max())
         del eye
 
-    mixed = None if args.no_mixed else run_mixed(args, lib, native, A, Tst, n, b, q, stream, dist)
+    mixed = None if (args.no_mixed or "mixed" not in args.forms) else run_mixed(args, lib, native, A, Tst, n, b, q,
+                                                                              stream, dist)
     if mixed is not None:
         mixed["speedup_vs_fp64"] = ms / mixed["ms_per_step"]
 

@@ -55,9 +55,14 @@ typedef struct randutv_opts {
                            min(m,n)) stores its (m - b(i-1)) x b matrix
                            column-major (ld = m - b(i-1)) right after step
                            i-1's.  Used instead of the Philox stream.          */
+  int overlap;          /* 1: accumulate U and V on a second, lower-priority
+                           stream, overlapped with the serial panel QR and
+                           small SVD of the T chain (same results); 0: one
+                           stream                                              */
 } randutv_opts;
 
-/* Defaults: FP64, form_uv = 1, max_sweeps = 30, p = 0, seed = 998, no g_inject. */
+/* Defaults: FP64, form_uv = 1, max_sweeps = 30, p = 0, seed = 998, no g_inject,
+   overlap = 1. */
 void randutv_opts_default(randutv_opts* opts);
 
 /* Stream used by all later calls in this process (a cudaStream_t; NULL =

@@ -40,8 +40,9 @@ def _bind_stream():
     native.lib().randutv_set_stream(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
-def _opts(seed, form_uv, max_sweeps, g_inject):
+def _opts(seed, form_uv, max_sweeps, g_inject, overlap=True):
     o = native.default_opts()
+    o.overlap = 1 if overlap else 0
     o.seed = int(seed)
     o.form_uv = 1 if form_uv else 0
     o.max_sweeps = int(max_sweeps)
@@ -49,7 +50,7 @@ def _opts(seed, form_uv, max_sweeps, g_inject):
     return o
 
 
-def factor(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sweeps=30):
+def factor(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sweeps=30, overlap=True):
     """A = U T V^T by randUTV (Fig. 4) on A's CUDA device, FP64.
 
     A: (m, n) float64 CUDA tensor.  g_inject: optional 1-D float64 CUDA tensor
@@ -67,7 +68,7 @@ def factor(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sw
         if g_inject is not None:
             if g_inject.dtype != torch.float64 or not g_inject.is_cuda or not g_inject.is_contiguous():
                 raise TypeError("g_inject must be a contiguous float64 CUDA tensor")
-        o = _opts(seed, form_uv, max_sweeps, g_inject)
+        o = _opts(seed, form_uv, max_sweeps, g_inject, overlap)
         kr = ctypes.c_int64(0)
         _bind_stream()
         st = native.lib().randutv_factor_ex(
@@ -78,7 +79,7 @@ def factor(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sw
     return UTV(Ust.t() if form_uv else None, Tst.t(), Vst.t() if form_uv else None, kr.value)
 
 
-def factor_mixed(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sweeps=30):
+def factor_mixed(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sweeps=30, overlap=True):
     """Mixed-precision randUTV: A is an (m, n) float32 CUDA tensor; U, T, V
     come back float32.  Panel QRs and small SVDs run in FP64 inside."""
     torch = _torch()
@@ -92,7 +93,7 @@ def factor_mixed(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, 
         if g_inject is not None:
             if g_inject.dtype != torch.float64 or not g_inject.is_cuda or not g_inject.is_contiguous():
                 raise TypeError("g_inject must be a contiguous float64 CUDA tensor")
-        o = _opts(seed, form_uv, max_sweeps, g_inject)
+        o = _opts(seed, form_uv, max_sweeps, g_inject, overlap)
         kr = ctypes.c_int64(0)
         _bind_stream()
         st = native.lib().randutv_factor_mixed(

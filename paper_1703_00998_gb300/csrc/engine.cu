@@ -246,6 +246,7 @@ void randutv_opts_default(randutv_opts* o) {
   o->p = 0;
   o->seed = 998;
   o->g_inject = nullptr;
+  o->overlap = 1;
 }
 
 int randutv_set_stream(void* s) {

@@ -132,10 +132,16 @@ cudaError_t sumsq32(cudaStream_t s, int64_t m, int64_t n, const float* X, int64_
   return cudaGetLastError();
 }
 
+// Depth of the ring of per-step reflectors and small factors that the U/V
+// stream reads while the T chain goes on with the next steps.
+constexpr int kRing = 3;
+
 // Workspace of the mixed form.
 struct MWork {
   // FP32
   float *G, *Y, *Z, *Vv, *Vu, *S, *Us, *Vs, *W1, *W2, *tmp, *gws;
+  float *Vvr[kRing], *Vur[kRing], *Svr[kRing], *Sur[kRing], *Usr[kRing], *Vsr[kRing];
+  float *W1u, *W2u, *tmpu, *gwsu;
   // FP64
   double *G64, *Y64, *P64, *Vv64, *Vu64, *tau, *R, *Rt, *gram, *S64, *Us64, *Vs64, *d, *part, *jws, *gws64,
       *red, *scal;
@@ -170,7 +176,14 @@ cudaError_t mwork_alloc(cudaStream_t s, int64_t m, int64_t n, int b, MWork* w) {
   struct I64 { double** p; int64_t n; };
   I32 f[] = {{&w->G, m * b}, {&w->Y, n * b}, {&w->Z, m * b}, {&w->Vv, mx * b}, {&w->Vu, mx * b}, {&w->S, bb},
              {&w->Us, bb}, {&w->Vs, bb}, {&w->W1, mx * b}, {&w->W2, mx * b}, {&w->tmp, mx * b},
-             {&w->gws, w->gws_elems}};
+             {&w->gws, w->gws_elems},
+             {&w->Vvr[0], mx * b}, {&w->Vvr[1], mx * b}, {&w->Vvr[2], mx * b},
+             {&w->Vur[0], mx * b}, {&w->Vur[1], mx * b}, {&w->Vur[2], mx * b},
+             {&w->Svr[0], bb}, {&w->Svr[1], bb}, {&w->Svr[2], bb}, {&w->Sur[0], bb}, {&w->Sur[1], bb},
+             {&w->Sur[2], bb}, {&w->Usr[0], bb}, {&w->Usr[1], bb}, {&w->Usr[2], bb}, {&w->Vsr[0], bb},
+             {&w->Vsr[1], bb}, {&w->Vsr[2], bb},
+             {&w->W1u, mx * b}, {&w->W2u, mx * b}, {&w->tmpu, mx * b}, {&w->gwsu, w->gws_elems}};
+  static_assert(kRing == 3, "ring buffers listed above");
   I64 d[] = {{&w->G64, m * b}, {&w->Y64, mx * b}, {&w->P64, mx * b}, {&w->Vv64, mx * b}, {&w->Vu64, mx * b},
              {&w->tau, b}, {&w->R, bb}, {&w->Rt, bb}, {&w->gram, bb}, {&w->S64, bb}, {&w->Us64, bb},
              {&w->Vs64, bb}, {&w->d, b}, {&w->part, panel_qr_part_elems(mx, b)}, {&w->jws, jacobi_work_elems(b)},
@@ -282,6 +295,7 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
   const bool uv = opts.form_uv != 0;
   cudaStream_t s = current_stream();
   MWork w{};
+  Lanes L;
   int st = RANDUTV_OK;
   double h_norm2 = 0.0, normA = 0.0;
   int64_t g_off = 0;
@@ -295,102 +309,132 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
       return e == cudaErrorMemoryAllocation ? RANDUTV_ENOMEM : RANDUTV_ECUDA;
     }
   }
-  RUTV_MCK(copy32(s, m, n, A, lda, T, ldt));
-  if (uv) {
-    f32_identity_kernel<<<blocks_for(m * m), 256, 0, s>>>(m, U, ldu);
-    f32_identity_kernel<<<blocks_for(n * n), 256, 0, s>>>(n, V, ldv);
-    note_launch(2);
-    RUTV_MCK(cudaGetLastError());
-  }
-  RUTV_MCK(sumsq32(s, m, n, T, ldt, w.red, w.scal));
-  RUTV_MCK(cudaMemcpyAsync(&h_norm2, w.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
-  RUTV_MCK(cudaStreamSynchronize(s));
-  if (!std::isfinite(h_norm2)) { st = RANDUTV_ENAN; goto done; }
-  normA = std::sqrt(h_norm2);
-
-  for (int64_t i = 1; i <= nsteps; ++i) {
-    const int64_t r0 = b * (i - 1);
-    const int64_t r1 = std::min<int64_t>(r0 + b, m), c1 = std::min<int64_t>(r0 + b, n);
-    const int64_t kr = m - r0, kc = n - r0;
-    float* X = T + r0 + r0 * ldt;
-    if (tol > 0.0) {
-      double t2 = 0.0;
-      RUTV_MCK(sumsq32(s, kr, kc, X, ldt, w.red, w.scal));
-      RUTV_MCK(cudaMemcpyAsync(&t2, w.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
-      RUTV_MCK(cudaStreamSynchronize(s));
-      if (!std::isfinite(t2)) { st = RANDUTV_ENAN; goto done; }
-      if (std::sqrt(t2) <= tol * normA) { *k_reached = r0; break; }
-    }
-    if (r1 < m && c1 < n) {
-      // sketch on the FP32 pipe; G from the same Philox stream (or the injected one) rounded to FP32
-      if (opts.g_inject) {
-        RUTV_MCK(down(s, kr, b, opts.g_inject + g_off, kr, w.G, kr));
-      } else {
-        RUTV_MCK(launch_gaussian(s, opts.seed, i, kr, b, w.G64, kr));
-        RUTV_MCK(down(s, kr, b, w.G64, kr, w.G, kr));
-      }
-      g_off += kr * b;
-      RUTV_MCK(gemm_f32(s, true, false, kc, b, kr, 1.f, X, ldt, w.G, kr, 0.f, w.Y, kc, w.gws, w.gws_elems));
-      for (int j = 0; j < q; ++j) {
-        RUTV_MCK(gemm_f32(s, false, false, kr, b, kc, 1.f, X, ldt, w.Y, kc, 0.f, w.Z, kr, w.gws, w.gws_elems));
-        RUTV_MCK(gemm_f32(s, true, false, kc, b, kr, 1.f, X, ldt, w.Z, kr, 0.f, w.Y, kc, w.gws, w.gws_elems));
-      }
-      // QR(Y) in FP64
-      RUTV_MCK(up(s, kc, b, w.Y, kc, w.Y64, kc));
-      RUTV_MCK(panel_wy(s, kc, b, w.Y64, w.tau, w.Vv64, w.Rt, w.gram, w.S64, w.Vv, w.S, w, slot_of(w.flags, 0)));
-      RUTV_MCK(wy_right32(s, m, kc, T + r0 * ldt, ldt, w.Vv, w.S, b, w.W1, w.W2, w.gws, w.gws_elems));
-      if (uv) RUTV_MCK(wy_right32(s, n, kc, V + r0 * ldv, ldv, w.Vv, w.S, b, w.W1, w.W2, w.gws, w.gws_elems));
-      // QR of the panel in FP64
-      RUTV_MCK(up(s, kr, b, X, ldt, w.P64, kr));
-      RUTV_MCK(panel_wy(s, kr, b, w.P64, w.tau, w.Vu64, w.R, w.gram, w.S64, w.Vu, w.S, w, slot_of(w.flags, 1)));
-      if (uv) RUTV_MCK(wy_right32(s, m, kr, U + r0 * ldu, ldu, w.Vu, w.S, b, w.W1, w.W2, w.gws, w.gws_elems));
-      RUTV_MCK(wy_left_t32(s, kr, kc - b, T + r0 + c1 * ldt, ldt, w.Vu, w.S, b, w.W1, w.W2, w.gws, w.gws_elems));
-      RUTV_MCK(fill32(s, kr, b, X, ldt));
-      // small SVD in FP64
-      RUTV_MCK(jacobi_svd(s, b, w.R, b, w.Us64, w.d, w.Vs64, opts.max_sweeps, w.jws, slot_of(w.flags, 2)));
-      f32_set_diag_kernel<<<(b + 127) / 128, 128, 0, s>>>(b, w.d, X, ldt);
-      note_launch();
+  RUTV_MCK(L.open(s, opts.overlap != 0 && uv));
+  {
+    cudaStream_t sT = L.t, sU = L.uv;
+    RUTV_MCK(copy32(sT, m, n, A, lda, T, ldt));
+    if (uv) {
+      f32_identity_kernel<<<blocks_for(m * m), 256, 0, sU>>>(m, U, ldu);
+      f32_identity_kernel<<<blocks_for(n * n), 256, 0, sU>>>(n, V, ldv);
+      note_launch(2);
       RUTV_MCK(cudaGetLastError());
-      RUTV_MCK(down(s, b, b, w.Us64, b, w.Us, b));
-      RUTV_MCK(down(s, b, b, w.Vs64, b, w.Vs, b));
-      RUTV_MCK(rot_left_t32(s, b, kc - b, T + r0 + c1 * ldt, ldt, w.Us, w.tmp, w.gws, w.gws_elems));
-      RUTV_MCK(rot_right32(s, r0, b, T + r0 * ldt, ldt, w.Vs, w.tmp, w.gws, w.gws_elems));
-      if (uv) {
-        RUTV_MCK(rot_right32(s, m, b, U + r0 * ldu, ldu, w.Us, w.tmp, w.gws, w.gws_elems));
-        RUTV_MCK(rot_right32(s, n, b, V + r0 * ldv, ldv, w.Vs, w.tmp, w.gws, w.gws_elems));
+    }
+    RUTV_MCK(sumsq32(sT, m, n, T, ldt, w.red, w.scal));
+    RUTV_MCK(cudaMemcpyAsync(&h_norm2, w.scal, sizeof(double), cudaMemcpyDeviceToHost, sT));
+    RUTV_MCK(cudaStreamSynchronize(sT));
+    if (!std::isfinite(h_norm2)) { st = RANDUTV_ENAN; goto done; }
+    normA = std::sqrt(h_norm2);
+
+    for (int64_t i = 1; i <= nsteps; ++i) {
+      const int64_t r0 = b * (i - 1);
+      const int64_t r1 = std::min<int64_t>(r0 + b, m), c1 = std::min<int64_t>(r0 + b, n);
+      const int64_t kr = m - r0, kc = n - r0;
+      const int sl = static_cast<int>((i - 1) % kRing);
+      float* X = T + r0 + r0 * ldt;
+      if (tol > 0.0) {
+        double t2 = 0.0;
+        RUTV_MCK(sumsq32(sT, kr, kc, X, ldt, w.red, w.scal));
+        RUTV_MCK(cudaMemcpyAsync(&t2, w.scal, sizeof(double), cudaMemcpyDeviceToHost, sT));
+        RUTV_MCK(cudaStreamSynchronize(sT));
+        if (!std::isfinite(t2)) { st = RANDUTV_ENAN; goto done; }
+        if (std::sqrt(t2) <= tol * normA) { *k_reached = r0; break; }
       }
-    } else {
-      // last block: QR first (tall or square) or QR of the rows (wide), then the FP64 SVD
-      int p;
-      if (kr >= kc) {
-        p = static_cast<int>(kc);
-        RUTV_MCK(up(s, kr, kc, X, ldt, w.P64, kr));
-        RUTV_MCK(panel_wy(s, kr, p, w.P64, w.tau, w.Vu64, w.R, w.gram, w.S64, w.Vu, w.S, w, slot_of(w.flags, 1)));
-        if (uv) RUTV_MCK(wy_right32(s, m, kr, U + r0 * ldu, ldu, w.Vu, w.S, p, w.W1, w.W2, w.gws, w.gws_elems));
-      } else {
-        p = static_cast<int>(kr);
-        f32_transpose_to_f64_kernel<<<blocks_for(kr * kc), 256, 0, s>>>(kr, kc, X, ldt, w.P64, kc);
+      // the ring slot of this step is free once the U/V stream finished step i - kRing
+      if (i > kRing) RUTV_MCK(cudaStreamWaitEvent(sT, L.done[sl], 0));
+      float *Vv = w.Vvr[sl], *Vu = w.Vur[sl], *Sv = w.Svr[sl], *Su = w.Sur[sl], *Us = w.Usr[sl], *Vs = w.Vsr[sl];
+      if (r1 < m && c1 < n) {
+        // sketch on the FP32 pipe; G from the same Philox stream (or the injected one) rounded to FP32
+        if (opts.g_inject) {
+          RUTV_MCK(down(sT, kr, b, opts.g_inject + g_off, kr, w.G, kr));
+        } else {
+          RUTV_MCK(launch_gaussian(sT, opts.seed, i, kr, b, w.G64, kr));
+          RUTV_MCK(down(sT, kr, b, w.G64, kr, w.G, kr));
+        }
+        g_off += kr * b;
+        RUTV_MCK(gemm_f32(sT, true, false, kc, b, kr, 1.f, X, ldt, w.G, kr, 0.f, w.Y, kc, w.gws, w.gws_elems));
+        for (int j = 0; j < q; ++j) {
+          RUTV_MCK(gemm_f32(sT, false, false, kr, b, kc, 1.f, X, ldt, w.Y, kc, 0.f, w.Z, kr, w.gws, w.gws_elems));
+          RUTV_MCK(gemm_f32(sT, true, false, kc, b, kr, 1.f, X, ldt, w.Z, kr, 0.f, w.Y, kc, w.gws, w.gws_elems));
+        }
+        // QR(Y) in FP64
+        RUTV_MCK(up(sT, kc, b, w.Y, kc, w.Y64, kc));
+        RUTV_MCK(panel_wy(sT, kc, b, w.Y64, w.tau, w.Vv64, w.Rt, w.gram, w.S64, Vv, Sv, w, slot_of(w.flags, 0)));
+        RUTV_MCK(cudaEventRecord(L.v[sl], sT));
+        RUTV_MCK(wy_right32(sT, m, kc, T + r0 * ldt, ldt, Vv, Sv, b, w.W1, w.W2, w.gws, w.gws_elems));
+        if (uv) {
+          RUTV_MCK(cudaStreamWaitEvent(sU, L.v[sl], 0));
+          RUTV_MCK(wy_right32(sU, n, kc, V + r0 * ldv, ldv, Vv, Sv, b, w.W1u, w.W2u, w.gwsu, w.gws_elems));
+        }
+        // QR of the panel in FP64
+        RUTV_MCK(up(sT, kr, b, X, ldt, w.P64, kr));
+        RUTV_MCK(panel_wy(sT, kr, b, w.P64, w.tau, w.Vu64, w.R, w.gram, w.S64, Vu, Su, w, slot_of(w.flags, 1)));
+        if (uv) {
+          RUTV_MCK(cudaEventRecord(L.u[sl], sT));
+          RUTV_MCK(cudaStreamWaitEvent(sU, L.u[sl], 0));
+          RUTV_MCK(wy_right32(sU, m, kr, U + r0 * ldu, ldu, Vu, Su, b, w.W1u, w.W2u, w.gwsu, w.gws_elems));
+        }
+        RUTV_MCK(wy_left_t32(sT, kr, kc - b, T + r0 + c1 * ldt, ldt, Vu, Su, b, w.W1, w.W2, w.gws, w.gws_elems));
+        RUTV_MCK(fill32(sT, kr, b, X, ldt));
+        // small SVD in FP64
+        RUTV_MCK(jacobi_svd(sT, b, w.R, b, w.Us64, w.d, w.Vs64, opts.max_sweeps, w.jws, slot_of(w.flags, 2)));
+        f32_set_diag_kernel<<<(b + 127) / 128, 128, 0, sT>>>(b, w.d, X, ldt);
         note_launch();
         RUTV_MCK(cudaGetLastError());
-        RUTV_MCK(panel_wy(s, kc, p, w.P64, w.tau, w.Vv64, w.Rt, w.gram, w.S64, w.Vv, w.S, w, slot_of(w.flags, 0)));
-        RUTV_MCK(wy_right32(s, m, kc, T + r0 * ldt, ldt, w.Vv, w.S, p, w.W1, w.W2, w.gws, w.gws_elems));
-        if (uv) RUTV_MCK(wy_right32(s, n, kc, V + r0 * ldv, ldv, w.Vv, w.S, p, w.W1, w.W2, w.gws, w.gws_elems));
-        RUTV_MCK(transpose_f64(s, p, p, w.Rt, p, w.R, p));
+        RUTV_MCK(down(sT, b, b, w.Us64, b, Us, b));
+        RUTV_MCK(down(sT, b, b, w.Vs64, b, Vs, b));
+        if (uv) {
+          RUTV_MCK(cudaEventRecord(L.s[sl], sT));
+          RUTV_MCK(cudaStreamWaitEvent(sU, L.s[sl], 0));
+          RUTV_MCK(rot_right32(sU, m, b, U + r0 * ldu, ldu, Us, w.tmpu, w.gwsu, w.gws_elems));
+          RUTV_MCK(rot_right32(sU, n, b, V + r0 * ldv, ldv, Vs, w.tmpu, w.gwsu, w.gws_elems));
+        }
+        RUTV_MCK(rot_left_t32(sT, b, kc - b, T + r0 + c1 * ldt, ldt, Us, w.tmp, w.gws, w.gws_elems));
+        RUTV_MCK(rot_right32(sT, r0, b, T + r0 * ldt, ldt, Vs, w.tmp, w.gws, w.gws_elems));
+      } else {
+        // last block: QR first (tall or square) or QR of the rows (wide), then the FP64 SVD
+        int p;
+        if (kr >= kc) {
+          p = static_cast<int>(kc);
+          RUTV_MCK(up(sT, kr, kc, X, ldt, w.P64, kr));
+          RUTV_MCK(panel_wy(sT, kr, p, w.P64, w.tau, w.Vu64, w.R, w.gram, w.S64, Vu, Su, w, slot_of(w.flags, 1)));
+          if (uv) {
+            RUTV_MCK(cudaEventRecord(L.u[sl], sT));
+            RUTV_MCK(cudaStreamWaitEvent(sU, L.u[sl], 0));
+            RUTV_MCK(wy_right32(sU, m, kr, U + r0 * ldu, ldu, Vu, Su, p, w.W1u, w.W2u, w.gwsu, w.gws_elems));
+          }
+        } else {
+          p = static_cast<int>(kr);
+          f32_transpose_to_f64_kernel<<<blocks_for(kr * kc), 256, 0, sT>>>(kr, kc, X, ldt, w.P64, kc);
+          note_launch();
+          RUTV_MCK(cudaGetLastError());
+          RUTV_MCK(panel_wy(sT, kc, p, w.P64, w.tau, w.Vv64, w.Rt, w.gram, w.S64, Vv, Sv, w, slot_of(w.flags, 0)));
+          RUTV_MCK(wy_right32(sT, m, kc, T + r0 * ldt, ldt, Vv, Sv, p, w.W1, w.W2, w.gws, w.gws_elems));
+          if (uv) {
+            RUTV_MCK(cudaEventRecord(L.v[sl], sT));
+            RUTV_MCK(cudaStreamWaitEvent(sU, L.v[sl], 0));
+            RUTV_MCK(wy_right32(sU, n, kc, V + r0 * ldv, ldv, Vv, Sv, p, w.W1u, w.W2u, w.gwsu, w.gws_elems));
+          }
+          RUTV_MCK(transpose_f64(sT, p, p, w.Rt, p, w.R, p));
+        }
+        RUTV_MCK(jacobi_svd(sT, p, w.R, p, w.Us64, w.d, w.Vs64, opts.max_sweeps, w.jws, slot_of(w.flags, 2)));
+        RUTV_MCK(fill32(sT, kr, kc, X, ldt));
+        f32_set_diag_kernel<<<(p + 127) / 128, 128, 0, sT>>>(p, w.d, X, ldt);
+        note_launch();
+        RUTV_MCK(cudaGetLastError());
+        RUTV_MCK(down(sT, p, p, w.Us64, p, Us, p));
+        RUTV_MCK(down(sT, p, p, w.Vs64, p, Vs, p));
+        if (uv) {
+          RUTV_MCK(cudaEventRecord(L.s[sl], sT));
+          RUTV_MCK(cudaStreamWaitEvent(sU, L.s[sl], 0));
+          RUTV_MCK(rot_right32(sU, m, p, U + r0 * ldu, ldu, Us, w.tmpu, w.gwsu, w.gws_elems));
+          RUTV_MCK(rot_right32(sU, n, p, V + r0 * ldv, ldv, Vs, w.tmpu, w.gwsu, w.gws_elems));
+        }
+        RUTV_MCK(rot_right32(sT, r0, p, T + r0 * ldt, ldt, Vs, w.tmp, w.gws, w.gws_elems));
       }
-      RUTV_MCK(jacobi_svd(s, p, w.R, p, w.Us64, w.d, w.Vs64, opts.max_sweeps, w.jws, slot_of(w.flags, 2)));
-      RUTV_MCK(fill32(s, kr, kc, X, ldt));
-      f32_set_diag_kernel<<<(p + 127) / 128, 128, 0, s>>>(p, w.d, X, ldt);
-      note_launch();
-      RUTV_MCK(cudaGetLastError());
-      RUTV_MCK(down(s, p, p, w.Us64, p, w.Us, p));
-      RUTV_MCK(down(s, p, p, w.Vs64, p, w.Vs, p));
-      RUTV_MCK(rot_right32(s, r0, p, T + r0 * ldt, ldt, w.Vs, w.tmp, w.gws, w.gws_elems));
-      if (uv) {
-        RUTV_MCK(rot_right32(s, m, p, U + r0 * ldu, ldu, w.Us, w.tmp, w.gws, w.gws_elems));
-        RUTV_MCK(rot_right32(s, n, p, V + r0 * ldv, ldv, w.Vs, w.tmp, w.gws, w.gws_elems));
-      }
+      if (uv) RUTV_MCK(cudaEventRecord(L.done[sl], sU));
     }
   }
+  RUTV_MCK(L.join(s));
   RUTV_MCK(cudaStreamSynchronize(s));
   {
     unsigned h[4 * kFlagSlots];
@@ -402,9 +446,11 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
   }
   if (prof_enabled()) prof_flush();
 done:
+  L.join(s);
   if (w.base) {
     cudaFreeAsync(w.base, s);
     cudaStreamSynchronize(s);
   }
+  L.close();
   return st;
 }

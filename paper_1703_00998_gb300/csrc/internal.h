@@ -79,4 +79,71 @@ cudaError_t set_identity(cudaStream_t s, int64_t n, double* X, int64_t ldx);
 cudaError_t copy_matrix(cudaStream_t s, int64_t m, int64_t n, const double* A, int64_t lda,
                         double* B, int64_t ldb);
 
+// Streams of one factorization: the T chain (high priority) and the U/V
+// accumulation (low priority), forked from and joined back into the caller's
+// stream with events.  With overlap off both are the caller's stream.  The
+// per-step events v, u, s (reflectors of Y, of the panel, small factors
+// ready) and done (U/V stream finished that step's ring slot) are indexed by
+// ring slot.
+struct Lanes {
+  static constexpr int kSlots = 3;
+  cudaStream_t t = nullptr, uv = nullptr;
+  cudaEvent_t v[kSlots] = {}, u[kSlots] = {}, s[kSlots] = {}, done[kSlots] = {};
+  cudaEvent_t fork_ev = nullptr, join_t = nullptr, join_u = nullptr;
+  bool own = false;
+
+  cudaError_t open(cudaStream_t caller, bool overlap) {
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < kSlots && e == cudaSuccess; ++i) {
+      e = cudaEventCreateWithFlags(&v[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&u[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join_t, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join_u, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    if (!overlap) {
+      t = uv = caller;
+      return cudaSuccess;
+    }
+    int lo = 0, hi = 0;
+    e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&t, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&uv, cudaStreamNonBlocking, lo);
+    if (e != cudaSuccess) return e;
+    own = true;
+    e = cudaEventRecord(fork_ev, caller);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(t, fork_ev, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(uv, fork_ev, 0);
+    return e;
+  }
+  // Make the caller's stream wait for everything queued on t and uv.
+  cudaError_t join(cudaStream_t caller) {
+    if (!own) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(join_t, t);
+    if (e == cudaSuccess) e = cudaEventRecord(join_u, uv);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, join_t, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, join_u, 0);
+    return e;
+  }
+  void close() {
+    if (own) {
+      cudaStreamDestroy(t);
+      cudaStreamDestroy(uv);
+      own = false;
+    }
+    for (int i = 0; i < kSlots; ++i) {
+      if (v[i]) cudaEventDestroy(v[i]);
+      if (u[i]) cudaEventDestroy(u[i]);
+      if (s[i]) cudaEventDestroy(s[i]);
+      if (done[i]) cudaEventDestroy(done[i]);
+    }
+    if (fork_ev) cudaEventDestroy(fork_ev);
+    if (join_t) cudaEventDestroy(join_t);
+    if (join_u) cudaEventDestroy(join_u);
+  }
+};
+
 }  // namespace rutv

@@ -31,6 +31,7 @@ class Opts(ctypes.Structure):
         ("p", ctypes.c_int),
         ("seed", ctypes.c_uint64),
         ("g_inject", ctypes.c_void_p),
+        ("overlap", ctypes.c_int),
     ]
 
 

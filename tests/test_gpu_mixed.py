@@ -77,3 +77,15 @@ def test_mixed_t_only_and_tolerance(R):
     assert out.U is None and 0 < out.k_reached < 400
     f = R.factor(dev(A.astype(np.float64)), b=32, q=1, tol=1e-4)
     assert out.k_reached == f.k_reached
+
+
+def test_mixed_overlap_off_matches(R):
+    # the U/V stream only reorders independent work: same factors either way
+    A = synth.make_matrix("exp50", 600, 600, 31).astype(np.float32)
+    g = dev(synth.gaussian_stream(SEED, 600, 600, 64))
+    a = R.factor_mixed(dev(A), b=64, q=1, g_inject=g, overlap=True)
+    c = R.factor_mixed(dev(A), b=64, q=1, g_inject=g, overlap=False)
+    for x, y in ((a.T, c.T), (a.U, c.U), (a.V, c.V)):
+        assert float((x - y).abs().max()) <= 1e-5
+    res, ou, ov = metrics(A.astype(np.float64), host(a.U), host(a.T), host(a.V))
+    assert res <= 1e-6 and ou <= 1e-6 and ov <= 1e-6
