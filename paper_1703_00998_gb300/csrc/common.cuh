@@ -15,8 +15,8 @@ constexpr int kDevErrNaN     = 4;   // non-finite value met
 
 // Barrier state for kernels launched cooperatively (all CTAs co-resident).
 struct GridBarrier {
-  unsigned* count;  // arrivals in the current generation
-  unsigned* gen;    // generation number
+  unsigned* count;  // arrivals since the launch (zeroed before it)
+  unsigned* gen;    // unused (kept for the slot layout)
   int* err;         // device error word (kDevErr* bits)
 };
 
@@ -32,26 +32,25 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Grid-wide barrier with a bounded wait.  Returns false (in every thread of
-// the CTA) when the wait ran out or another CTA reported an error; the caller
-// must then return without touching shared state.  The wait gives up after
-// ~2 s of wall time and sets kDevErrTimeout.
+// Grid-wide barrier with a bounded wait.  One monotonic arrival counter
+// (zeroed before the launch): a CTA adds 1 with acquire-release semantics and
+// waits until the counter reaches the next multiple of the grid size, so the
+// last arriver does a single atomic and nobody resets anything.  Returns false
+// (in every thread of the CTA) when the wait ran out or another CTA reported
+// an error; the caller must then return without touching shared state.  The
+// wait gives up after ~2 s of wall time and sets kDevErrTimeout.
 __device__ __forceinline__ bool grid_barrier(const GridBarrier& g, unsigned nblocks) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    unsigned my_gen = ld_acquire_u32(g.gen);
-    __threadfence();
-    unsigned prev = atomicAdd(g.count, 1u);
-    if (prev == nblocks - 1) {
-      atomicExch(g.count, 0u);
-      __threadfence();
-      atomicAdd(g.gen, 1u);
-    } else {
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(g.count) : "memory");
+    const unsigned target = (old / nblocks + 1) * nblocks;
+    if (old + 1 != target) {
       const unsigned long long t0 = global_ns();
       unsigned spins = 0;
-      while (ld_acquire_u32(g.gen) == my_gen) {
+      while (static_cast<int>(ld_acquire_u32(g.count) - target) < 0) {
         if (++spins > 1024) __nanosleep(32);
         if ((spins & 255u) == 0 && global_ns() - t0 > 2000000000ull) {
           atomicOr(g.err, kDevErrTimeout);
@@ -60,7 +59,6 @@ __device__ __forceinline__ bool grid_barrier(const GridBarrier& g, unsigned nblo
         }
       }
     }
-    __threadfence();
     if (ok && (*(volatile int*)g.err & kDevErrTimeout)) ok = 0;
     s_ok = ok;
   }

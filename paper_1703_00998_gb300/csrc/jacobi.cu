@@ -20,7 +20,8 @@
 // Order and signs: singular values descending (stable in the column index);
 // the largest-|.| entry of each Vs column positive (lowest index on ties),
 // Us flipped with it; zero singular values get Vs columns that complete an
-// orthonormal basis (Gram-Schmidt of unit vectors).
+// orthonormal basis (Gram-Schmidt of unit vectors).  The ordering, scaling
+// and signs are done in the epilogue of the FP64 sweep kernel, on all 16 SMs.
 #include <cooperative_groups.h>
 #include "common.cuh"
 #include "internal.h"
@@ -52,9 +53,8 @@ __device__ __forceinline__ void rr_pair(int pp, int r, int kpair, int* a, int* b
 // of W (= M^T, rotated) and of Q (accumulated rotations) lives in the shared
 // memory of CTA c % cs, slot c / cs, with its squared norm; a warp that
 // rotates the pair (i, j) reads and writes both columns through distributed
-// shared memory, and the rounds are separated by the cluster barrier.  On
-// exit the columns are copied to Wg and Qg (p x p, ld p) for the ordering
-// kernel.
+// shared memory, and the rounds are separated by the cluster barrier.  The
+// epilogue writes the ordered, signed Us, d and Vs.
 //
 // FP64 issues at 2 lanes/clk/SM on this GPU, so every FP64 instruction of a
 // warp costs its SM sub-partition ~64 cycles; the kernel keeps their number
@@ -67,7 +67,8 @@ __device__ __forceinline__ void rr_pair(int pp, int r, int kpair, int* a, int* b
 template <int NU>
 __global__ void __launch_bounds__(JC_NT)
 jacobi_cluster_kernel(int p, const double* __restrict__ M, int64_t ldm, const double* W0, const double* Q0,
-                      double* Wg, double* Qg, int max_sweeps, double tol, int* __restrict__ err) {
+                      double* __restrict__ Us, double* __restrict__ d, double* __restrict__ Vs, int max_sweeps,
+                      double tol, int* __restrict__ err, int* __restrict__ zero_flag) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ double jsm[];
@@ -141,13 +142,17 @@ jacobi_cluster_kernel(int p, const double* __restrict__ M, int64_t ldm, const do
         double* wj = cluster.map_shared_rank(Wl + sj * p, oj);
         double* ni = cluster.map_shared_rank(Nl + si, oi);
         double* nj = cluster.map_shared_rank(Nl + sj, oj);
-        double x[NU], y[NU];
+        double* qi = cluster.map_shared_rank(Ql + si * p, oi);
+        double* qj = cluster.map_shared_rank(Ql + sj * p, oj);
+        double x[NU], y[NU], q1[NU], q2[NU];
         double g = 0.0;
 #pragma unroll
-        for (int u = 0; u < NU; ++u) {
+        for (int u = 0; u < NU; ++u) {   // Q columns fetched with W: one round trip
           const int t = lane + 32 * u;
           x[u] = (t < p) ? wi[t] : 0.0;
           y[u] = (t < p) ? wj[t] : 0.0;
+          q1[u] = (t < p) ? qi[t] : 0.0;
+          q2[u] = (t < p) ? qj[t] : 0.0;
           g = fma(x[u], y[u], g);
         }
         const double a = *ni, b = *nj;
@@ -182,17 +187,14 @@ jacobi_cluster_kernel(int p, const double* __restrict__ M, int64_t ldm, const do
         }
         const double c = rsqrt(fma(tt, tt, 1.0));
         const double sn = c * tt;
-        double* qi = cluster.map_shared_rank(Ql + si * p, oi);
-        double* qj = cluster.map_shared_rank(Ql + sj * p, oj);
 #pragma unroll
         for (int u = 0; u < NU; ++u) {
           const int t = lane + 32 * u;
           if (t < p) {
             wi[t] = fma(c, x[u], -sn * y[u]);
             wj[t] = fma(sn, x[u], c * y[u]);
-            const double q1 = qi[t], q2 = qj[t];
-            qi[t] = fma(c, q1, -sn * q2);
-            qj[t] = fma(sn, q1, c * q2);
+            qi[t] = fma(c, q1[u], -sn * q2[u]);
+            qj[t] = fma(sn, q1[u], c * q2[u]);
           }
         }
         if (lane == 0) {
@@ -211,12 +213,59 @@ jacobi_cluster_kernel(int p, const double* __restrict__ M, int64_t ldm, const do
     converged = (any == 0);
   }
   if (!converged && rank == 0 && tid == 0) atomicOr(err, kDevErrNoConv);
-  for (int sl = 0; sl < slots; ++sl) {
+
+  // Epilogue on the 16 SMs: sigma_c = ||w_c||, the order (descending, stable
+  // in c), Vs = w / sigma, Us = Q, each pair signed so that the largest-|.|
+  // entry of its Vs column is positive (lowest index on ties).  sigma at the
+  // rounding level of the block (<= p u ||M||_F) counts as zero; those Vs
+  // columns are left zero and the completion kernel fills them.
+  cluster.sync();
+  for (int sl = warp; sl < slots; sl += JC_WARPS) {
+    const int c = sl * cs + rank;
+    double f = 0.0;
+    for (int t = lane; t < p; t += 32) f = fma(Wl[sl * p + t], Wl[sl * p + t], f);
+    f = warp_sum(f);
+    if (lane == 0) Nl[sl] = (c < p) ? sqrt(f) : -1.0;
+  }
+  cluster.sync();
+  const double cut = pu * sqrt(s_fro);
+  for (int sl = warp; sl < slots; sl += JC_WARPS) {
     const int c = sl * cs + rank;
     if (c >= p) continue;
-    for (int t = tid; t < p; t += JC_NT) {
-      Wg[t + static_cast<int64_t>(c) * p] = Wl[sl * p + t];
-      Qg[t + static_cast<int64_t>(c) * p] = Ql[sl * p + t];
+    double sc = Nl[sl];
+    if (sc <= cut) sc = 0.0;
+    int cnt = 0;
+    for (int o = lane; o < p; o += 32) {
+      double so = *cluster.map_shared_rank(Nl + o / cs, o % cs);
+      if (so <= cut) so = 0.0;
+      cnt += (so > sc) || (so == sc && o < c);
+    }
+    const int r = __reduce_add_sync(0xffffffffu, cnt);
+    const double* w = Wl + sl * p;
+    double bv = -1.0;
+    int bi = p;
+    for (int t = lane; t < p; t += 32) {
+      const double a = fabs(w[t]);
+      if (a > bv) { bv = a; bi = t; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    const double sgn = (sc > 0.0 && w[bi] < 0.0) ? -1.0 : 1.0;
+    const double inv = (sc > 0.0) ? sgn / sc : 0.0;
+    double* vs = Vs + static_cast<int64_t>(r) * p;
+    double* us = Us + static_cast<int64_t>(r) * p;
+    const double* qc = Ql + sl * p;
+    for (int t = lane; t < p; t += 32) {
+      vs[t] = w[t] * inv;
+      us[t] = sgn * qc[t];
+    }
+    if (lane == 0) {
+      d[r] = sc;
+      if (sc == 0.0) atomicOr(zero_flag, 1);
     }
   }
   cluster.sync();   // no CTA leaves while others may still read its shared memory
@@ -313,13 +362,17 @@ jacobi32_cluster_kernel(int p, const double* __restrict__ M, int64_t ldm, double
         float* wj = cluster.map_shared_rank(Wl + sj * p, oj);
         float* ni = cluster.map_shared_rank(Nl + si, oi);
         float* nj = cluster.map_shared_rank(Nl + sj, oj);
-        float x[NU], y[NU];
+        float* qi = cluster.map_shared_rank(Ql + si * p, oi);
+        float* qj = cluster.map_shared_rank(Ql + sj * p, oj);
+        float x[NU], y[NU], q1[NU], q2[NU];
         float g = 0.f;
 #pragma unroll
         for (int u = 0; u < NU; ++u) {
           const int t = lane + 32 * u;
           x[u] = (t < p) ? wi[t] : 0.f;
           y[u] = (t < p) ? wj[t] : 0.f;
+          q1[u] = (t < p) ? qi[t] : 0.f;
+          q2[u] = (t < p) ? qj[t] : 0.f;
           g = fmaf(x[u], y[u], g);
         }
         const float a = *ni, b = *nj;
@@ -331,17 +384,14 @@ jacobi32_cluster_kernel(int p, const double* __restrict__ M, int64_t ldm, double
                                                 : copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)));
         const float c = rsqrtf(fmaf(tf, tf, 1.0f));
         const float sn = c * tf;
-        float* qi = cluster.map_shared_rank(Ql + si * p, oi);
-        float* qj = cluster.map_shared_rank(Ql + sj * p, oj);
 #pragma unroll
         for (int u = 0; u < NU; ++u) {
           const int t = lane + 32 * u;
           if (t < p) {
             wi[t] = fmaf(c, x[u], -sn * y[u]);
             wj[t] = fmaf(sn, x[u], c * y[u]);
-            const float q1 = qi[t], q2 = qj[t];
-            qi[t] = fmaf(c, q1, -sn * q2);
-            qj[t] = fmaf(sn, q1, c * q2);
+            qi[t] = fmaf(c, q1[u], -sn * q2[u]);
+            qj[t] = fmaf(sn, q1[u], c * q2[u]);
           }
         }
         if (lane == 0) {
@@ -374,52 +424,24 @@ __global__ void polar_step_kernel(int p, double* E) {
   E[t] = (i == j ? 1.5 : 0.0) - 0.5 * E[t];
 }
 
-// Sort, normalise, complete, sign-fix; one CTA of 256 threads.
+// Basis completion for zero singular values (they sort last): the Vs
+// columns of those are built by two-pass Gram-Schmidt of unit vectors
+// against the others, then signed like the rest.  Runs as one CTA and
+// returns at once unless the sweep kernel flagged a zero singular value.
 __global__ void __launch_bounds__(256)
-jacobi_finish_kernel(int p, const double* __restrict__ W, const double* __restrict__ V,
-                     double* __restrict__ Us, double* __restrict__ d, double* __restrict__ Vs) {
-  __shared__ double sig[JC_MAXP];
-  __shared__ int perm[JC_MAXP];
+jacobi_complete_kernel(int p, double* __restrict__ Us, const double* __restrict__ d, double* __restrict__ Vs,
+                       int* __restrict__ zero_flag) {
   __shared__ double red[8];
-  __shared__ double s_cut;
+  __shared__ int s_need;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int c = warp; c < p; c += 8) {
-    const double* w = W + static_cast<int64_t>(c) * p;
-    double s = 0.0;
-    for (int t = lane; t < p; t += 32) s = fma(w[t], w[t], s);
-    s = warp_sum(s);
-    if (lane == 0) sig[c] = sqrt(s);
-  }
-  __syncthreads();
   if (tid == 0) {
-    // negligible columns (see the sweep kernel) count as exact zeros
-    double f = 0.0;
-    for (int c = 0; c < p; ++c) f = fma(sig[c], sig[c], f);
-    s_cut = static_cast<double>(p) * 0x1p-53 * sqrt(f);
+    s_need = *zero_flag;
+    *zero_flag = 0;
   }
   __syncthreads();
-  for (int c = tid; c < p; c += blockDim.x)
-    if (sig[c] <= s_cut) sig[c] = 0.0;
-  __syncthreads();
-  for (int c = tid; c < p; c += blockDim.x) {
-    int rank = 0;
-    const double sc = sig[c];
-    for (int o = 0; o < p; ++o) rank += (sig[o] > sc) || (sig[o] == sc && o < c);
-    perm[rank] = c;
-  }
-  __syncthreads();
-  for (int64_t e = tid; e < static_cast<int64_t>(p) * p; e += blockDim.x) {
-    const int t = static_cast<int>(e % p), r = static_cast<int>(e / p);
-    const int c = perm[r];
-    const double s = sig[c];
-    Vs[t + static_cast<int64_t>(r) * p] = (s > 0.0) ? W[t + static_cast<int64_t>(c) * p] / s : 0.0;
-    Us[t + static_cast<int64_t>(r) * p] = V[t + static_cast<int64_t>(c) * p];
-    if (t == 0) d[r] = s;
-  }
-  __syncthreads();
-  // Complete the basis for zero singular values (they sort last).
+  if (!s_need) return;
   for (int r = 0; r < p; ++r) {
-    if (sig[perm[r]] > 0.0) continue;
+    if (d[r] > 0.0) continue;
     double* u = Vs + static_cast<int64_t>(r) * p;
     for (int e = 0; e < p; ++e) {
       for (int t = tid; t < p; t += blockDim.x) u[t] = (t == e) ? 1.0 : 0.0;
@@ -454,28 +476,26 @@ jacobi_finish_kernel(int p, const double* __restrict__ W, const double* __restri
         break;
       }
     }
-  }
-  __syncthreads();
-  // Sign convention: the largest-|.| entry of each Vs column positive (lowest
-  // index on ties); one warp per column.
-  for (int r = warp; r < p; r += 8) {
-    double* v = Vs + static_cast<int64_t>(r) * p;
-    double bv = -1.0;
-    int bi = p;
-    for (int t = lane; t < p; t += 32) {
-      const double a = fabs(v[t]);
-      if (a > bv) { bv = a; bi = t; }
-    }
+    // sign rule on the completed column
+    if (warp == 0) {
+      double bv = -1.0;
+      int bi = p;
+      for (int t = lane; t < p; t += 32) {
+        const double a = fabs(u[t]);
+        if (a > bv) { bv = a; bi = t; }
+      }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+      }
+      if (u[bi] < 0.0) {
+        double* us = Us + static_cast<int64_t>(r) * p;
+        for (int t = lane; t < p; t += 32) { u[t] = -u[t]; us[t] = -us[t]; }
+      }
     }
-    if (v[bi] < 0.0) {
-      double* u = Us + static_cast<int64_t>(r) * p;
-      for (int t = lane; t < p; t += 32) { v[t] = -v[t]; u[t] = -u[t]; }
-    }
+    __syncthreads();
   }
 }
 
@@ -505,7 +525,8 @@ cudaError_t prepare(K kern, int csize, size_t smem_max) {
 
 template <int NU>
 cudaError_t launch64(cudaStream_t s, int csize, int p, const double* M, int64_t ldm, const double* W0,
-                     const double* Q0, double* W, double* V, int max_sweeps, double tol, int* err) {
+                     const double* Q0, double* Us, double* d, double* Vs, int max_sweeps, double tol, int* err,
+                     int* zflag) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = prepare(jacobi_cluster_kernel<NU>, csize, kJcSmemMax);
@@ -514,7 +535,8 @@ cudaError_t launch64(cudaStream_t s, int csize, int p, const double* M, int64_t 
   }
   cudaLaunchAttribute at[1];
   cudaLaunchConfig_t cfg = cluster_cfg(s, csize, jc_smem(p, csize), at);
-  return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel<NU>, p, M, ldm, W0, Q0, W, V, max_sweeps, tol, err);
+  return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel<NU>, p, M, ldm, W0, Q0, Us, d, Vs, max_sweeps, tol, err,
+                            zflag);
 }
 
 template <int NU>
@@ -531,11 +553,11 @@ cudaError_t launch32(cudaStream_t s, int csize, int p, const double* M, int64_t 
 }
 
 cudaError_t run64(cudaStream_t s, int csize, int p, const double* M, int64_t ldm, const double* W0, const double* Q0,
-                  double* W, double* V, int max_sweeps, double tol, int* err) {
-  if (p <= 32) return launch64<1>(s, csize, p, M, ldm, W0, Q0, W, V, max_sweeps, tol, err);
-  if (p <= 64) return launch64<2>(s, csize, p, M, ldm, W0, Q0, W, V, max_sweeps, tol, err);
-  if (p <= 128) return launch64<4>(s, csize, p, M, ldm, W0, Q0, W, V, max_sweeps, tol, err);
-  return launch64<8>(s, csize, p, M, ldm, W0, Q0, W, V, max_sweeps, tol, err);
+                  double* Us, double* d, double* Vs, int max_sweeps, double tol, int* err, int* zf) {
+  if (p <= 32) return launch64<1>(s, csize, p, M, ldm, W0, Q0, Us, d, Vs, max_sweeps, tol, err, zf);
+  if (p <= 64) return launch64<2>(s, csize, p, M, ldm, W0, Q0, Us, d, Vs, max_sweeps, tol, err, zf);
+  if (p <= 128) return launch64<4>(s, csize, p, M, ldm, W0, Q0, Us, d, Vs, max_sweeps, tol, err, zf);
+  return launch64<8>(s, csize, p, M, ldm, W0, Q0, Us, d, Vs, max_sweeps, tol, err, zf);
 }
 
 cudaError_t run32(cudaStream_t s, int csize, int p, const double* M, int64_t ldm, double* Qg, int sweeps) {
@@ -580,6 +602,7 @@ cudaError_t jacobi_svd(cudaStream_t s, int p, const double* M, int64_t ldm, doub
   double* gw = X2 + pe;    // split-K partials of the p x p products (4 p^2)
   const int64_t gwe = 4 * pe;
   int* err = reinterpret_cast<int*>(bar + 2);
+  int* zflag = reinterpret_cast<int*>(bar + 3);
   const int csize = cluster_size();
   const double tol = static_cast<double>(p) * 0x1p-53;
   const ProfToken tok = prof_begin(s, kProfJacobi);
@@ -600,13 +623,13 @@ cudaError_t jacobi_svd(cudaStream_t s, int p, const double* M, int64_t ldm, doub
       if (e == cudaSuccess) e = gemm_f64(s, false, false, p, p, p, 1.0, Qin, p, X1, p, 0.0, Qout, p, gw, gwe);
     }
     if (e == cudaSuccess) e = gemm_f64(s, true, false, p, p, p, 1.0, M, ldm, V, p, 0.0, W, p, gw, gwe);
-    if (e == cudaSuccess) e = run64(s, csize, p, M, ldm, W, V, W, V, max_sweeps, tol, err);
+    if (e == cudaSuccess) e = run64(s, csize, p, M, ldm, W, V, Us, d, Vs, max_sweeps, tol, err, zflag);
   } else {
-    e = run64(s, csize, p, M, ldm, nullptr, nullptr, W, V, max_sweeps, tol, err);
+    e = run64(s, csize, p, M, ldm, nullptr, nullptr, Us, d, Vs, max_sweeps, tol, err, zflag);
   }
   note_launch();
   if (e != cudaSuccess) return e;
-  jacobi_finish_kernel<<<1, 256, 0, s>>>(p, W, V, Us, d, Vs);
+  jacobi_complete_kernel<<<1, 256, 0, s>>>(p, Us, d, Vs, zflag);
   note_launch();
   // flops are iteration-dependent; record the p x p input and three p x p outputs
   prof_end(s, tok, 0.0, 8.0 * 4.0 * p * p);
