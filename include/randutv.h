@@ -59,10 +59,14 @@ typedef struct randutv_opts {
                            stream, overlapped with the serial panel QR and
                            small SVD of the T chain (same results); 0: one
                            stream                                              */
+  int tensor_cores;     /* mixed form only: 1 = the sketch products X^T G and
+                           X^T Z on the tcgen05 tensor cores (3xTF32, FP32
+                           accumulation) when the operands meet the TMA
+                           alignment rules; 0 = FP32 CUDA cores               */
 } randutv_opts;
 
 /* Defaults: FP64, form_uv = 1, max_sweeps = 30, p = 0, seed = 998, no g_inject,
-   overlap = 1. */
+   overlap = 1, tensor_cores = 1. */
 void randutv_opts_default(randutv_opts* opts);
 
 /* Stream used by all later calls in this process (a cudaStream_t; NULL =
@@ -132,6 +136,7 @@ const char* randutv_last_error(void);
 #define RANDUTV_PROF_GAUSS    4  /* Philox Gaussian                                   */
 #define RANDUTV_PROF_OTHER    5  /* copies, fills, norms                              */
 #define RANDUTV_PROF_GEMM32   6  /* FP32 GEMM of the mixed-precision form             */
+#define RANDUTV_PROF_GEMMTC   7  /* tensor-core (tcgen05, TF32) GEMM of the sketch    */
 
 /* Turn per-kernel-class timing on (1) or off (0).  While on, each launch of a
  * class is bracketed by CUDA events on its stream and its algorithmic flops
@@ -172,6 +177,15 @@ int randutv_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k, dou
 int randutv_sgemm(char transa, char transb, int64_t m, int64_t n, int64_t k, float alpha,
                   const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
                   float* C, int64_t ldc);
+
+/* C = alpha A^T B + beta C on the tcgen05 tensor cores: A is k x m (lda), B
+ * k x n (ldb), C m x n (ldc), all FP32 column-major, FP32 accumulation in
+ * tensor memory.  passes = 1: inputs used as TF32 (10-bit mantissa);
+ * passes = 3: each input split into two TF32 parts and three products
+ * accumulated (3xTF32, FP32-level products).  Requires 16-byte aligned A, B
+ * and lda, ldb multiples of 4 (TMA); otherwise RANDUTV_EUNSUPPORTED. */
+int randutv_sgemm_tc(int64_t m, int64_t n, int64_t k, float alpha, const float* A, int64_t lda,
+                     const float* B, int64_t ldb, float beta, float* C, int64_t ldc, int passes);
 
 /* Unpivoted Householder QR of the k x w panel P (k >= w >= 1, ldp >= k), in
  * place (eq. unpivQR; LAPACK dlarfg convention: beta = -sign(alpha)||x||,

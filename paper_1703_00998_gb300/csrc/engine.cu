@@ -247,6 +247,7 @@ void randutv_opts_default(randutv_opts* o) {
   o->seed = 998;
   o->g_inject = nullptr;
   o->overlap = 1;
+  o->tensor_cores = 1;
 }
 
 int randutv_set_stream(void* s) {

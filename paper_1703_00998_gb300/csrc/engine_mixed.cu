@@ -220,6 +220,15 @@ cudaError_t wy_left_t32(cudaStream_t s, int64_t rows, int64_t cols, float* C, in
   return gemm_f32(s, false, false, rows, cols, w, -1.f, Vx, rows, W2, w, 1.f, C, ldc, gws, ge);
 }
 
+// Y (kc x b) = X^T G (X kr x kc, G kr x b): the sketch product, on the
+// tensor cores when allowed and the operands meet the TMA rules.
+cudaError_t sketch_tn(cudaStream_t s, bool tc, int64_t kc, int64_t b, int64_t kr, const float* X, int64_t ldx,
+                      const float* G, int64_t ldg, float* Y, int64_t ldy, float* gws, int64_t ge, int* err) {
+  if (tc && gemm_tc_supported(X, ldx, G, ldg, kc, b, kr))
+    return gemm_tc_tn(s, kc, b, kr, 1.f, X, ldx, G, ldg, 0.f, Y, ldy, gws, ge, err, true);
+  return gemm_f32(s, true, false, kc, b, kr, 1.f, X, ldx, G, ldg, 0.f, Y, ldy, gws, ge);
+}
+
 cudaError_t rot_right32(cudaStream_t s, int64_t rows, int w, float* X, int64_t ldx, const float* Q, float* tmp,
                         float* gws, int64_t ge) {
   if (rows <= 0 || w <= 0) return cudaSuccess;
@@ -296,6 +305,8 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
   cudaStream_t s = current_stream();
   MWork w{};
   Lanes L;
+  bool tc = false;
+  int* tc_err = nullptr;
   int st = RANDUTV_OK;
   double h_norm2 = 0.0, normA = 0.0;
   int64_t g_off = 0;
@@ -309,6 +320,8 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
       return e == cudaErrorMemoryAllocation ? RANDUTV_ENOMEM : RANDUTV_ECUDA;
     }
   }
+  tc = opts.tensor_cores != 0;
+  tc_err = reinterpret_cast<int*>(slot_of(w.flags, 3) + 2);
   RUTV_MCK(L.open(s, opts.overlap != 0 && uv));
   {
     cudaStream_t sT = L.t, sU = L.uv;
@@ -351,10 +364,10 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
           RUTV_MCK(down(sT, kr, b, w.G64, kr, w.G, kr));
         }
         g_off += kr * b;
-        RUTV_MCK(gemm_f32(sT, true, false, kc, b, kr, 1.f, X, ldt, w.G, kr, 0.f, w.Y, kc, w.gws, w.gws_elems));
+        RUTV_MCK(sketch_tn(sT, tc, kc, b, kr, X, ldt, w.G, kr, w.Y, kc, w.gws, w.gws_elems, tc_err));
         for (int j = 0; j < q; ++j) {
           RUTV_MCK(gemm_f32(sT, false, false, kr, b, kc, 1.f, X, ldt, w.Y, kc, 0.f, w.Z, kr, w.gws, w.gws_elems));
-          RUTV_MCK(gemm_f32(sT, true, false, kc, b, kr, 1.f, X, ldt, w.Z, kr, 0.f, w.Y, kc, w.gws, w.gws_elems));
+          RUTV_MCK(sketch_tn(sT, tc, kc, b, kr, X, ldt, w.Z, kr, w.Y, kc, w.gws, w.gws_elems, tc_err));
         }
         // QR(Y) in FP64
         RUTV_MCK(up(sT, kc, b, w.Y, kc, w.Y64, kc));

@@ -159,6 +159,15 @@ SPlan plan_sgemm(int64_t M, int64_t N, int64_t K, int64_t work_elems) {
 }
 }  // namespace
 
+cudaError_t gemm_f32_reduce(cudaStream_t s, int64_t m, int64_t n, int splits, float alpha, const float* part,
+                            float beta, float* C, int64_t ldc) {
+  const int64_t tot = m * n;
+  sgemm_reduce_kernel<<<static_cast<unsigned>((tot + 255) / 256), 256, 0, s>>>(m, n, splits, alpha, part, beta, C,
+                                                                               ldc);
+  note_launch();
+  return cudaGetLastError();
+}
+
 int64_t gemm_f32_work_elems(int64_t m, int64_t n, int64_t k) {
   SPlan p = plan_sgemm(m, n, k, INT64_MAX / 4);
   return p.splits > 1 ? p.splits * m * n : 0;

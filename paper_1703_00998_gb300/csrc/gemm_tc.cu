@@ -1,0 +1,417 @@
+// Tensor-core GEMM of the mixed-precision form (tcgen05, TF32 inputs, FP32
+// accumulation in tensor memory): D = alpha A^T B + beta D with A stored
+// K x M and B stored K x N, both column-major FP32 (so both tiles are
+// K-major: the form of the sketch products Y = X^T G and Y = X^T Z of
+// Section 4.3).  The sketch only decides which subspace a step captures, so
+// TF32 inputs are enough there.
+//
+// One CTA computes a 128 x 128 tile of D over a K range (split-K partials
+// are summed in FP64 by the FP32 GEMM's reduction kernel):
+//   warp 0, one thread: TMA loads of 32-wide K slices of A and B (128B
+//     swizzle) into a 4-stage shared-memory ring, mbarrier transaction counts;
+//   warp 1, one thread: tcgen05.mma.kind::tf32 (M = N = 128, K = 8 per
+//     instruction) into a 128-column FP32 accumulator in tensor memory, each
+//     stage released by tcgen05.commit on its "empty" mbarrier;
+//   all 4 warps: tcgen05.ld of their 32 lanes, alpha/beta, coalesced stores.
+// Every mbarrier wait is bounded (~2 s of GPU time); on expiry the CTA sets
+// the error word, waits (bounded) for its copies in flight, frees its tensor
+// memory and returns.
+#include <cuda.h>
+#include "common.cuh"
+#include "internal.h"
+
+namespace rutv {
+namespace {
+
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 32;   // BK = 32 fp32 = 128 bytes = one swizzle row
+constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 4;       // 16 KB per operand per stage
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long t0) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t spin = 0;; ++spin) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((spin & 1023u) == 1023u && global_ns() - t0 > 2000000000ull) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile with 128B swizzle:
+// rows of 128 bytes, 8-row swizzle atoms 1024 bytes apart (stride byte
+// offset), leading byte offset unused for this layout, descriptor version 1,
+// layout type 2 (128B swizzle).
+__device__ __forceinline__ uint64_t kmajor_sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>(1u) << 16;                 // leading byte offset (unused), 16 B units
+  d |= static_cast<uint64_t>(1024u >> 4) << 32;         // stride byte offset, 16 B units
+  d |= static_cast<uint64_t>(1u) << 46;                 // descriptor version
+  d |= static_cast<uint64_t>(2u) << 61;                 // 128B swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::tf32: D FP32, A and B TF32, both K-major,
+// N = 128, M = 128.
+constexpr uint32_t kIdescTf32 = (1u << 4)            // D format F32
+                                | (2u << 7)          // A format TF32
+                                | (2u << 10)         // B format TF32
+                                | ((TC_BN >> 3) << 17)
+                                | ((TC_BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(kIdescTf32), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+  return __uint_as_float(u);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Kernel configuration.  SPLIT = true is the 3xTF32 form: four more warps
+// split each landed tile x into hi = rna_tf32(x) (in place) and
+// lo = rna_tf32(x - hi), both exactly representable in TF32, and the MMA
+// warp accumulates hi*hi + hi*lo + lo*hi (error ~2^-22 relative per product,
+// FP32 level); the lo*lo term is dropped.
+template <bool SPLIT>
+struct TcCfg {
+  static constexpr int STAGES = SPLIT ? 3 : 4;
+  static constexpr int TILES = SPLIT ? 4 : 2;               // tiles per stage: A, B (, A_lo, B_lo)
+  static constexpr int NT = SPLIT ? 192 : 128;
+  static constexpr int EPI_WARP0 = SPLIT ? 2 : 0;            // first of the 4 epilogue warps
+  static constexpr int SMEM = STAGES * TILES * TC_TILE_BYTES + 1024 + 256;
+};
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(TcCfg<SPLIT>::NT, 1)
+gemm_tc_tn_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int64_t M,
+                  int64_t N, int64_t K, float alpha, float beta, float* __restrict__ D, int64_t ldd,
+                  float* __restrict__ part, int64_t kchunk, int* __restrict__ err) {
+  using C = TcCfg<SPLIT>;
+  constexpr int S = C::STAGES;
+  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  // 1024-byte aligned tiles (the 128B swizzle pattern repeats every 1024 bytes)
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  auto tileA = [&](int st) { return base + st * C::TILES * TC_TILE_BYTES; };
+  auto tileB = [&](int st) { return base + st * C::TILES * TC_TILE_BYTES + TC_TILE_BYTES; };
+  auto tileAlo = [&](int st) { return base + st * C::TILES * TC_TILE_BYTES + 2 * TC_TILE_BYTES; };
+  auto tileBlo = [&](int st) { return base + st * C::TILES * TC_TILE_BYTES + 3 * TC_TILE_BYTES; };
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + S * C::TILES * TC_TILE_BYTES);
+  uint64_t* split = full + S;
+  uint64_t* empty = split + S;
+  uint64_t* done = empty + S;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  __shared__ int s_fail;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = static_cast<int>(blockIdx.x) * TC_BM;
+  const int n0 = static_cast<int>(blockIdx.y) * TC_BN;
+  const int64_t kbeg = static_cast<int64_t>(blockIdx.z) * kchunk;
+  const int64_t kend = (kbeg + kchunk < K) ? kbeg + kchunk : K;
+  const int nkb = static_cast<int>((kend - kbeg + TC_BK - 1) / TC_BK);
+
+  if (tid == 0) {
+    s_fail = 0;
+    for (int st = 0; st < S; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&split[st], 128);
+      mbar_init(&empty[st], 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {   // allocate 128 tensor-memory columns (the 128 x 128 FP32 accumulator)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TC_BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const unsigned long long t0 = global_ns();
+  int issued = 0;   // TMA stages issued by the producer
+
+  if (warp == 0 && lane == 0) {
+    // producer
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int st = kb % S;
+      if (!mbar_wait(&empty[st], ((kb / S) & 1) ^ 1, t0)) { s_fail = 1; break; }
+      mbar_expect_tx(&full[st], 2 * TC_TILE_BYTES);
+      const int kx = static_cast<int>(kbeg + static_cast<int64_t>(kb) * TC_BK);
+      tma_load_2d(tileA(st), &mapA, kx, m0, &full[st]);
+      tma_load_2d(tileB(st), &mapB, kx, n0, &full[st]);
+      ++issued;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int st = kb % S;
+      if (!mbar_wait(SPLIT ? &split[st] : &full[st], (kb / S) & 1, t0)) { s_fail = 1; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint64_t da = kmajor_sw128_desc(smem_u32(tileA(st)));
+      const uint64_t db = kmajor_sw128_desc(smem_u32(tileB(st)));
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 8; ++kk) {   // K = 8 per instruction: +32 bytes = +2 in 16 B units
+        mma_tf32(tmem, da + 2ull * kk, db + 2ull * kk, (kb > 0 || kk > 0) ? 1u : 0u);
+        if (SPLIT) {
+          const uint64_t dal = kmajor_sw128_desc(smem_u32(tileAlo(st)));
+          const uint64_t dbl = kmajor_sw128_desc(smem_u32(tileBlo(st)));
+          mma_tf32(tmem, da + 2ull * kk, dbl + 2ull * kk, 1u);
+          mma_tf32(tmem, dal + 2ull * kk, db + 2ull * kk, 1u);
+        }
+      }
+      mma_commit(&empty[st]);
+    }
+    mma_commit(done);   // arrives once every issued MMA has completed
+  } else if (SPLIT && warp >= 2) {
+    // splitters: hi = rna_tf32(x) in place, lo = rna_tf32(x - hi); the A and B
+    // tiles of a stage are adjacent (8192 floats), and so are their lo tiles
+    const int w = tid - 64;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int st = kb % S;
+      if (!mbar_wait(&full[st], (kb / S) & 1, t0)) { s_fail = 1; break; }
+      float4* hi = reinterpret_cast<float4*>(tileA(st));
+      float4* lo = reinterpret_cast<float4*>(tileAlo(st));
+#pragma unroll 4
+      for (int e = w; e < 2 * TC_TILE_BYTES / 16; e += 128) {
+        const float4 x = hi[e];
+        float4 h, l;
+        h.x = tf32_rna(x.x); h.y = tf32_rna(x.y); h.z = tf32_rna(x.z); h.w = tf32_rna(x.w);
+        l.x = tf32_rna(x.x - h.x); l.y = tf32_rna(x.y - h.y); l.z = tf32_rna(x.z - h.z); l.w = tf32_rna(x.w - h.w);
+        hi[e] = h;
+        lo[e] = l;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor-core reads
+      mbar_arrive(&split[st]);
+    }
+  }
+  __syncwarp();
+  // epilogue: wait for the accumulator (the decision is made uniform across
+  // the CTA: tcgen05.ld below is a warp-collective instruction)
+  const bool epi = warp >= C::EPI_WARP0 && warp < C::EPI_WARP0 + 4;
+  const bool waited = epi ? mbar_wait(done, 0, t0) : true;
+  const bool warp_ok = __all_sync(0xffffffffu, waited) != 0;
+  if (!warp_ok && lane == 0) s_fail = 1;
+  __syncthreads();
+  const bool ok = (s_fail == 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int quarter = warp & 3;   // the 32 tensor-memory lanes this warp may read
+  if (epi && ok && nkb > 0) {
+    const int row = m0 + quarter * 32 + lane;
+    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+      uint32_t r[32];
+      const uint32_t taddr = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + static_cast<uint32_t>(c0);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int64_t col = n0 + c0 + j;
+          if (col < N) {
+            const float v = __uint_as_float(r[j]);
+            if (part) {
+              part[static_cast<int64_t>(blockIdx.z) * M * N + row + col * M] = v;
+            } else {
+              float* dp = D + row + col * ldd;
+              *dp = (beta == 0.f) ? alpha * v : fmaf(alpha, v, beta * *dp);
+            }
+          }
+        }
+      }
+    }
+  } else if (epi && nkb == 0 && ok) {
+    // empty K range: D = beta D (or zero partials)
+    const int row = m0 + quarter * 32 + lane;
+    if (row < M)
+      for (int j = 0; j < TC_BN; ++j) {
+        const int64_t col = n0 + j;
+        if (col >= N) break;
+        if (part) part[static_cast<int64_t>(blockIdx.z) * M * N + row + col * M] = 0.f;
+        else { float* dp = D + row + col * ldd; *dp = (beta == 0.f) ? 0.f : beta * *dp; }
+      }
+  }
+  if (!ok && tid == 0) atomicOr(err, kDevErrTimeout);
+  // drain: the producer's copies in flight must land before the CTA exits
+  if (!ok && warp == 0 && lane == 0) {
+    for (int kb = 0; kb < issued; ++kb) mbar_wait(&full[kb % S], (kb / S) & 1, global_ns());
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN) : "memory");
+  }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2-D map of a column-major FP32 matrix with `rows` contiguous entries per
+// column (the K direction) and `cols` columns, leading dimension ld; box
+// 32 x 128 with 128B swizzle, zero fill outside the matrix.
+bool make_map(CUtensorMap* map, const float* ptr, int64_t rows, int64_t cols, int64_t ld) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(cols)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * sizeof(float)};
+  cuuint32_t box[2] = {TC_BK, TC_BM};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool gemm_tc_supported(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t m, int64_t n, int64_t k) {
+  // TMA: 16-byte aligned bases and strides; sizes within the 32-bit coordinate range
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  return encode_fn() != nullptr && al16(A) && al16(B) && (lda % 4) == 0 && (ldb % 4) == 0 && m > 0 && n > 0 &&
+         k > 0 && m < (1ll << 31) && n < (1ll << 31) && k < (1ll << 31);
+}
+
+// D (m x n) = alpha A^T B + beta D with A k x m (lda), B k x n (ldb);
+// split = true runs the 3xTF32 form (FP32-level products).
+cudaError_t gemm_tc_tn(cudaStream_t s, int64_t m, int64_t n, int64_t k, float alpha, const float* A, int64_t lda,
+                       const float* B, int64_t ldb, float beta, float* D, int64_t ldd, float* work, int64_t work_elems,
+                       int* err, bool split) {
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, k, m, lda) || !make_map(&mb, B, k, n, ldb)) return cudaErrorInvalidValue;
+  static bool attr[2] = {false, false};
+  if (!attr[split]) {
+    cudaError_t e = split ? cudaFuncSetAttribute(gemm_tc_tn_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 TcCfg<true>::SMEM)
+                          : cudaFuncSetAttribute(gemm_tc_tn_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 TcCfg<false>::SMEM);
+    if (e != cudaSuccess) return e;
+    attr[split] = true;
+  }
+  const int64_t tiles = ((m + TC_BM - 1) / TC_BM) * ((n + TC_BN - 1) / TC_BN);
+  // split K until the tiles cover the SMs (each CTA uses one SM: >= 130 KB of shared memory)
+  int splits = 1;
+  while (tiles * splits < kNumSMs && (k / (splits + 1)) >= 4 * TC_BK && (splits + 1) * m * n <= work_elems) ++splits;
+  int64_t kc = (k + splits - 1) / splits;
+  kc = ((kc + TC_BK - 1) / TC_BK) * TC_BK;
+  splits = static_cast<int>((k + kc - 1) / kc);
+  float* part = splits > 1 ? work : nullptr;
+  dim3 grid(static_cast<unsigned>((m + TC_BM - 1) / TC_BM), static_cast<unsigned>((n + TC_BN - 1) / TC_BN),
+            static_cast<unsigned>(splits));
+  const ProfToken tok = prof_begin(s, kProfGemmTc);
+  if (split)
+    gemm_tc_tn_kernel<true><<<grid, TcCfg<true>::NT, TcCfg<true>::SMEM, s>>>(ma, mb, m, n, k, alpha, beta, D, ldd,
+                                                                            part, kc, err);
+  else
+    gemm_tc_tn_kernel<false><<<grid, TcCfg<false>::NT, TcCfg<false>::SMEM, s>>>(ma, mb, m, n, k, alpha, beta, D,
+                                                                               ldd, part, kc, err);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && splits > 1) e = gemm_f32_reduce(s, m, n, splits, alpha, part, beta, D, ldd);
+  prof_end(s, tok, (split ? 3.0 : 1.0) * 2.0 * m * n * k, 4.0 * (m * k + k * n + m * n * (beta != 0.f ? 2.0 : 1.0)));
+  return e;
+}
+
+}  // namespace rutv
+
+extern "C" int randutv_sgemm_tc(int64_t m, int64_t n, int64_t k, float alpha, const float* A, int64_t lda,
+                                const float* B, int64_t ldb, float beta, float* C, int64_t ldc, int passes) {
+  using namespace rutv;
+  if (m < 1) return -1;
+  if (n < 1) return -2;
+  if (k < 1) return -3;
+  if (!A) return -5;
+  if (lda < k) return -6;
+  if (!B) return -7;
+  if (ldb < k) return -8;
+  if (!C) return -10;
+  if (ldc < m) return -11;
+  if (passes != 1 && passes != 3) return -12;
+  if (!gemm_tc_supported(A, lda, B, ldb, m, n, k)) {
+    set_last_error("randutv_sgemm_tc: operands do not meet the TMA alignment rules");
+    return RANDUTV_EUNSUPPORTED;
+  }
+  cudaStream_t s = current_stream();
+  const int64_t we = 16 * m * n;
+  float* ws = nullptr;
+  int* err = nullptr;
+  int herr = 0;
+  cudaError_t e = cudaMallocAsync(&ws, we * sizeof(float) + 256, s);
+  if (e != cudaSuccess) { cudaGetLastError(); return RANDUTV_ENOMEM; }
+  err = reinterpret_cast<int*>(reinterpret_cast<char*>(ws) + we * sizeof(float));
+  e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = gemm_tc_tn(s, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, we, err, passes == 3);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = e2;
+  cudaFreeAsync(ws, s);
+  cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    set_last_error(cudaGetErrorString(e));
+    return RANDUTV_ECUDA;
+  }
+  return (herr & kDevErrTimeout) ? RANDUTV_ETIMEOUT : RANDUTV_OK;
+}

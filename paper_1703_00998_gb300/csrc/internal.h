@@ -18,7 +18,7 @@ constexpr int kFlagSlots = 8;
 
 // ---- prof.cu ----
 enum ProfClass { kProfGemm = 0, kProfPanel = 1, kProfTfactor = 2, kProfJacobi = 3, kProfGauss = 4,
-                 kProfOther = 5, kProfGemm32 = 6, kProfClasses = 7 };
+                 kProfOther = 5, kProfGemm32 = 6, kProfGemmTc = 7, kProfClasses = 8 };
 struct ProfTotals { double ms = 0.0; int64_t launches = 0; double flops = 0.0; double bytes = 0.0; };
 struct ProfToken { int idx; };
 void note_launch(int n = 1);
@@ -43,6 +43,19 @@ cudaError_t gemm_f32(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int
                      const float* A, int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
                      float* work, int64_t work_elems);
 int64_t gemm_f32_work_elems(int64_t m, int64_t n, int64_t k);
+// Sum split-K FP32 partials (m x n each) in FP64 into C = alpha sum + beta C.
+cudaError_t gemm_f32_reduce(cudaStream_t s, int64_t m, int64_t n, int splits, float alpha, const float* part,
+                            float beta, float* C, int64_t ldc);
+
+// ---- gemm_tc.cu ----
+// D (m x n) = alpha A^T B + beta D on the tensor cores (tcgen05, TF32 inputs,
+// FP32 accumulation), A k x m (lda), B k x n (ldb), column-major FP32.  `work`
+// holds split-K partials; `err` receives kDevErrTimeout if a wait ran out.
+cudaError_t gemm_tc_tn(cudaStream_t s, int64_t m, int64_t n, int64_t k, float alpha, const float* A, int64_t lda,
+                       const float* B, int64_t ldb, float beta, float* D, int64_t ldd, float* work, int64_t work_elems,
+                       int* err, bool split);
+// Whether gemm_tc_tn can take these operands (TMA alignment rules, driver entry point).
+bool gemm_tc_supported(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t m, int64_t n, int64_t k);
 
 // ---- philox.cu ----
 cudaError_t launch_gaussian(cudaStream_t s, uint64_t seed, int64_t step, int64_t k, int64_t b,

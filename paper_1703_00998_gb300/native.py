@@ -32,6 +32,7 @@ class Opts(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("g_inject", ctypes.c_void_p),
         ("overlap", ctypes.c_int),
+        ("tensor_cores", ctypes.c_int),
     ]
 
 
@@ -58,6 +59,8 @@ SIGNATURES = {
                              _vp, _i64]),
     "randutv_sgemm": (_i32, [ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, ctypes.c_float, _vp, _i64, _vp, _i64,
                              ctypes.c_float, _vp, _i64]),
+    "randutv_sgemm_tc": (_i32, [_i64, _i64, _i64, ctypes.c_float, _vp, _i64, _vp, _i64, ctypes.c_float, _vp, _i64,
+                                _i32]),
     "randutv_panel_qr": (_i32, [_i64, _i64, _vp, _i64, _vp, _vp, _vp]),
     "randutv_small_svd": (_i32, [_i64, _vp, _i64, _vp, _vp, _vp, _i32]),
     "randutv_profile_enable": (_i32, [_i32]),
@@ -68,8 +71,8 @@ SIGNATURES = {
     "randutv_small_svd_noalloc": (_i32, [_i64, _vp, _i64, _vp, _vp, _vp, _i32]),
 }
 
-PROF_GEMM, PROF_PANEL, PROF_TFACTOR, PROF_JACOBI, PROF_GAUSS, PROF_OTHER, PROF_GEMM32 = range(7)
-PROF_NAMES = ["gemm", "panel_qr", "tfactor", "jacobi", "gauss", "other", "gemm32"]
+PROF_GEMM, PROF_PANEL, PROF_TFACTOR, PROF_JACOBI, PROF_GAUSS, PROF_OTHER, PROF_GEMM32, PROF_GEMMTC = range(8)
+PROF_NAMES = ["gemm", "panel_qr", "tfactor", "jacobi", "gauss", "other", "gemm32", "gemm_tc"]
 
 
 def profile_read(cls):
