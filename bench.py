@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-verify", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--tensor-cores", type=int, default=1, choices=[0, 1],
+                    help="mixed form: 0 CUDA cores only, 1 sketch products on the tcgen05 tensor cores")
     ap.add_argument("--forms", default="fp64,mixed", help="fp64, mixed or both (the FP64 form carries the line)")
     return ap.parse_args()
 
@@ -205,6 +207,7 @@ def run_mixed(args, lib, native, A, Tst64, n, b, q, stream, dist):
     Ust = torch.empty((n, n), dtype=torch.float32, device="cuda")
     Vst = torch.empty((n, n), dtype=torch.float32, device="cuda")
     opts = native.default_opts()
+    opts.tensor_cores = args.tensor_cores
     kr = ctypes.c_int64(0)
 
     def step():
@@ -235,7 +238,7 @@ def run_mixed(args, lib, native, A, Tst64, n, b, q, stream, dist):
         ms = float(t.item())
     world = dist.get_world_size() if dist else 1
     out = {"value": world * total_flops(n, q) / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
-           "dtype": "f32 storage and products, f64 panel QR and small SVD",
+           "dtype": "f32 storage and products, f64 panel QR and small SVD", "tensor_cores": args.tensor_cores,
            "breakdown": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
                          for k, v in prof.items()}}
     g = prof["gemm32"]

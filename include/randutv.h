@@ -59,10 +59,12 @@ typedef struct randutv_opts {
                            stream, overlapped with the serial panel QR and
                            small SVD of the T chain (same results); 0: one
                            stream                                              */
-  int tensor_cores;     /* mixed form only: 1 = the sketch products X^T G and
-                           X^T Z on the tcgen05 tensor cores (3xTF32, FP32
-                           accumulation) when the operands meet the TMA
-                           alignment rules; 0 = FP32 CUDA cores               */
+  int tensor_cores;     /* mixed form only: 1 = the sketch products X^T G,
+                           X Y and X^T Z on the tcgen05 tensor cores (3xTF32,
+                           FP32 accumulation) when the operands meet the TMA
+                           alignment rules; 0 = FP32 CUDA cores.  The
+                           block-reflector and rotation products always run
+                           on the FP32 CUDA cores (round to nearest).        */
 } randutv_opts;
 
 /* Defaults: FP64, form_uv = 1, max_sweeps = 30, p = 0, seed = 998, no g_inject,
@@ -178,14 +180,22 @@ int randutv_sgemm(char transa, char transb, int64_t m, int64_t n, int64_t k, flo
                   const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
                   float* C, int64_t ldc);
 
-/* C = alpha A^T B + beta C on the tcgen05 tensor cores: A is k x m (lda), B
- * k x n (ldb), C m x n (ldc), all FP32 column-major, FP32 accumulation in
- * tensor memory.  passes = 1: inputs used as TF32 (10-bit mantissa);
- * passes = 3: each input split into two TF32 parts and three products
- * accumulated (3xTF32, FP32-level products).  Requires 16-byte aligned A, B
- * and lda, ldb multiples of 4 (TMA); otherwise RANDUTV_EUNSUPPORTED. */
-int randutv_sgemm_tc(int64_t m, int64_t n, int64_t k, float alpha, const float* A, int64_t lda,
-                     const float* B, int64_t ldb, float beta, float* C, int64_t ldc, int passes);
+/* C = alpha op(A) op(B) + beta C on the tcgen05 tensor cores, FP32
+ * column-major operands, FP32 accumulation in tensor memory.  transa 'T':
+ * op(A) = A^T with A k x m; 'N': op(A) = A with A m x k.  transb 'N':
+ * op(B) = B with B k x n; 'T': op(B) = B^T with B n x k.  C is m x n (ldc).
+ * The products of Section 4.3 (sketch) and of the block-reflector
+ * applications (eq. WYrepresentation) all take one of these four forms.
+ * passes = 1: inputs used as TF32 (10-bit mantissa); passes = 3: each input
+ * split into two TF32 parts and three products accumulated (3xTF32,
+ * FP32-level products; the accumulator itself does not round to nearest,
+ * so the error grows with k).  Requires 16-byte aligned A, B and lda, ldb
+ * multiples of 4 (TMA); otherwise RANDUTV_EUNSUPPORTED.  Negative return:
+ * the position of the first invalid argument.  Allocates its split-K
+ * scratch with cudaMallocAsync on the bound stream and synchronises it. */
+int randutv_sgemm_tc(char transa, char transb, int64_t m, int64_t n, int64_t k, float alpha,
+                     const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
+                     float* C, int64_t ldc, int passes);
 
 /* Unpivoted Householder QR of the k x w panel P (k >= w >= 1, ldp >= k), in
  * place (eq. unpivQR; LAPACK dlarfg convention: beta = -sign(alpha)||x||,

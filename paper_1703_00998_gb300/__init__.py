@@ -79,9 +79,11 @@ def factor(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sw
     return UTV(Ust.t() if form_uv else None, Tst.t(), Vst.t() if form_uv else None, kr.value)
 
 
-def factor_mixed(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sweeps=30, overlap=True):
+def factor_mixed(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sweeps=30, overlap=True,
+                 tensor_cores=1):
     """Mixed-precision randUTV: A is an (m, n) float32 CUDA tensor; U, T, V
-    come back float32.  Panel QRs and small SVDs run in FP64 inside."""
+    come back float32.  Panel QRs and small SVDs run in FP64 inside.
+    tensor_cores: 1 runs the sketch products on the tcgen05 tensor cores."""
     torch = _torch()
     if not isinstance(A, torch.Tensor) or A.dim() != 2 or A.dtype != torch.float32 or not A.is_cuda:
         raise TypeError("A must be a 2-D float32 CUDA tensor")
@@ -94,6 +96,7 @@ def factor_mixed(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, 
             if g_inject.dtype != torch.float64 or not g_inject.is_cuda or not g_inject.is_contiguous():
                 raise TypeError("g_inject must be a contiguous float64 CUDA tensor")
         o = _opts(seed, form_uv, max_sweeps, g_inject, overlap)
+        o.tensor_cores = int(tensor_cores)
         kr = ctypes.c_int64(0)
         _bind_stream()
         st = native.lib().randutv_factor_mixed(

@@ -200,47 +200,62 @@ cudaError_t mwork_alloc(cudaStream_t s, int64_t m, int64_t n, int b, MWork* w) {
   return cudaMemsetAsync(w->flags, 0, 4 * kFlagSlots * sizeof(unsigned), s);
 }
 
+// Where each FP32 product runs.  The sketch products (kSketch) only decide
+// which subspace a step captures, so with tensor_cores = 1 they run on the
+// tcgen05 tensor cores (3xTF32, FP32 accumulation in tensor memory).  The
+// products of the block-reflector applications and rotations (kUpdate)
+// enter the backward error directly and stay on the FP32 CUDA cores (round
+// to nearest, split sums in FP64): the tensor-core accumulator does not
+// round to nearest, and putting even the inner-dimension-b updates on it
+// measured a residual of 3e-6 at n = 8000 (1e-6 is the target), and slower.
+enum GemmKind { kSketch = 0, kUpdate = 1 };
+
+struct Mg {
+  bool tc;
+  int* err;
+  float* gws;
+  int64_t ge;
+  cudaError_t run(cudaStream_t s, GemmKind kind, bool ta, bool tb, int64_t m, int64_t n, int64_t k, float alpha,
+                  const float* A, int64_t lda, const float* B, int64_t ldb, float beta, float* C,
+                  int64_t ldc) const {
+    if (kind == kSketch && tc && gemm_tc_supported(A, lda, B, ldb, m, n, k))
+      return gemm_tc(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, gws, ge, err, true);
+    return gemm_f32(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, gws, ge);
+  }
+};
+
 // C (rows x cols) <- C (I - Vx S Vx^T), Vx cols x w, all FP32.
-cudaError_t wy_right32(cudaStream_t s, int64_t rows, int64_t cols, float* C, int64_t ldc, const float* Vx,
-                       const float* S, int w, float* W1, float* W2, float* gws, int64_t ge) {
+cudaError_t wy_right32(cudaStream_t s, const Mg& g, int64_t rows, int64_t cols, float* C, int64_t ldc,
+                       const float* Vx, const float* S, int w, float* W1, float* W2) {
   if (rows <= 0 || cols <= 0) return cudaSuccess;
   cudaError_t e;
-  if ((e = gemm_f32(s, false, false, rows, w, cols, 1.f, C, ldc, Vx, cols, 0.f, W1, rows, gws, ge))) return e;
-  if ((e = gemm_f32(s, false, false, rows, w, w, 1.f, W1, rows, S, w, 0.f, W2, rows, gws, ge))) return e;
-  return gemm_f32(s, false, true, rows, cols, w, -1.f, W2, rows, Vx, cols, 1.f, C, ldc, gws, ge);
+  if ((e = g.run(s, kUpdate, false, false, rows, w, cols, 1.f, C, ldc, Vx, cols, 0.f, W1, rows))) return e;
+  if ((e = g.run(s, kUpdate, false, false, rows, w, w, 1.f, W1, rows, S, w, 0.f, W2, rows))) return e;
+  return g.run(s, kUpdate, false, true, rows, cols, w, -1.f, W2, rows, Vx, cols, 1.f, C, ldc);
 }
 
 // C (rows x cols) <- (I - Vx S Vx^T)^T C, Vx rows x w.
-cudaError_t wy_left_t32(cudaStream_t s, int64_t rows, int64_t cols, float* C, int64_t ldc, const float* Vx,
-                        const float* S, int w, float* W1, float* W2, float* gws, int64_t ge) {
+cudaError_t wy_left_t32(cudaStream_t s, const Mg& g, int64_t rows, int64_t cols, float* C, int64_t ldc,
+                        const float* Vx, const float* S, int w, float* W1, float* W2) {
   if (rows <= 0 || cols <= 0) return cudaSuccess;
   cudaError_t e;
-  if ((e = gemm_f32(s, true, false, w, cols, rows, 1.f, Vx, rows, C, ldc, 0.f, W1, w, gws, ge))) return e;
-  if ((e = gemm_f32(s, true, false, w, cols, w, 1.f, S, w, W1, w, 0.f, W2, w, gws, ge))) return e;
-  return gemm_f32(s, false, false, rows, cols, w, -1.f, Vx, rows, W2, w, 1.f, C, ldc, gws, ge);
+  if ((e = g.run(s, kUpdate, true, false, w, cols, rows, 1.f, Vx, rows, C, ldc, 0.f, W1, w))) return e;
+  if ((e = g.run(s, kUpdate, true, false, w, cols, w, 1.f, S, w, W1, w, 0.f, W2, w))) return e;
+  return g.run(s, kUpdate, false, false, rows, cols, w, -1.f, Vx, rows, W2, w, 1.f, C, ldc);
 }
 
-// Y (kc x b) = X^T G (X kr x kc, G kr x b): the sketch product, on the
-// tensor cores when allowed and the operands meet the TMA rules.
-cudaError_t sketch_tn(cudaStream_t s, bool tc, int64_t kc, int64_t b, int64_t kr, const float* X, int64_t ldx,
-                      const float* G, int64_t ldg, float* Y, int64_t ldy, float* gws, int64_t ge, int* err) {
-  if (tc && gemm_tc_supported(X, ldx, G, ldg, kc, b, kr))
-    return gemm_tc_tn(s, kc, b, kr, 1.f, X, ldx, G, ldg, 0.f, Y, ldy, gws, ge, err, true);
-  return gemm_f32(s, true, false, kc, b, kr, 1.f, X, ldx, G, ldg, 0.f, Y, ldy, gws, ge);
-}
-
-cudaError_t rot_right32(cudaStream_t s, int64_t rows, int w, float* X, int64_t ldx, const float* Q, float* tmp,
-                        float* gws, int64_t ge) {
+cudaError_t rot_right32(cudaStream_t s, const Mg& g, int64_t rows, int w, float* X, int64_t ldx, const float* Q,
+                        float* tmp) {
   if (rows <= 0 || w <= 0) return cudaSuccess;
-  cudaError_t e = gemm_f32(s, false, false, rows, w, w, 1.f, X, ldx, Q, w, 0.f, tmp, rows, gws, ge);
+  cudaError_t e = g.run(s, kUpdate, false, false, rows, w, w, 1.f, X, ldx, Q, w, 0.f, tmp, rows);
   if (e) return e;
   return copy32(s, rows, w, tmp, rows, X, ldx);
 }
 
-cudaError_t rot_left_t32(cudaStream_t s, int w, int64_t cols, float* X, int64_t ldx, const float* Q, float* tmp,
-                         float* gws, int64_t ge) {
+cudaError_t rot_left_t32(cudaStream_t s, const Mg& g, int w, int64_t cols, float* X, int64_t ldx, const float* Q,
+                         float* tmp) {
   if (cols <= 0 || w <= 0) return cudaSuccess;
-  cudaError_t e = gemm_f32(s, true, false, w, cols, w, 1.f, Q, w, X, ldx, 0.f, tmp, w, gws, ge);
+  cudaError_t e = g.run(s, kUpdate, true, false, w, cols, w, 1.f, Q, w, X, ldx, 0.f, tmp, w);
   if (e) return e;
   return copy32(s, w, cols, tmp, w, X, ldx);
 }
@@ -305,8 +320,7 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
   cudaStream_t s = current_stream();
   MWork w{};
   Lanes L;
-  bool tc = false;
-  int* tc_err = nullptr;
+  Mg gT{}, gU{};
   int st = RANDUTV_OK;
   double h_norm2 = 0.0, normA = 0.0;
   int64_t g_off = 0;
@@ -320,8 +334,12 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
       return e == cudaErrorMemoryAllocation ? RANDUTV_ENOMEM : RANDUTV_ECUDA;
     }
   }
-  tc = opts.tensor_cores != 0;
-  tc_err = reinterpret_cast<int*>(slot_of(w.flags, 3) + 2);
+  {
+    const bool tcl = opts.tensor_cores != 0;
+    int* tc_err = reinterpret_cast<int*>(slot_of(w.flags, 3) + 2);
+    gT = Mg{tcl, tc_err, w.gws, w.gws_elems};
+    gU = Mg{tcl, tc_err, w.gwsu, w.gws_elems};
+  }
   RUTV_MCK(L.open(s, opts.overlap != 0 && uv));
   {
     cudaStream_t sT = L.t, sU = L.uv;
@@ -364,19 +382,19 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
           RUTV_MCK(down(sT, kr, b, w.G64, kr, w.G, kr));
         }
         g_off += kr * b;
-        RUTV_MCK(sketch_tn(sT, tc, kc, b, kr, X, ldt, w.G, kr, w.Y, kc, w.gws, w.gws_elems, tc_err));
+        RUTV_MCK(gT.run(sT, kSketch, true, false, kc, b, kr, 1.f, X, ldt, w.G, kr, 0.f, w.Y, kc));
         for (int j = 0; j < q; ++j) {
-          RUTV_MCK(gemm_f32(sT, false, false, kr, b, kc, 1.f, X, ldt, w.Y, kc, 0.f, w.Z, kr, w.gws, w.gws_elems));
-          RUTV_MCK(sketch_tn(sT, tc, kc, b, kr, X, ldt, w.Z, kr, w.Y, kc, w.gws, w.gws_elems, tc_err));
+          RUTV_MCK(gT.run(sT, kSketch, false, false, kr, b, kc, 1.f, X, ldt, w.Y, kc, 0.f, w.Z, kr));
+          RUTV_MCK(gT.run(sT, kSketch, true, false, kc, b, kr, 1.f, X, ldt, w.Z, kr, 0.f, w.Y, kc));
         }
         // QR(Y) in FP64
         RUTV_MCK(up(sT, kc, b, w.Y, kc, w.Y64, kc));
         RUTV_MCK(panel_wy(sT, kc, b, w.Y64, w.tau, w.Vv64, w.Rt, w.gram, w.S64, Vv, Sv, w, slot_of(w.flags, 0)));
         RUTV_MCK(cudaEventRecord(L.v[sl], sT));
-        RUTV_MCK(wy_right32(sT, m, kc, T + r0 * ldt, ldt, Vv, Sv, b, w.W1, w.W2, w.gws, w.gws_elems));
+        RUTV_MCK(wy_right32(sT, gT, m, kc, T + r0 * ldt, ldt, Vv, Sv, b, w.W1, w.W2));
         if (uv) {
           RUTV_MCK(cudaStreamWaitEvent(sU, L.v[sl], 0));
-          RUTV_MCK(wy_right32(sU, n, kc, V + r0 * ldv, ldv, Vv, Sv, b, w.W1u, w.W2u, w.gwsu, w.gws_elems));
+          RUTV_MCK(wy_right32(sU, gU, n, kc, V + r0 * ldv, ldv, Vv, Sv, b, w.W1u, w.W2u));
         }
         // QR of the panel in FP64
         RUTV_MCK(up(sT, kr, b, X, ldt, w.P64, kr));
@@ -384,9 +402,9 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
         if (uv) {
           RUTV_MCK(cudaEventRecord(L.u[sl], sT));
           RUTV_MCK(cudaStreamWaitEvent(sU, L.u[sl], 0));
-          RUTV_MCK(wy_right32(sU, m, kr, U + r0 * ldu, ldu, Vu, Su, b, w.W1u, w.W2u, w.gwsu, w.gws_elems));
+          RUTV_MCK(wy_right32(sU, gU, m, kr, U + r0 * ldu, ldu, Vu, Su, b, w.W1u, w.W2u));
         }
-        RUTV_MCK(wy_left_t32(sT, kr, kc - b, T + r0 + c1 * ldt, ldt, Vu, Su, b, w.W1, w.W2, w.gws, w.gws_elems));
+        RUTV_MCK(wy_left_t32(sT, gT, kr, kc - b, T + r0 + c1 * ldt, ldt, Vu, Su, b, w.W1, w.W2));
         RUTV_MCK(fill32(sT, kr, b, X, ldt));
         // small SVD in FP64
         RUTV_MCK(jacobi_svd(sT, b, w.R, b, w.Us64, w.d, w.Vs64, opts.max_sweeps, w.jws, slot_of(w.flags, 2)));
@@ -398,11 +416,11 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
         if (uv) {
           RUTV_MCK(cudaEventRecord(L.s[sl], sT));
           RUTV_MCK(cudaStreamWaitEvent(sU, L.s[sl], 0));
-          RUTV_MCK(rot_right32(sU, m, b, U + r0 * ldu, ldu, Us, w.tmpu, w.gwsu, w.gws_elems));
-          RUTV_MCK(rot_right32(sU, n, b, V + r0 * ldv, ldv, Vs, w.tmpu, w.gwsu, w.gws_elems));
+          RUTV_MCK(rot_right32(sU, gU, m, b, U + r0 * ldu, ldu, Us, w.tmpu));
+          RUTV_MCK(rot_right32(sU, gU, n, b, V + r0 * ldv, ldv, Vs, w.tmpu));
         }
-        RUTV_MCK(rot_left_t32(sT, b, kc - b, T + r0 + c1 * ldt, ldt, Us, w.tmp, w.gws, w.gws_elems));
-        RUTV_MCK(rot_right32(sT, r0, b, T + r0 * ldt, ldt, Vs, w.tmp, w.gws, w.gws_elems));
+        RUTV_MCK(rot_left_t32(sT, gT, b, kc - b, T + r0 + c1 * ldt, ldt, Us, w.tmp));
+        RUTV_MCK(rot_right32(sT, gT, r0, b, T + r0 * ldt, ldt, Vs, w.tmp));
       } else {
         // last block: QR first (tall or square) or QR of the rows (wide), then the FP64 SVD
         int p;
@@ -413,7 +431,7 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
           if (uv) {
             RUTV_MCK(cudaEventRecord(L.u[sl], sT));
             RUTV_MCK(cudaStreamWaitEvent(sU, L.u[sl], 0));
-            RUTV_MCK(wy_right32(sU, m, kr, U + r0 * ldu, ldu, Vu, Su, p, w.W1u, w.W2u, w.gwsu, w.gws_elems));
+            RUTV_MCK(wy_right32(sU, gU, m, kr, U + r0 * ldu, ldu, Vu, Su, p, w.W1u, w.W2u));
           }
         } else {
           p = static_cast<int>(kr);
@@ -421,11 +439,11 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
           note_launch();
           RUTV_MCK(cudaGetLastError());
           RUTV_MCK(panel_wy(sT, kc, p, w.P64, w.tau, w.Vv64, w.Rt, w.gram, w.S64, Vv, Sv, w, slot_of(w.flags, 0)));
-          RUTV_MCK(wy_right32(sT, m, kc, T + r0 * ldt, ldt, Vv, Sv, p, w.W1, w.W2, w.gws, w.gws_elems));
+          RUTV_MCK(wy_right32(sT, gT, m, kc, T + r0 * ldt, ldt, Vv, Sv, p, w.W1, w.W2));
           if (uv) {
             RUTV_MCK(cudaEventRecord(L.v[sl], sT));
             RUTV_MCK(cudaStreamWaitEvent(sU, L.v[sl], 0));
-            RUTV_MCK(wy_right32(sU, n, kc, V + r0 * ldv, ldv, Vv, Sv, p, w.W1u, w.W2u, w.gwsu, w.gws_elems));
+            RUTV_MCK(wy_right32(sU, gU, n, kc, V + r0 * ldv, ldv, Vv, Sv, p, w.W1u, w.W2u));
           }
           RUTV_MCK(transpose_f64(sT, p, p, w.Rt, p, w.R, p));
         }
@@ -439,10 +457,10 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
         if (uv) {
           RUTV_MCK(cudaEventRecord(L.s[sl], sT));
           RUTV_MCK(cudaStreamWaitEvent(sU, L.s[sl], 0));
-          RUTV_MCK(rot_right32(sU, m, p, U + r0 * ldu, ldu, Us, w.tmpu, w.gwsu, w.gws_elems));
-          RUTV_MCK(rot_right32(sU, n, p, V + r0 * ldv, ldv, Vs, w.tmpu, w.gwsu, w.gws_elems));
+          RUTV_MCK(rot_right32(sU, gU, m, p, U + r0 * ldu, ldu, Us, w.tmpu));
+          RUTV_MCK(rot_right32(sU, gU, n, p, V + r0 * ldv, ldv, Vs, w.tmpu));
         }
-        RUTV_MCK(rot_right32(sT, r0, p, T + r0 * ldt, ldt, Vs, w.tmp, w.gws, w.gws_elems));
+        RUTV_MCK(rot_right32(sT, gT, r0, p, T + r0 * ldt, ldt, Vs, w.tmp));
       }
       if (uv) RUTV_MCK(cudaEventRecord(L.done[sl], sU));
     }

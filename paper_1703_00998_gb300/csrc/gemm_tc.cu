@@ -1,9 +1,10 @@
 // Tensor-core GEMM of the mixed-precision form (tcgen05, TF32 inputs, FP32
-// accumulation in tensor memory): D = alpha A^T B + beta D with A stored
-// K x M and B stored K x N, both column-major FP32 (so both tiles are
-// K-major: the form of the sketch products Y = X^T G and Y = X^T Z of
-// Section 4.3).  The sketch only decides which subspace a step captures, so
-// TF32 inputs are enough there.
+// accumulation in tensor memory): D = alpha op(A) op(B) + beta D, all
+// column-major FP32, any transpose combination.  A transposed operand (A^T
+// with A stored K x M, or B with B stored K x N) gives K-major tiles; the
+// others give MN-major tiles.  Used for the sketch products Y = X^T G,
+// Z = X Y, Y = X^T Z of Section 4.3 and for the short (inner dimension b)
+// products of the block-reflector applications and rotations.
 //
 // One CTA computes a 128 x 128 tile of D over a K range (split-K partials
 // are summed in FP64 by the FP32 GEMM's reduction kernel):
@@ -75,19 +76,43 @@ __device__ __forceinline__ uint64_t kmajor_sw128_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor, kind::tf32: D FP32, A and B TF32, both K-major,
-// N = 128, M = 128.
-constexpr uint32_t kIdescTf32 = (1u << 4)            // D format F32
-                                | (2u << 7)          // A format TF32
-                                | (2u << 10)         // B format TF32
-                                | ((TC_BN >> 3) << 17)
-                                | ((TC_BM >> 4) << 24);
+// Descriptor of an MN-major 32-bit tile.  For 32-bit elements an MN-major
+// operand takes the "128B swizzle with 32-byte atoms" layout (type 1): rows
+// of 128 bytes along M or N, whose four 32-byte granules are permuted across
+// groups of 4 rows, written by TMA in its matching swizzle mode.  The tile
+// is four 32-element (128-byte) chunks along M or N, each a TMA box of 32
+// K-rows x 128 bytes (4096 bytes).  Leading byte offset = stride between
+// those chunks (4096 bytes); stride byte offset = stride between 4-row
+// groups along K (512 bytes: the rows are contiguous).
+__device__ __forceinline__ uint64_t mnmajor_sw128a32_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>(4096u >> 4) << 16;
+  d |= static_cast<uint64_t>(512u >> 4) << 32;
+  d |= static_cast<uint64_t>(1u) << 46;
+  d |= static_cast<uint64_t>(1u) << 61;                 // 128B swizzle, 32-byte atoms
+  return d;
+}
 
+// Instruction descriptor, kind::tf32: D FP32, A and B TF32, N = 128, M = 128;
+// bit 15 / 16 set for an MN-major A / B.
+template <bool AMN, bool BMN>
+__host__ __device__ constexpr uint32_t idesc_tf32() {
+  return (1u << 4)               // D format F32
+         | (2u << 7)             // A format TF32
+         | (2u << 10)            // B format TF32
+         | ((AMN ? 1u : 0u) << 15)
+         | ((BMN ? 1u : 0u) << 16)
+         | ((TC_BN >> 3) << 17)
+         | ((TC_BM >> 4) << 24);
+}
+
+template <bool AMN, bool BMN>
 __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-      ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(kIdescTf32), "r"(accumulate)
+      ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(idesc_tf32<AMN, BMN>()), "r"(accumulate)
       : "memory");
 }
 
@@ -120,9 +145,9 @@ struct TcCfg {
   static constexpr int SMEM = STAGES * TILES * TC_TILE_BYTES + 1024 + 256;
 };
 
-template <bool SPLIT>
+template <bool SPLIT, bool AMN, bool BMN>
 __global__ void __launch_bounds__(TcCfg<SPLIT>::NT, 1)
-gemm_tc_tn_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int64_t M,
+gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int64_t M,
                   int64_t N, int64_t K, float alpha, float beta, float* __restrict__ D, int64_t ldd,
                   float* __restrict__ part, int64_t kchunk, int* __restrict__ err) {
   using C = TcCfg<SPLIT>;
@@ -179,8 +204,16 @@ gemm_tc_tn_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
       if (!mbar_wait(&empty[st], ((kb / S) & 1) ^ 1, t0)) { s_fail = 1; break; }
       mbar_expect_tx(&full[st], 2 * TC_TILE_BYTES);
       const int kx = static_cast<int>(kbeg + static_cast<int64_t>(kb) * TC_BK);
-      tma_load_2d(tileA(st), &mapA, kx, m0, &full[st]);
-      tma_load_2d(tileB(st), &mapB, kx, n0, &full[st]);
+      if (AMN) {
+        for (int j = 0; j < 4; ++j) tma_load_2d(tileA(st) + j * 4096, &mapA, m0 + 32 * j, kx, &full[st]);
+      } else {
+        tma_load_2d(tileA(st), &mapA, kx, m0, &full[st]);
+      }
+      if (BMN) {
+        for (int j = 0; j < 4; ++j) tma_load_2d(tileB(st) + j * 4096, &mapB, n0 + 32 * j, kx, &full[st]);
+      } else {
+        tma_load_2d(tileB(st), &mapB, kx, n0, &full[st]);
+      }
       ++issued;
     }
   } else if (warp == 1 && lane == 0) {
@@ -189,16 +222,19 @@ gemm_tc_tn_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
       const int st = kb % S;
       if (!mbar_wait(SPLIT ? &split[st] : &full[st], (kb / S) & 1, t0)) { s_fail = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint64_t da = kmajor_sw128_desc(smem_u32(tileA(st)));
-      const uint64_t db = kmajor_sw128_desc(smem_u32(tileB(st)));
+      // K = 8 per instruction: a K-major tile advances 32 bytes (+2 in 16 B
+      // units) along its rows, an MN-major tile one 1024-byte atom (+64)
+      const uint64_t da = AMN ? mnmajor_sw128a32_desc(smem_u32(tileA(st))) : kmajor_sw128_desc(smem_u32(tileA(st)));
+      const uint64_t db = BMN ? mnmajor_sw128a32_desc(smem_u32(tileB(st))) : kmajor_sw128_desc(smem_u32(tileB(st)));
+      const uint64_t dal = AMN ? mnmajor_sw128a32_desc(smem_u32(tileAlo(st))) : kmajor_sw128_desc(smem_u32(tileAlo(st)));
+      const uint64_t dbl = BMN ? mnmajor_sw128a32_desc(smem_u32(tileBlo(st))) : kmajor_sw128_desc(smem_u32(tileBlo(st)));
+      constexpr uint64_t stepA = AMN ? 64ull : 2ull, stepB = BMN ? 64ull : 2ull;
 #pragma unroll
-      for (int kk = 0; kk < TC_BK / 8; ++kk) {   // K = 8 per instruction: +32 bytes = +2 in 16 B units
-        mma_tf32(tmem, da + 2ull * kk, db + 2ull * kk, (kb > 0 || kk > 0) ? 1u : 0u);
+      for (int kk = 0; kk < TC_BK / 8; ++kk) {
+        mma_tf32<AMN, BMN>(tmem, da + stepA * kk, db + stepB * kk, (kb > 0 || kk > 0) ? 1u : 0u);
         if (SPLIT) {
-          const uint64_t dal = kmajor_sw128_desc(smem_u32(tileAlo(st)));
-          const uint64_t dbl = kmajor_sw128_desc(smem_u32(tileBlo(st)));
-          mma_tf32(tmem, da + 2ull * kk, dbl + 2ull * kk, 1u);
-          mma_tf32(tmem, dal + 2ull * kk, db + 2ull * kk, 1u);
+          mma_tf32<AMN, BMN>(tmem, da + stepA * kk, dbl + stepB * kk, 1u);
+          mma_tf32<AMN, BMN>(tmem, dal + stepA * kk, db + stepB * kk, 1u);
         }
       }
       mma_commit(&empty[st]);
@@ -312,17 +348,20 @@ EncodeTiledFn encode_fn() {
 }
 
 // 2-D map of a column-major FP32 matrix with `rows` contiguous entries per
-// column (the K direction) and `cols` columns, leading dimension ld; box
-// 32 x 128 with 128B swizzle, zero fill outside the matrix.
-bool make_map(CUtensorMap* map, const float* ptr, int64_t rows, int64_t cols, int64_t ld) {
+// column and `cols` columns, leading dimension ld, zero fill outside the
+// matrix.  K-major operand (rows = K): box 32 (K) x 128, 128B swizzle;
+// MN-major operand (rows = M or N): box 32 x 32 (K), four per tile, 128B
+// swizzle with 32-byte atoms.
+bool make_map(CUtensorMap* map, const float* ptr, int64_t rows, int64_t cols, int64_t ld, bool mn_major) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(cols)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * sizeof(float)};
-  cuuint32_t box[2] = {TC_BK, TC_BM};
+  cuuint32_t box[2] = {32u, mn_major ? 32u : static_cast<cuuint32_t>(TC_BM)};
   cuuint32_t estr[2] = {1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, mn_major ? CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B : CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -335,22 +374,31 @@ bool gemm_tc_supported(const float* A, int64_t lda, const float* B, int64_t ldb,
          k > 0 && m < (1ll << 31) && n < (1ll << 31) && k < (1ll << 31);
 }
 
-// D (m x n) = alpha A^T B + beta D with A k x m (lda), B k x n (ldb);
-// split = true runs the 3xTF32 form (FP32-level products).
-cudaError_t gemm_tc_tn(cudaStream_t s, int64_t m, int64_t n, int64_t k, float alpha, const float* A, int64_t lda,
-                       const float* B, int64_t ldb, float beta, float* D, int64_t ldd, float* work, int64_t work_elems,
-                       int* err, bool split) {
-  CUtensorMap ma, mb;
-  if (!make_map(&ma, A, k, m, lda) || !make_map(&mb, B, k, n, ldb)) return cudaErrorInvalidValue;
-  static bool attr[2] = {false, false};
-  if (!attr[split]) {
-    cudaError_t e = split ? cudaFuncSetAttribute(gemm_tc_tn_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 TcCfg<true>::SMEM)
-                          : cudaFuncSetAttribute(gemm_tc_tn_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 TcCfg<false>::SMEM);
+template <bool SPLIT, bool AMN, bool BMN>
+cudaError_t launch_tc(dim3 grid, cudaStream_t s, const CUtensorMap& ma, const CUtensorMap& mb, int64_t m, int64_t n,
+                      int64_t k, float alpha, float beta, float* D, int64_t ldd, float* part, int64_t kc, int* err) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<SPLIT, AMN, BMN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TcCfg<SPLIT>::SMEM);
     if (e != cudaSuccess) return e;
-    attr[split] = true;
+    attr = true;
   }
+  gemm_tc_kernel<SPLIT, AMN, BMN><<<grid, TcCfg<SPLIT>::NT, TcCfg<SPLIT>::SMEM, s>>>(ma, mb, m, n, k, alpha, beta, D,
+                                                                                    ldd, part, kc, err);
+  return cudaGetLastError();
+}
+
+// D (m x n) = alpha op(A) op(B) + beta D, column-major FP32: op(A) = A^T with
+// A k x m (ta) or A with A m x k; op(B) = B with B k x n (!tb) or B^T with
+// B n x k.  split = true runs the 3xTF32 form (FP32-level products).
+cudaError_t gemm_tc(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, float alpha, const float* A,
+                    int64_t lda, const float* B, int64_t ldb, float beta, float* D, int64_t ldd, float* work,
+                    int64_t work_elems, int* err, bool split) {
+  const bool amn = !ta, bmn = tb;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, amn ? m : k, amn ? k : m, lda, amn) || !make_map(&mb, B, bmn ? n : k, bmn ? k : n, ldb, bmn))
+    return cudaErrorInvalidValue;
   const int64_t tiles = ((m + TC_BM - 1) / TC_BM) * ((n + TC_BN - 1) / TC_BN);
   // split K until the tiles cover the SMs (each CTA uses one SM: >= 130 KB of shared memory)
   int splits = 1;
@@ -362,34 +410,51 @@ cudaError_t gemm_tc_tn(cudaStream_t s, int64_t m, int64_t n, int64_t k, float al
   dim3 grid(static_cast<unsigned>((m + TC_BM - 1) / TC_BM), static_cast<unsigned>((n + TC_BN - 1) / TC_BN),
             static_cast<unsigned>(splits));
   const ProfToken tok = prof_begin(s, kProfGemmTc);
-  if (split)
-    gemm_tc_tn_kernel<true><<<grid, TcCfg<true>::NT, TcCfg<true>::SMEM, s>>>(ma, mb, m, n, k, alpha, beta, D, ldd,
-                                                                            part, kc, err);
-  else
-    gemm_tc_tn_kernel<false><<<grid, TcCfg<false>::NT, TcCfg<false>::SMEM, s>>>(ma, mb, m, n, k, alpha, beta, D,
-                                                                               ldd, part, kc, err);
+  cudaError_t e;
+#define RUTV_TC(S_, A_, B_) e = launch_tc<S_, A_, B_>(grid, s, ma, mb, m, n, k, alpha, beta, D, ldd, part, kc, err)
+  if (split) {
+    if (!amn && !bmn) RUTV_TC(true, false, false);
+    else if (amn && !bmn) RUTV_TC(true, true, false);
+    else if (amn && bmn) RUTV_TC(true, true, true);
+    else RUTV_TC(true, false, true);
+  } else {
+    if (!amn && !bmn) RUTV_TC(false, false, false);
+    else if (amn && !bmn) RUTV_TC(false, true, false);
+    else if (amn && bmn) RUTV_TC(false, true, true);
+    else RUTV_TC(false, false, true);
+  }
+#undef RUTV_TC
   note_launch();
-  cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && splits > 1) e = gemm_f32_reduce(s, m, n, splits, alpha, part, beta, D, ldd);
   prof_end(s, tok, (split ? 3.0 : 1.0) * 2.0 * m * n * k, 4.0 * (m * k + k * n + m * n * (beta != 0.f ? 2.0 : 1.0)));
   return e;
 }
 
+cudaError_t gemm_tc_tn(cudaStream_t s, int64_t m, int64_t n, int64_t k, float alpha, const float* A, int64_t lda,
+                       const float* B, int64_t ldb, float beta, float* D, int64_t ldd, float* work, int64_t work_elems,
+                       int* err, bool split) {
+  return gemm_tc(s, true, false, m, n, k, alpha, A, lda, B, ldb, beta, D, ldd, work, work_elems, err, split);
+}
+
 }  // namespace rutv
 
-extern "C" int randutv_sgemm_tc(int64_t m, int64_t n, int64_t k, float alpha, const float* A, int64_t lda,
-                                const float* B, int64_t ldb, float beta, float* C, int64_t ldc, int passes) {
+extern "C" int randutv_sgemm_tc(char transa, char transb, int64_t m, int64_t n, int64_t k, float alpha,
+                                const float* A, int64_t lda, const float* B, int64_t ldb, float beta, float* C,
+                                int64_t ldc, int passes) {
   using namespace rutv;
-  if (m < 1) return -1;
-  if (n < 1) return -2;
-  if (k < 1) return -3;
-  if (!A) return -5;
-  if (lda < k) return -6;
-  if (!B) return -7;
-  if (ldb < k) return -8;
-  if (!C) return -10;
-  if (ldc < m) return -11;
-  if (passes != 1 && passes != 3) return -12;
+  const bool ta = (transa == 'T' || transa == 't'), tb = (transb == 'T' || transb == 't');
+  if (!ta && transa != 'N' && transa != 'n') return -1;
+  if (!tb && transb != 'N' && transb != 'n') return -2;
+  if (m < 1) return -3;
+  if (n < 1) return -4;
+  if (k < 1) return -5;
+  if (!A) return -7;
+  if (lda < (ta ? k : m)) return -8;
+  if (!B) return -9;
+  if (ldb < (tb ? n : k)) return -10;
+  if (!C) return -12;
+  if (ldc < m) return -13;
+  if (passes != 1 && passes != 3) return -14;
   if (!gemm_tc_supported(A, lda, B, ldb, m, n, k)) {
     set_last_error("randutv_sgemm_tc: operands do not meet the TMA alignment rules");
     return RANDUTV_EUNSUPPORTED;
@@ -403,7 +468,7 @@ extern "C" int randutv_sgemm_tc(int64_t m, int64_t n, int64_t k, float alpha, co
   if (e != cudaSuccess) { cudaGetLastError(); return RANDUTV_ENOMEM; }
   err = reinterpret_cast<int*>(reinterpret_cast<char*>(ws) + we * sizeof(float));
   e = cudaMemsetAsync(err, 0, sizeof(int), s);
-  if (e == cudaSuccess) e = gemm_tc_tn(s, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, we, err, passes == 3);
+  if (e == cudaSuccess) e = gemm_tc(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, we, err, passes == 3);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaError_t e2 = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = e2;

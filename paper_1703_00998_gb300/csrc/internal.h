@@ -54,7 +54,12 @@ cudaError_t gemm_f32_reduce(cudaStream_t s, int64_t m, int64_t n, int splits, fl
 cudaError_t gemm_tc_tn(cudaStream_t s, int64_t m, int64_t n, int64_t k, float alpha, const float* A, int64_t lda,
                        const float* B, int64_t ldb, float beta, float* D, int64_t ldd, float* work, int64_t work_elems,
                        int* err, bool split);
-// Whether gemm_tc_tn can take these operands (TMA alignment rules, driver entry point).
+// D (m x n) = alpha op(A) op(B) + beta D on the tensor cores for any of the
+// four transpose combinations (K-major or MN-major tiles).
+cudaError_t gemm_tc(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, float alpha, const float* A,
+                    int64_t lda, const float* B, int64_t ldb, float beta, float* D, int64_t ldd, float* work,
+                    int64_t work_elems, int* err, bool split);
+// Whether gemm_tc can take these operands (TMA alignment rules, driver entry point).
 bool gemm_tc_supported(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t m, int64_t n, int64_t k);
 
 // ---- philox.cu ----

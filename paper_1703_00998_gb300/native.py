@@ -59,8 +59,8 @@ SIGNATURES = {
                              _vp, _i64]),
     "randutv_sgemm": (_i32, [ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, ctypes.c_float, _vp, _i64, _vp, _i64,
                              ctypes.c_float, _vp, _i64]),
-    "randutv_sgemm_tc": (_i32, [_i64, _i64, _i64, ctypes.c_float, _vp, _i64, _vp, _i64, ctypes.c_float, _vp, _i64,
-                                _i32]),
+    "randutv_sgemm_tc": (_i32, [ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, ctypes.c_float, _vp, _i64, _vp,
+                                _i64, ctypes.c_float, _vp, _i64, _i32]),
     "randutv_panel_qr": (_i32, [_i64, _i64, _vp, _i64, _vp, _vp, _vp]),
     "randutv_small_svd": (_i32, [_i64, _vp, _i64, _vp, _vp, _vp, _i32]),
     "randutv_profile_enable": (_i32, [_i32]),

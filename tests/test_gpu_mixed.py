@@ -38,13 +38,14 @@ def diag_close(d, dref, normA, rel):
     return float(np.max(np.abs(np.abs(d) - np.abs(dref)) / (np.abs(dref) + floor / rel)))
 
 
+@pytest.mark.parametrize("tc", [0, 1])
 @pytest.mark.parametrize("m,n,b,q", [(500, 500, 32, 1), (300, 200, 32, 1), (200, 300, 32, 1), (257, 257, 64, 0),
                                      (1000, 1000, 128, 1)])
-def test_mixed_small_shapes(R, m, n, b, q):
+def test_mixed_small_shapes(R, m, n, b, q, tc):
     A = synth.make_matrix("exp50", m, n, 1703001 + m).astype(np.float32)
     A64 = A.astype(np.float64)
     g = dev(synth.gaussian_stream(SEED, m, n, b)) if synth.stream_layout(m, n, b)[1] > 0 else None
-    out = R.factor_mixed(dev(A), b=b, q=q, g_inject=g)
+    out = R.factor_mixed(dev(A), b=b, q=q, g_inject=g, tensor_cores=tc)
     U, T, V = host(out.U), host(out.T), host(out.V)
     assert out.k_reached == min(m, n)
     res, ou, ov = metrics(A64, U, T, V)
@@ -57,13 +58,14 @@ def test_mixed_small_shapes(R, m, n, b, q):
     assert diag_close(T.diagonal(), To.diagonal(), np.linalg.norm(A64, 2), 1e-4) <= 1e-4
 
 
+@pytest.mark.parametrize("tc", [0, 1])
 @pytest.mark.parametrize("kind", ["exp200", "inv"])
-def test_mixed_n4000_against_fp64_and_oracle(R, kind):
+def test_mixed_n4000_against_fp64(R, kind, tc):
     n, b = 4000, 128
     A64 = synth.make_matrix(kind, n, n, 1703002 + ["exp200", "inv"].index(kind))
     A = A64.astype(np.float32)
     A64 = A.astype(np.float64)
-    out = R.factor_mixed(dev(A), b=b, q=1, seed=SEED)
+    out = R.factor_mixed(dev(A), b=b, q=1, seed=SEED, tensor_cores=tc)
     res, ou, ov = metrics(A64, host(out.U), host(out.T), host(out.V))
     assert res <= 1e-6 and ou <= 1e-6 and ov <= 1e-6, (res, ou, ov)
     f = R.factor(dev(A64), b=b, q=1, seed=SEED)
