@@ -174,8 +174,14 @@ static cudaError_t rot_left_t(cudaStream_t s, int w, int64_t cols, double* X, in
 }
 
 // ------------------------------------------------------------- workspace
+// The reflectors and small-SVD factors of a step live in a ring of
+// Lanes::kSlots slots, so the U/V lane can still be applying step i's while
+// the T lane forms step i+1's; W1u/W2u/tmpu/gwsu are the U/V lane's scratch.
 struct Work {
-  double *G, *Y, *Z, *Vv, *Vu, *tau, *R, *Rt, *gram, *S, *W1, *W2, *Us, *Vs, *d, *tmp;
+  static constexpr int kR = Lanes::kSlots;
+  double *G, *Y, *Z, *tau, *R, *Rt, *gram, *W1, *W2, *d, *tmp;
+  double *Vvr[kR], *Vur[kR], *Svr[kR], *Sur[kR], *Usr[kR], *Vsr[kR];
+  double *W1u, *W2u, *tmpu, *gwsu;
   double *gws, *part, *jws, *red, *scal;
   int64_t gws_elems;
   unsigned* flags;
@@ -189,18 +195,25 @@ static int64_t gemm_budget(int64_t mx, int b) {
   return std::max<int64_t>(24 * mx * b, 64ll * b * b);
 }
 
-static cudaError_t work_alloc(cudaStream_t s, int64_t m, int64_t n, int b, Work* w) {
+static cudaError_t work_alloc(cudaStream_t s, int64_t m, int64_t n, int b, bool uv, Work* w) {
   const int64_t mx = std::max(m, n);
   const int64_t bb = static_cast<int64_t>(b) * b;
+  const int64_t ux = uv ? 1 : 0;   // the U/V lane's scratch only when U and V are formed
   struct Item { double** p; int64_t n; };
   w->gws_elems = gemm_budget(mx, b);
   Item items[] = {
-      {&w->G, m * b}, {&w->Y, n * b}, {&w->Z, m * b}, {&w->Vv, mx * b}, {&w->Vu, mx * b},
-      {&w->tau, b}, {&w->R, bb}, {&w->Rt, bb}, {&w->gram, bb}, {&w->S, bb}, {&w->W1, mx * b},
-      {&w->W2, mx * b}, {&w->Us, bb}, {&w->Vs, bb}, {&w->d, b}, {&w->tmp, mx * b},
+      {&w->G, m * b}, {&w->Y, n * b}, {&w->Z, m * b},
+      {&w->tau, b}, {&w->R, bb}, {&w->Rt, bb}, {&w->gram, bb}, {&w->W1, mx * b},
+      {&w->W2, mx * b}, {&w->d, b}, {&w->tmp, mx * b},
+      {&w->Vvr[0], mx * b}, {&w->Vvr[1], mx * b}, {&w->Vvr[2], mx * b},
+      {&w->Vur[0], mx * b}, {&w->Vur[1], mx * b}, {&w->Vur[2], mx * b},
+      {&w->Svr[0], bb}, {&w->Svr[1], bb}, {&w->Svr[2], bb}, {&w->Sur[0], bb}, {&w->Sur[1], bb}, {&w->Sur[2], bb},
+      {&w->Usr[0], bb}, {&w->Usr[1], bb}, {&w->Usr[2], bb}, {&w->Vsr[0], bb}, {&w->Vsr[1], bb}, {&w->Vsr[2], bb},
+      {&w->W1u, ux * mx * b}, {&w->W2u, ux * mx * b}, {&w->tmpu, ux * mx * b}, {&w->gwsu, ux * w->gws_elems},
       {&w->gws, w->gws_elems}, {&w->part, panel_qr_part_elems(mx, b)}, {&w->jws, jacobi_work_elems(b)},
       {&w->red, kSumsqBlocks}, {&w->scal, 8},
   };
+  static_assert(Work::kR == 3, "ring buffers listed above");
   size_t total = 0;
   for (auto& it : items) total += align_up(static_cast<size_t>(it.n) * sizeof(double));
   total += align_up(4 * kFlagSlots * sizeof(unsigned));
@@ -302,6 +315,7 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
   const bool uv = opts.form_uv != 0;
   cudaStream_t s = g_stream;
   Work w{};
+  Lanes L;
   int st = RANDUTV_OK;
   double h_norm2 = 0.0, normA = 0.0;
   int64_t g_off = 0;
@@ -309,123 +323,158 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
   const int64_t nsteps = std::min((m + b - 1) / b, (n + b - 1) / b);
 
   {
-    cudaError_t e = work_alloc(s, m, n, b, &w);
+    cudaError_t e = work_alloc(s, m, n, b, uv, &w);
     if (e != cudaSuccess) {
       cudaGetLastError();
       snprintf(g_detail, sizeof(g_detail), "workspace: %s", cudaGetErrorString(e));
       return e == cudaErrorMemoryAllocation ? RANDUTV_ENOMEM : RANDUTV_ECUDA;
     }
   }
-  RUTV_CK(copy_matrix(s, m, n, A, lda, T, ldt));
-  if (uv) {
-    RUTV_CK(set_identity(s, m, U, ldu));
-    RUTV_CK(set_identity(s, n, V, ldv));
-  }
-  RUTV_CK(sumsq(s, m, n, T, ldt, w.red, w.scal));
-  RUTV_CK(cudaMemcpyAsync(&h_norm2, w.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
-  RUTV_CK(cudaStreamSynchronize(s));
-  if (!std::isfinite(h_norm2)) { st = RANDUTV_ENAN; goto done; }
-  normA = std::sqrt(h_norm2);
-
-  for (int64_t i = 1; i <= nsteps; ++i) {
-    const int64_t r0 = b * (i - 1);
-    const int64_t r1 = std::min<int64_t>(r0 + b, m), c1 = std::min<int64_t>(r0 + b, n);
-    const int64_t kr = m - r0, kc = n - r0;
-    double* X = T + r0 + r0 * ldt;
-    if (tol > 0.0) {
-      double t2 = 0.0;
-      RUTV_CK(sumsq(s, kr, kc, X, ldt, w.red, w.scal));
-      RUTV_CK(cudaMemcpyAsync(&t2, w.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
-      RUTV_CK(cudaStreamSynchronize(s));
-      if (!std::isfinite(t2)) { st = RANDUTV_ENAN; goto done; }
-      if (std::sqrt(t2) <= tol * normA) { *k_reached = r0; break; }
+  // Two lanes (Section 5.2's transforms applied as soon as formed, split by
+  // what they touch): the T lane (high priority) carries the serial chain
+  // sketch -> QR(Y) -> T right apply -> panel QR -> T left apply -> small
+  // SVD -> T rotations; the U/V lane (low priority) applies each step's
+  // reflectors and rotations to V and U as soon as the T lane has formed
+  // them, filling the SMs that the latency-bound panel QR and Jacobi SVD
+  // leave idle.  No step of the T lane reads U or V, so only the ring slots
+  // order the lanes.  overlap = 0 puts both on the caller's stream.
+  RUTV_CK(L.open(s, opts.overlap != 0 && uv));
+  {
+    cudaStream_t sT = L.t, sU = L.uv;
+    const int64_t ge = w.gws_elems;
+    RUTV_CK(copy_matrix(sT, m, n, A, lda, T, ldt));
+    if (uv) {
+      RUTV_CK(set_identity(sU, m, U, ldu));
+      RUTV_CK(set_identity(sU, n, V, ldv));
     }
-    if (r1 < m && c1 < n) {
-      // ---- randomized step: sketch, QR(Y) -> VV, QR(panel) -> UU, small SVD
-      const double* G = w.G;
-      if (opts.g_inject) {
-        G = opts.g_inject + g_off;
-      } else {
-        RUTV_CK(launch_gaussian(s, opts.seed, i, kr, b, w.G, kr));
-      }
-      g_off += kr * b;
-      RUTV_CK(gemm_f64(s, true, false, kc, b, kr, 1.0, X, ldt, G, kr, 0.0, w.Y, kc, w.gws, w.gws_elems));
-      for (int j = 0; j < q; ++j) {
-        RUTV_CK(gemm_f64(s, false, false, kr, b, kc, 1.0, X, ldt, w.Y, kc, 0.0, w.Z, kr, w.gws, w.gws_elems));
-        RUTV_CK(gemm_f64(s, true, false, kc, b, kr, 1.0, X, ldt, w.Z, kr, 0.0, w.Y, kc, w.gws, w.gws_elems));
-      }
-      RUTV_CK(panel_qr(s, kc, b, w.Y, kc, w.tau, w.Vv, w.Rt, w.part, slot(w, 0)));
-      RUTV_CK(gemm_f64(s, true, false, b, b, kc, 1.0, w.Vv, kc, w.Vv, kc, 0.0, w.gram, b, w.gws, w.gws_elems));
-      RUTV_CK(tfactor_from_gram(s, b, w.gram, w.tau, w.S));
-      RUTV_CK(wy_right(s, m, kc, T + r0 * ldt, ldt, w.Vv, w.S, b, w.W1, w.W2, w.gws, w.gws_elems));
-      if (uv) RUTV_CK(wy_right(s, n, kc, V + r0 * ldv, ldv, w.Vv, w.S, b, w.W1, w.W2, w.gws, w.gws_elems));
+    RUTV_CK(sumsq(sT, m, n, T, ldt, w.red, w.scal));
+    RUTV_CK(cudaMemcpyAsync(&h_norm2, w.scal, sizeof(double), cudaMemcpyDeviceToHost, sT));
+    RUTV_CK(cudaStreamSynchronize(sT));
+    if (!std::isfinite(h_norm2)) { st = RANDUTV_ENAN; goto done; }
+    normA = std::sqrt(h_norm2);
 
-      RUTV_CK(panel_qr(s, kr, b, X, ldt, w.tau, w.Vu, w.R, w.part, slot(w, 1)));
-      RUTV_CK(gemm_f64(s, true, false, b, b, kr, 1.0, w.Vu, kr, w.Vu, kr, 0.0, w.gram, b, w.gws, w.gws_elems));
-      RUTV_CK(tfactor_from_gram(s, b, w.gram, w.tau, w.S));
-      if (uv) RUTV_CK(wy_right(s, m, kr, U + r0 * ldu, ldu, w.Vu, w.S, b, w.W1, w.W2, w.gws, w.gws_elems));
-      RUTV_CK(wy_left_t(s, kr, kc - b, T + r0 + c1 * ldt, ldt, w.Vu, w.S, b, w.W1, w.W2, w.gws, w.gws_elems));
-      RUTV_CK(fill(s, kr, b, X, ldt, 0.0));
+    for (int64_t i = 1; i <= nsteps; ++i) {
+      const int64_t r0 = b * (i - 1);
+      const int64_t r1 = std::min<int64_t>(r0 + b, m), c1 = std::min<int64_t>(r0 + b, n);
+      const int64_t kr = m - r0, kc = n - r0;
+      const int sl = static_cast<int>((i - 1) % Work::kR);
+      double* X = T + r0 + r0 * ldt;
+      if (tol > 0.0) {
+        double t2 = 0.0;
+        RUTV_CK(sumsq(sT, kr, kc, X, ldt, w.red, w.scal));
+        RUTV_CK(cudaMemcpyAsync(&t2, w.scal, sizeof(double), cudaMemcpyDeviceToHost, sT));
+        RUTV_CK(cudaStreamSynchronize(sT));
+        if (!std::isfinite(t2)) { st = RANDUTV_ENAN; goto done; }
+        if (std::sqrt(t2) <= tol * normA) { *k_reached = r0; break; }
+      }
+      // this step's ring slot is free once the U/V lane has finished step i - kR
+      if (i > Work::kR) RUTV_CK(cudaStreamWaitEvent(sT, L.done[sl], 0));
+      double *Vv = w.Vvr[sl], *Vu = w.Vur[sl], *Sv = w.Svr[sl], *Su = w.Sur[sl], *Us = w.Usr[sl], *Vs = w.Vsr[sl];
+      if (r1 < m && c1 < n) {
+        // ---- randomized step: sketch, QR(Y) -> VV, QR(panel) -> UU, small SVD
+        const double* G = w.G;
+        if (opts.g_inject) {
+          G = opts.g_inject + g_off;
+        } else {
+          RUTV_CK(launch_gaussian(sT, opts.seed, i, kr, b, w.G, kr));
+        }
+        g_off += kr * b;
+        RUTV_CK(gemm_f64(sT, true, false, kc, b, kr, 1.0, X, ldt, G, kr, 0.0, w.Y, kc, w.gws, ge));
+        for (int j = 0; j < q; ++j) {
+          RUTV_CK(gemm_f64(sT, false, false, kr, b, kc, 1.0, X, ldt, w.Y, kc, 0.0, w.Z, kr, w.gws, ge));
+          RUTV_CK(gemm_f64(sT, true, false, kc, b, kr, 1.0, X, ldt, w.Z, kr, 0.0, w.Y, kc, w.gws, ge));
+        }
+        RUTV_CK(panel_qr(sT, kc, b, w.Y, kc, w.tau, Vv, w.Rt, w.part, slot(w, 0)));
+        RUTV_CK(gemm_f64(sT, true, false, b, b, kc, 1.0, Vv, kc, Vv, kc, 0.0, w.gram, b, w.gws, ge));
+        RUTV_CK(tfactor_from_gram(sT, b, w.gram, w.tau, Sv));
+        RUTV_CK(cudaEventRecord(L.v[sl], sT));
+        RUTV_CK(wy_right(sT, m, kc, T + r0 * ldt, ldt, Vv, Sv, b, w.W1, w.W2, w.gws, ge));
+        if (uv) {
+          RUTV_CK(cudaStreamWaitEvent(sU, L.v[sl], 0));
+          RUTV_CK(wy_right(sU, n, kc, V + r0 * ldv, ldv, Vv, Sv, b, w.W1u, w.W2u, w.gwsu, ge));
+        }
 
-      RUTV_CK(jacobi_svd(s, b, w.R, b, w.Us, w.d, w.Vs, opts.max_sweeps, w.jws, slot(w, 2)));
-      set_diag_kernel<<<(b + 127) / 128, 128, 0, s>>>(b, w.d, X, ldt);
-      note_launch();
-      RUTV_CK(cudaGetLastError());
-      RUTV_CK(rot_left_t(s, b, kc - b, T + r0 + c1 * ldt, ldt, w.Us, w.tmp, w.gws, w.gws_elems));
-      RUTV_CK(rot_right(s, r0, b, T + r0 * ldt, ldt, w.Vs, w.tmp, w.gws, w.gws_elems));
-      if (uv) {
-        RUTV_CK(rot_right(s, m, b, U + r0 * ldu, ldu, w.Us, w.tmp, w.gws, w.gws_elems));
-        RUTV_CK(rot_right(s, n, b, V + r0 * ldv, ldv, w.Vs, w.tmp, w.gws, w.gws_elems));
-      }
-    } else {
-      // ---- last block: full SVD, economically through a QR when not square
-      int p;
-      const double* core;
-      int64_t ldcore;
-      if (kr >= kc) {
-        // QR first, also for a square block: one-sided Jacobi converges in a
-        // few sweeps on the rows of a triangular R, far more slowly on a
-        // general dense block of high condition number
-        p = static_cast<int>(kc);
-        RUTV_CK(panel_qr(s, kr, p, X, ldt, w.tau, w.Vu, w.R, w.part, slot(w, 1)));
-        RUTV_CK(gemm_f64(s, true, false, p, p, kr, 1.0, w.Vu, kr, w.Vu, kr, 0.0, w.gram, p, w.gws, w.gws_elems));
-        RUTV_CK(tfactor_from_gram(s, p, w.gram, w.tau, w.S));
-        if (uv) RUTV_CK(wy_right(s, m, kr, U + r0 * ldu, ldu, w.Vu, w.S, p, w.W1, w.W2, w.gws, w.gws_elems));
-        core = w.R;
-        ldcore = p;
+        RUTV_CK(panel_qr(sT, kr, b, X, ldt, w.tau, Vu, w.R, w.part, slot(w, 1)));
+        RUTV_CK(gemm_f64(sT, true, false, b, b, kr, 1.0, Vu, kr, Vu, kr, 0.0, w.gram, b, w.gws, ge));
+        RUTV_CK(tfactor_from_gram(sT, b, w.gram, w.tau, Su));
+        if (uv) {
+          RUTV_CK(cudaEventRecord(L.u[sl], sT));
+          RUTV_CK(cudaStreamWaitEvent(sU, L.u[sl], 0));
+          RUTV_CK(wy_right(sU, m, kr, U + r0 * ldu, ldu, Vu, Su, b, w.W1u, w.W2u, w.gwsu, ge));
+        }
+        RUTV_CK(wy_left_t(sT, kr, kc - b, T + r0 + c1 * ldt, ldt, Vu, Su, b, w.W1, w.W2, w.gws, ge));
+        RUTV_CK(fill(sT, kr, b, X, ldt, 0.0));
+
+        RUTV_CK(jacobi_svd(sT, b, w.R, b, Us, w.d, Vs, opts.max_sweeps, w.jws, slot(w, 2)));
+        set_diag_kernel<<<(b + 127) / 128, 128, 0, sT>>>(b, w.d, X, ldt);
+        note_launch();
+        RUTV_CK(cudaGetLastError());
+        if (uv) {
+          RUTV_CK(cudaEventRecord(L.s[sl], sT));
+          RUTV_CK(cudaStreamWaitEvent(sU, L.s[sl], 0));
+          RUTV_CK(rot_right(sU, m, b, U + r0 * ldu, ldu, Us, w.tmpu, w.gwsu, ge));
+          RUTV_CK(rot_right(sU, n, b, V + r0 * ldv, ldv, Vs, w.tmpu, w.gwsu, ge));
+        }
+        RUTV_CK(rot_left_t(sT, b, kc - b, T + r0 + c1 * ldt, ldt, Us, w.tmp, w.gws, ge));
+        RUTV_CK(rot_right(sT, r0, b, T + r0 * ldt, ldt, Vs, w.tmp, w.gws, ge));
       } else {
-        p = static_cast<int>(kr);
-        RUTV_CK(transpose(s, kr, kc, X, ldt, w.W1, kc));
-        RUTV_CK(panel_qr(s, kc, p, w.W1, kc, w.tau, w.Vv, w.Rt, w.part, slot(w, 0)));
-        RUTV_CK(gemm_f64(s, true, false, p, p, kc, 1.0, w.Vv, kc, w.Vv, kc, 0.0, w.gram, p, w.gws, w.gws_elems));
-        RUTV_CK(tfactor_from_gram(s, p, w.gram, w.tau, w.S));
-        RUTV_CK(wy_right(s, m, kc, T + r0 * ldt, ldt, w.Vv, w.S, p, w.W2, w.tmp, w.gws, w.gws_elems));
-        if (uv) RUTV_CK(wy_right(s, n, kc, V + r0 * ldv, ldv, w.Vv, w.S, p, w.W2, w.tmp, w.gws, w.gws_elems));
-        RUTV_CK(transpose(s, p, p, w.Rt, p, w.R, p));
-        core = w.R;
-        ldcore = p;
+        // ---- last block: full SVD, economically through a QR when not square
+        int p;
+        if (kr >= kc) {
+          // QR first, also for a square block: one-sided Jacobi converges in a
+          // few sweeps on the rows of a triangular R, far more slowly on a
+          // general dense block of high condition number
+          p = static_cast<int>(kc);
+          RUTV_CK(panel_qr(sT, kr, p, X, ldt, w.tau, Vu, w.R, w.part, slot(w, 1)));
+          RUTV_CK(gemm_f64(sT, true, false, p, p, kr, 1.0, Vu, kr, Vu, kr, 0.0, w.gram, p, w.gws, ge));
+          RUTV_CK(tfactor_from_gram(sT, p, w.gram, w.tau, Su));
+          if (uv) {
+            RUTV_CK(cudaEventRecord(L.u[sl], sT));
+            RUTV_CK(cudaStreamWaitEvent(sU, L.u[sl], 0));
+            RUTV_CK(wy_right(sU, m, kr, U + r0 * ldu, ldu, Vu, Su, p, w.W1u, w.W2u, w.gwsu, ge));
+          }
+        } else {
+          p = static_cast<int>(kr);
+          RUTV_CK(transpose(sT, kr, kc, X, ldt, w.W1, kc));
+          RUTV_CK(panel_qr(sT, kc, p, w.W1, kc, w.tau, Vv, w.Rt, w.part, slot(w, 0)));
+          RUTV_CK(gemm_f64(sT, true, false, p, p, kc, 1.0, Vv, kc, Vv, kc, 0.0, w.gram, p, w.gws, ge));
+          RUTV_CK(tfactor_from_gram(sT, p, w.gram, w.tau, Sv));
+          RUTV_CK(wy_right(sT, m, kc, T + r0 * ldt, ldt, Vv, Sv, p, w.W2, w.tmp, w.gws, ge));
+          if (uv) {
+            RUTV_CK(cudaEventRecord(L.v[sl], sT));
+            RUTV_CK(cudaStreamWaitEvent(sU, L.v[sl], 0));
+            RUTV_CK(wy_right(sU, n, kc, V + r0 * ldv, ldv, Vv, Sv, p, w.W1u, w.W2u, w.gwsu, ge));
+          }
+          RUTV_CK(transpose(sT, p, p, w.Rt, p, w.R, p));
+        }
+        RUTV_CK(jacobi_svd(sT, p, w.R, p, Us, w.d, Vs, opts.max_sweeps, w.jws, slot(w, 2)));
+        RUTV_CK(fill(sT, kr, kc, X, ldt, 0.0));
+        set_diag_kernel<<<(p + 127) / 128, 128, 0, sT>>>(p, w.d, X, ldt);
+        note_launch();
+        RUTV_CK(cudaGetLastError());
+        if (uv) {
+          RUTV_CK(cudaEventRecord(L.s[sl], sT));
+          RUTV_CK(cudaStreamWaitEvent(sU, L.s[sl], 0));
+          RUTV_CK(rot_right(sU, m, p, U + r0 * ldu, ldu, Us, w.tmpu, w.gwsu, ge));
+          RUTV_CK(rot_right(sU, n, p, V + r0 * ldv, ldv, Vs, w.tmpu, w.gwsu, ge));
+        }
+        RUTV_CK(rot_right(sT, r0, p, T + r0 * ldt, ldt, Vs, w.tmp, w.gws, ge));
       }
-      RUTV_CK(jacobi_svd(s, p, core, ldcore, w.Us, w.d, w.Vs, opts.max_sweeps, w.jws, slot(w, 2)));
-      RUTV_CK(fill(s, kr, kc, X, ldt, 0.0));
-      set_diag_kernel<<<(p + 127) / 128, 128, 0, s>>>(p, w.d, X, ldt);
-      note_launch();
-      RUTV_CK(cudaGetLastError());
-      RUTV_CK(rot_right(s, r0, p, T + r0 * ldt, ldt, w.Vs, w.tmp, w.gws, w.gws_elems));
-      if (uv) {
-        RUTV_CK(rot_right(s, m, p, U + r0 * ldu, ldu, w.Us, w.tmp, w.gws, w.gws_elems));
-        RUTV_CK(rot_right(s, n, p, V + r0 * ldv, ldv, w.Vs, w.tmp, w.gws, w.gws_elems));
-      }
+      if (uv) RUTV_CK(cudaEventRecord(L.done[sl], sU));
     }
   }
+  RUTV_CK(L.join(s));
   RUTV_CK(cudaStreamSynchronize(s));
   st = device_status(w);
   if (prof_enabled()) prof_flush();
 
 done:
+  L.join(s);
   if (w.base) {
     cudaFreeAsync(w.base, s);
     cudaStreamSynchronize(s);
   }
+  L.close();
   return st;
 }
 

@@ -207,3 +207,14 @@ def test_n8000_closed_forms(R):
     s = synth.spectrum("inv", n)
     assert abs(float(torch.linalg.norm(out.T)) / np.linalg.norm(s) - 1) <= 1e-13
     assert float(torch.tril(out.T, -1).abs().max()) == 0.0
+
+
+def test_fp64_overlap_off_matches(R):
+    # the U/V lane only reorders independent work: the same factors either
+    # way, up to the run-to-run rounding of the panel QR's atomic sums
+    A = synth.make_matrix("exp50", 600, 600, 31)
+    g = dev(synth.gaussian_stream(SEED, 600, 600, 64))
+    a = R.factor(dev(A), b=64, q=1, g_inject=g, overlap=True)
+    c = R.factor(dev(A), b=64, q=1, g_inject=g, overlap=False)
+    for x, y in ((a.T, c.T), (a.U, c.U), (a.V, c.V)):
+        assert float((x - y).abs().max()) <= 1e-10
