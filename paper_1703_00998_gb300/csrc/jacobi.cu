@@ -8,15 +8,19 @@
 // columns N, i.e. M = Q diag(sigma) N^T: Us = Q, Vs = N.  Working on the rows
 // matters for the upper triangular R11 of randUTV: its columns are graded
 // like its singular values and one-sided Jacobi on them converges several
-// times more slowly than on its rows.  The p(p-1)/2 pairs of a sweep are
-// ordered as a round-robin tournament: p-1 rounds of p/2 disjoint pairs.
+// times more slowly than on its rows.  Every sweep visits each of the
+// p(p-1)/2 pairs once.
 //
 // GB300 design: FP64 runs at ~4 flop/clk/SM, so one SM would need tens of
 // milliseconds for a 128 x 128 SVD.  One thread-block cluster of 16 CTAs
-// (16 SMs) holds W and Q in distributed shared memory (2 p^2 doubles spread
-// over the 16 CTAs), each warp rotates one pair of a round at a time through
-// DSMEM loads and stores, and the hardware cluster barrier separates the
-// rounds: no global-memory round trips and no software grid barrier.
+// (16 SMs) holds W and Q in shared memory, and the pairs are visited in a
+// block-cyclic order (blocks of columns play a round-robin tournament, two
+// blocks per CTA; see the block layout below): each CTA rotates the pairs of
+// its two blocks in local shared memory, separated by __syncthreads, and the
+// hardware cluster barrier is needed only once per round of blocks (P - 1 = 31
+// per sweep instead of p - 1 = 127), when each CTA passes a block to its
+// neighbour through distributed shared memory.  No global-memory round trips
+// and no software grid barrier.
 // Order and signs: singular values descending (stable in the column index);
 // the largest-|.| entry of each Vs column positive (lowest index on ties),
 // Us flipped with it; zero singular values get Vs columns that complete an
@@ -32,14 +36,26 @@ constexpr int JC_CLUSTER = 16;   // CTAs of the cluster (non-portable size, opt-
 constexpr int JC_NT = 128;       // 4 warps per CTA, one pair per warp at a time
 constexpr int JC_WARPS = JC_NT / 32;
 constexpr int JC_MAXP = 256;
+constexpr size_t kJcSmemLimit = 226 * 1024;   // dynamic; the static arrays need the rest of 227 KB
 
-// dynamic shared memory of one CTA: W and Q slots (p doubles each) + norms
-__host__ __device__ constexpr size_t jc_smem(int p, int cs) {
-  return (2ull * ((p + (p & 1) + cs - 1) / cs) * p + ((p + (p & 1) + cs - 1) / cs)) * sizeof(double);
-}
-constexpr size_t kJcSmemMax = jc_smem(JC_MAXP, 8);
-__host__ __device__ constexpr size_t jc_smem32(int p, int cs) {
-  return (2ull * ((p + (p & 1) + cs - 1) / cs) * p + ((p + (p & 1) + cs - 1) / cs)) * sizeof(float);
+// Block layout.  The p columns (padded with zero columns) form P = 2 cs
+// blocks of bs = ceil(p / P) consecutive columns; column c is entry c % bs of
+// block c / bs.  The blocks play a round-robin tournament: P - 1 rounds, in
+// each of which the cs CTAs of the cluster host P / 2 disjoint block pairs.
+// CTA k hosts the players at positions k (its top seat) and P - 1 - k (its
+// bottom seat); between rounds every player but the one at position 0 moves
+// one position down the cycle 1, 2, ..., P - 1 (so after P - 1 rounds every
+// block is home again).  Within a round a CTA rotates all bs^2 column pairs
+// across its two blocks in bs sub-rounds of bs disjoint pairs, separated by
+// __syncthreads only; in round 0 it first rotates the pairs inside each of
+// its two blocks.  Every column pair meets exactly once per sweep, as in the
+// plain cyclic order, but the cluster synchronises only once per round.
+// Each seat holds bs columns of W and of Q (p entries each) and their
+// squared norms; a seat moves to the next CTA by distributed-shared-memory
+// stores into that CTA's second buffer, and the buffers swap every round.
+__host__ __device__ constexpr int jb_bs(int p, int cs) { return (p + 2 * cs - 1) / (2 * cs); }
+__host__ __device__ constexpr size_t jb_smem(int p, int cs, size_t real_bytes) {
+  return (8ull * jb_bs(p, cs) * p + 4ull * jb_bs(p, cs)) * real_bytes;
 }
 
 __device__ __forceinline__ void rr_pair(int pp, int r, int kpair, int* a, int* b) {
@@ -49,60 +65,248 @@ __device__ __forceinline__ void rr_pair(int pp, int r, int kpair, int* a, int* b
   *b = max(x, y);
 }
 
-// One cluster of cs CTAs (16, or 8 where 16 cannot be scheduled).  Column c
-// of W (= M^T, rotated) and of Q (accumulated rotations) lives in the shared
-// memory of CTA c % cs, slot c / cs, with its squared norm; a warp that
-// rotates the pair (i, j) reads and writes both columns through distributed
-// shared memory, and the rounds are separated by the cluster barrier.  The
-// epilogue writes the ordered, signed Us, d and Vs.
-//
-// FP64 issues at 2 lanes/clk/SM on this GPU, so every FP64 instruction of a
-// warp costs its SM sub-partition ~64 cycles; the kernel keeps their number
-// per rotation small: NU = ceil(p/32) rows per lane exactly, one dot product
-// per pair (the squared column norms are carried along with the exact norm
-// formulas of the applied rotation and recomputed at every sweep), and the
-// rotation angle t from FP32 arithmetic.  The rotation itself is exactly
-// orthogonal in FP64 (c = 1/sqrt(1 + t^2), s = c t), so an FP32 angle only
-// changes how much of w_i . w_j a rotation removes, not the accuracy of W, Q.
+// Home seat of block B (its place at the start of every sweep).
+__device__ __forceinline__ void jb_home(int B, int cs, int* cta, int* seat) {
+  if (B < cs) { *cta = B; *seat = 0; }
+  else { *cta = 2 * cs - 1 - B; *seat = 1; }
+}
+
+template <typename Real>
+struct JbSeats {
+  Real* base;   // [buf][seat][bs][2p]: W column then Q column
+  Real* nrm;    // [buf][seat][bs]
+  int p, bs;
+  __device__ Real* w(int buf, int seat, int i) const {
+    return base + (static_cast<size_t>((buf * 2 + seat) * bs + i)) * 2 * p;
+  }
+  __device__ Real* q(int buf, int seat, int i) const { return w(buf, seat, i) + p; }
+  __device__ Real* n(int buf, int seat, int i) const { return nrm + (buf * 2 + seat) * bs + i; }
+};
+
+// Rotation angle t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (b - a) / (2 g).
+// FP64 columns: zeta from FP32 arithmetic after an exact power-of-two scaling
+// of (b - a) and g into [-2, 2] (blocks at the rounding level have
+// w_i . w_j ~ 1e-46, below the FP32 range), FP64 where that still fails.  The
+// rotation itself is exactly orthogonal in the columns' precision
+// (c = 1/sqrt(1 + t^2), s = c t), so an FP32 angle only changes how much of
+// w_i . w_j a rotation removes, not the accuracy of W and Q.
+__device__ __forceinline__ double jb_angle(double a, double b, double g) {
+  const double dba = b - a;
+  const double mx = fmax(fabs(dba), fabs(g));
+  const long long ex = (__double_as_longlong(mx) >> 52) & 0x7ff;
+  bool fp32_ok = ex > 0 && ex < 2046;
+  float zf = 0.f;
+  if (fp32_ok) {
+    const double sc = __longlong_as_double(static_cast<long long>(2046 - ex) << 52);   // 2^(1023 - ex)
+    const float bf = static_cast<float>(dba * sc);
+    const float gf = static_cast<float>(g * sc);
+    fp32_ok = fabsf(gf) >= 0x1p-100f;
+    if (fp32_ok) zf = bf / (2.0f * gf);
+  }
+  if (fp32_ok) {
+    // for |zeta| > 2^60, zeta^2 would overflow: t -> 1 / (2 zeta)
+    const float tf = (fabsf(zf) > 0x1p60f) ? 0.5f / zf
+                                            : copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)));
+    return static_cast<double>(tf);
+  }
+  const double zeta = (b - a) / (2.0 * g);   // rare: outside the FP32 range
+  return (fabs(zeta) > 0x1p500) ? 0.5 / zeta : copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+}
+
+__device__ __forceinline__ float jb_angle(float a, float b, float g) {
+  const float zf = (b - a) / (2.0f * g);
+  return (fabsf(zf) > 0x1p60f) ? 0.5f / zf : copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)));
+}
+
+__device__ __forceinline__ double jb_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float jb_rsqrt(float x) { return rsqrtf(x); }
+
+template <typename Real>
+__device__ __forceinline__ Real jb_warp_sum(Real v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One warp rotates the local column pair (wi, wj) with (qi, qj) and the
+// squared norms *ni, *nj, unless the pair is already orthogonal to the
+// tolerance (|w_i . w_j| <= tol ||w_i|| ||w_j||) or a column is at the
+// rounding level of the block (||w||^2 <= thr2).  Each lane owns NU = ceil(p/32)
+// rows; one dot product per pair: the squared norms are carried along with
+// the exact norm formulas of the applied rotation (recomputed every sweep).
+// Returns whether a rotation was applied (identical in all lanes).
+template <typename Real, int NU>
+__device__ __forceinline__ bool jb_rotate(int p, int lane, Real* wi, Real* wj, Real* qi, Real* qj, Real* ni,
+                                          Real* nj, Real thr2, Real tol2) {
+  Real x[NU], y[NU], q1[NU], q2[NU];
+  Real g = 0;
+#pragma unroll
+  for (int u = 0; u < NU; ++u) {
+    const int t = lane + 32 * u;
+    x[u] = (t < p) ? wi[t] : Real(0);
+    y[u] = (t < p) ? wj[t] : Real(0);
+    q1[u] = (t < p) ? qi[t] : Real(0);
+    q2[u] = (t < p) ? qj[t] : Real(0);
+    g = fma(x[u], y[u], g);
+  }
+  const Real a = *ni, b = *nj;
+  g = jb_warp_sum(g);   // identical in every lane
+  if (g == Real(0) || a <= thr2 || b <= thr2 || !(g * g > tol2 * a * b)) return false;
+  const Real tt = jb_angle(a, b, g);
+  const Real c = jb_rsqrt(fma(tt, tt, Real(1)));
+  const Real sn = c * tt;
+#pragma unroll
+  for (int u = 0; u < NU; ++u) {
+    const int t = lane + 32 * u;
+    if (t < p) {
+      wi[t] = fma(c, x[u], -sn * y[u]);
+      wj[t] = fma(sn, x[u], c * y[u]);
+      qi[t] = fma(c, q1[u], -sn * q2[u]);
+      qj[t] = fma(sn, q1[u], c * q2[u]);
+    }
+  }
+  __syncwarp();
+  if (lane == 0) {
+    const Real cc = c * c, ss = sn * sn, csg = Real(2) * c * sn * g;
+    *ni = fma(cc, a, fma(ss, b, -csg));
+    *nj = fma(ss, a, fma(cc, b, csg));
+  }
+  return true;
+}
+
+// The sweeps of the block-cyclic order on the seats of this CTA (buffer
+// *cur at entry and exit).  Returns whether the last sweep converged (the
+// same in every CTA).
+template <typename Real, int NU>
+__device__ bool jb_sweeps(const JbSeats<Real>& S, int* cur_io, int p, int cs, int rank, int max_sweeps, Real thr2,
+                          Real tol2, int* s_flag) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int bs = S.bs, P = 2 * cs;
+  const int bsp = bs + (bs & 1);
+  int cur = *cur_io;
+  bool converged = false;
+  for (int sw = 0; sw < max_sweeps && !converged; ++sw) {
+    // exact squared norms of this CTA's columns at the start of the sweep
+    for (int e = warp; e < 2 * bs; e += JC_WARPS) {
+      const Real* w = S.w(cur, e / bs, e % bs);
+      Real f = 0;
+      for (int t = lane; t < p; t += 32) f = fma(w[t], w[t], f);
+      f = jb_warp_sum(f);
+      if (lane == 0) *S.n(cur, e / bs, e % bs) = f;
+    }
+    if (tid == 0) s_flag[sw & 1] = 0;
+    bool rotated = false;
+    __syncthreads();
+    for (int r = 0; r < P - 1; ++r) {
+      if (r == 0 && bs > 1) {
+        // pairs inside each of the two blocks: bsp - 1 sub-rounds
+        for (int sub = 0; sub < bsp - 1; ++sub) {
+          for (int kk = warp; kk < bsp; kk += JC_WARPS) {
+            const int seat = kk / (bsp / 2), kp = kk % (bsp / 2);
+            int a, b;
+            rr_pair(bsp, sub, kp, &a, &b);
+            if (b >= bs) continue;
+            rotated |= jb_rotate<Real, NU>(p, lane, S.w(cur, seat, a), S.w(cur, seat, b), S.q(cur, seat, a),
+                                           S.q(cur, seat, b), S.n(cur, seat, a), S.n(cur, seat, b), thr2, tol2);
+          }
+          __syncthreads();
+        }
+      }
+      // pairs across the two blocks: bs sub-rounds of bs disjoint pairs
+      for (int sub = 0; sub < bs; ++sub) {
+        for (int i = warp; i < bs; i += JC_WARPS) {
+          const int j = (i + sub) % bs;
+          rotated |= jb_rotate<Real, NU>(p, lane, S.w(cur, 0, i), S.w(cur, 1, j), S.q(cur, 0, i), S.q(cur, 1, j),
+                                         S.n(cur, 0, i), S.n(cur, 1, j), thr2, tol2);
+        }
+        __syncthreads();
+      }
+      // move the seats (top: k -> k-1, k = 1 -> bottom of 0, k = 0 stays;
+      // bottom: k -> k+1, k = cs-1 -> its own top) into the other buffer
+      const int nx = cur ^ 1;
+      int dt_cta, dt_seat, db_cta, db_seat;
+      if (rank == 0) { dt_cta = 0; dt_seat = 0; }
+      else if (rank == 1) { dt_cta = 0; dt_seat = 1; }
+      else { dt_cta = rank - 1; dt_seat = 0; }
+      if (rank < cs - 1) { db_cta = rank + 1; db_seat = 1; }
+      else { db_cta = rank; db_seat = 0; }
+      Real* dt = cluster.map_shared_rank(S.w(nx, dt_seat, 0), dt_cta);
+      Real* db = cluster.map_shared_rank(S.w(nx, db_seat, 0), db_cta);
+      Real* dtn = cluster.map_shared_rank(S.n(nx, dt_seat, 0), dt_cta);
+      Real* dbn = cluster.map_shared_rank(S.n(nx, db_seat, 0), db_cta);
+      const Real* st = S.w(cur, 0, 0);
+      const Real* sb = S.w(cur, 1, 0);
+      const int len = bs * 2 * p;
+      for (int e = tid; e < len; e += JC_NT) {
+        dt[e] = st[e];
+        db[e] = sb[e];
+      }
+      if (tid < bs) {
+        dtn[tid] = *S.n(cur, 0, tid);
+        dbn[tid] = *S.n(cur, 1, tid);
+      }
+      cur = nx;
+      cluster.sync();
+    }
+    // a sweep without rotations anywhere in the cluster: converged
+    if (rotated) s_flag[sw & 1] = 1;   // benign race: every writer stores 1
+    cluster.sync();
+    int any = 0;
+    for (int q = 0; q < cs; ++q) any |= *cluster.map_shared_rank(&s_flag[sw & 1], q);
+    converged = (any == 0);
+  }
+  *cur_io = cur;
+  return converged;
+}
+
+// FP64 sweeps, then the epilogue on the 16 SMs: sigma_c = ||w_c||, the order
+// (descending, stable in c), Vs = w / sigma, Us = Q, each pair signed so
+// that the largest-|.| entry of its Vs column is positive (lowest index on
+// ties).  sigma at the rounding level of the block (<= p u ||M||_F) counts as
+// zero; those Vs columns are left zero and the completion kernel fills them.
+// Start: W(:, c) = M(c, :)^T and Q = I, or W0 = M^T Q0 (p x p, ld p) after
+// the FP32 sweeps.
 template <int NU>
-__global__ void __launch_bounds__(JC_NT)
-jacobi_cluster_kernel(int p, const double* __restrict__ M, int64_t ldm, const double* W0, const double* Q0,
+__global__ void __launch_bounds__(JC_NT, 1)
+jacobi_block64_kernel(int p, const double* __restrict__ M, int64_t ldm, const double* W0, const double* Q0,
                       double* __restrict__ Us, double* __restrict__ d, double* __restrict__ Vs, int max_sweeps,
                       double tol, int* __restrict__ err, int* __restrict__ zero_flag) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ double jsm[];
   const int rank = static_cast<int>(cluster.block_rank());
-  const int cs = static_cast<int>(cluster.num_blocks());   // 16, or 8 where 16 cannot be scheduled
-  const int pp = p + (p & 1);
-  const int slots = (pp + cs - 1) / cs;
-  double* Wl = jsm;                                    // slots x p
-  double* Ql = jsm + static_cast<size_t>(slots) * p;   // slots x p
-  double* Nl = Ql + static_cast<size_t>(slots) * p;    // slots: squared norms of the W columns
+  const int cs = static_cast<int>(cluster.num_blocks());
+  const int bs = jb_bs(p, cs);
+  JbSeats<double> S{jsm, jsm + 8ull * bs * p, p, bs};
   __shared__ double s_part[JC_CLUSTER];
   __shared__ double s_fro;
   __shared__ int s_flag[2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  // Load this CTA's columns: W(:, c) = M(c, :)^T and Q = I, or the given
-  // starting point W0 = M^T Q0 (p x p, ld p) after the FP32 sweeps.
-  for (int sl = 0; sl < slots; ++sl) {
-    const int c = sl * cs + rank;
-    for (int t = tid; t < p; t += JC_NT) {
-      if (W0) {
-        Wl[sl * p + t] = (c < p) ? W0[t + static_cast<int64_t>(c) * p] : 0.0;
-        Ql[sl * p + t] = (c < p) ? Q0[t + static_cast<int64_t>(c) * p] : 0.0;
-      } else {
-        Wl[sl * p + t] = (c < p) ? M[c + static_cast<int64_t>(t) * ldm] : 0.0;
-        Ql[sl * p + t] = (c < p && t == c) ? 1.0 : 0.0;
+  // this CTA's two home blocks: rank (top) and 2 cs - 1 - rank (bottom)
+  for (int seat = 0; seat < 2; ++seat) {
+    const int B = seat == 0 ? rank : 2 * cs - 1 - rank;
+    for (int i = 0; i < bs; ++i) {
+      const int c = B * bs + i;
+      double* w = S.w(0, seat, i);
+      double* q = S.q(0, seat, i);
+      for (int t = tid; t < p; t += JC_NT) {
+        if (c >= p) { w[t] = 0.0; q[t] = 0.0; }
+        else if (W0) { w[t] = W0[t + static_cast<int64_t>(c) * p]; q[t] = Q0[t + static_cast<int64_t>(c) * p]; }
+        else { w[t] = M[c + static_cast<int64_t>(t) * ldm]; q[t] = (t == c) ? 1.0 : 0.0; }
       }
     }
   }
   __syncthreads();
-  // ||M||_F^2, summed in the same order by every CTA.
+  // ||M||_F^2, summed in the same order by every CTA
   if (warp == 0) {
     double f = 0.0;
-    for (int e = lane; e < slots * p; e += 32) f = fma(Wl[e], Wl[e], f);
+    for (int e = 0; e < 2 * bs; ++e) {
+      const double* w = S.w(0, e / bs, e % bs);
+      for (int t = lane; t < p; t += 32) f = fma(w[t], w[t], f);
+    }
     f = warp_sum(f);
     if (lane == 0) s_part[rank] = f;
   }
@@ -114,134 +318,42 @@ jacobi_cluster_kernel(int p, const double* __restrict__ M, int64_t ldm, const do
     s_fro = f;
   }
   __syncthreads();
-  // Columns with ||w|| <= p u ||M||_F are at the rounding level of the block
-  // and count as zero (rotating them only stirs rounding noise).
+  // columns with ||w|| <= p u ||M||_F are at the rounding level of the block
+  // and count as zero (rotating them only stirs rounding noise)
   const double pu = static_cast<double>(p) * 0x1p-53;
   const double thr2 = pu * pu * s_fro;
-  const double tol2 = tol * tol;
-  const int npairs = pp / 2;
-
-  bool converged = false;
-  for (int sw = 0; sw < max_sweeps && !converged; ++sw) {
-    // exact squared norms of this CTA's columns at the start of the sweep
-    for (int sl = warp; sl < slots; sl += JC_WARPS) {
-      double f = 0.0;
-      for (int t = lane; t < p; t += 32) f = fma(Wl[sl * p + t], Wl[sl * p + t], f);
-      f = warp_sum(f);
-      if (lane == 0) Nl[sl] = f;
-    }
-    if (tid == 0) s_flag[sw & 1] = 0;
-    cluster.sync();
-    for (int r = 0; r < pp - 1; ++r) {
-      for (int k = rank * JC_WARPS + warp; k < npairs; k += cs * JC_WARPS) {
-        int i, j;
-        rr_pair(pp, r, k, &i, &j);
-        if (j >= p) continue;
-        const int oi = i % cs, oj = j % cs, si = (i / cs), sj = (j / cs);
-        double* wi = cluster.map_shared_rank(Wl + si * p, oi);
-        double* wj = cluster.map_shared_rank(Wl + sj * p, oj);
-        double* ni = cluster.map_shared_rank(Nl + si, oi);
-        double* nj = cluster.map_shared_rank(Nl + sj, oj);
-        double* qi = cluster.map_shared_rank(Ql + si * p, oi);
-        double* qj = cluster.map_shared_rank(Ql + sj * p, oj);
-        double x[NU], y[NU], q1[NU], q2[NU];
-        double g = 0.0;
-#pragma unroll
-        for (int u = 0; u < NU; ++u) {   // Q columns fetched with W: one round trip
-          const int t = lane + 32 * u;
-          x[u] = (t < p) ? wi[t] : 0.0;
-          y[u] = (t < p) ? wj[t] : 0.0;
-          q1[u] = (t < p) ? qi[t] : 0.0;
-          q2[u] = (t < p) ? qj[t] : 0.0;
-          g = fma(x[u], y[u], g);
-        }
-        const double a = *ni, b = *nj;
-        g = warp_sum(g);   // identical in every lane
-        if (g == 0.0 || a <= thr2 || b <= thr2 || !(g * g > tol2 * a * b)) continue;
-        // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (b - a) / (2 g), in FP32
-        // zeta is scale-invariant: bring (b - a) and g to [-2, 2] by an exact
-        // power of two before rounding them to FP32 (blocks at the rounding
-        // level have w_i . w_j ~ 1e-46, below the FP32 range)
-        const double dba = b - a;
-        const double mx = fmax(fabs(dba), fabs(g));
-        const long long ex = (__double_as_longlong(mx) >> 52) & 0x7ff;
-        double tt;
-        float bf = 0.f, gf = 0.f, zf = 0.f;
-        bool fp32_ok = ex > 0 && ex < 2046;
-        if (fp32_ok) {
-          const double sc = __longlong_as_double(static_cast<long long>(2046 - ex) << 52);   // 2^(1023 - ex)
-          bf = static_cast<float>(dba * sc);
-          gf = static_cast<float>(g * sc);
-          fp32_ok = fabsf(gf) >= 0x1p-100f;
-          if (fp32_ok) zf = bf / (2.0f * gf);
-        }
-        if (fp32_ok) {
-          // for |zeta| > 2^60, zeta^2 would overflow: t -> 1 / (2 zeta)
-          const float tf = (fabsf(zf) > 0x1p60f) ? 0.5f / zf
-                                                  : copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)));
-          tt = static_cast<double>(tf);
-        } else {
-          const double zeta = (b - a) / (2.0 * g);   // rare: outside the FP32 range
-          tt = (fabs(zeta) > 0x1p500) ? 0.5 / zeta
-                                      : copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-        }
-        const double c = rsqrt(fma(tt, tt, 1.0));
-        const double sn = c * tt;
-#pragma unroll
-        for (int u = 0; u < NU; ++u) {
-          const int t = lane + 32 * u;
-          if (t < p) {
-            wi[t] = fma(c, x[u], -sn * y[u]);
-            wj[t] = fma(sn, x[u], c * y[u]);
-            qi[t] = fma(c, q1[u], -sn * q2[u]);
-            qj[t] = fma(sn, q1[u], c * q2[u]);
-          }
-        }
-        if (lane == 0) {
-          // squared norms after the applied rotation (c, s)
-          const double cc = c * c, ss = sn * sn, csg = 2.0 * c * sn * g;
-          *ni = fma(cc, a, fma(ss, b, -csg));
-          *nj = fma(ss, a, fma(cc, b, csg));
-          s_flag[sw & 1] = 1;
-        }
-      }
-      cluster.sync();
-    }
-    // A sweep without rotations anywhere in the cluster: converged.
-    int any = 0;
-    for (int q = 0; q < cs; ++q) any |= *cluster.map_shared_rank(&s_flag[sw & 1], q);
-    converged = (any == 0);
-  }
+  int cur = 0;
+  const bool converged = jb_sweeps<double, NU>(S, &cur, p, cs, rank, max_sweeps, thr2, tol * tol, s_flag);
   if (!converged && rank == 0 && tid == 0) atomicOr(err, kDevErrNoConv);
 
-  // Epilogue on the 16 SMs: sigma_c = ||w_c||, the order (descending, stable
-  // in c), Vs = w / sigma, Us = Q, each pair signed so that the largest-|.|
-  // entry of its Vs column is positive (lowest index on ties).  sigma at the
-  // rounding level of the block (<= p u ||M||_F) counts as zero; those Vs
-  // columns are left zero and the completion kernel fills them.
-  cluster.sync();
-  for (int sl = warp; sl < slots; sl += JC_WARPS) {
-    const int c = sl * cs + rank;
+  // every block is at its home seat again (buffer cur): exact norms
+  for (int e = warp; e < 2 * bs; e += JC_WARPS) {
+    const int seat = e / bs, i = e % bs;
+    const int c = (seat == 0 ? rank : 2 * cs - 1 - rank) * bs + i;
+    const double* w = S.w(cur, seat, i);
     double f = 0.0;
-    for (int t = lane; t < p; t += 32) f = fma(Wl[sl * p + t], Wl[sl * p + t], f);
+    for (int t = lane; t < p; t += 32) f = fma(w[t], w[t], f);
     f = warp_sum(f);
-    if (lane == 0) Nl[sl] = (c < p) ? sqrt(f) : -1.0;
+    if (lane == 0) *S.n(cur, seat, i) = (c < p) ? sqrt(f) : -1.0;
   }
   cluster.sync();
   const double cut = pu * sqrt(s_fro);
-  for (int sl = warp; sl < slots; sl += JC_WARPS) {
-    const int c = sl * cs + rank;
+  for (int e = warp; e < 2 * bs; e += JC_WARPS) {
+    const int seat = e / bs, i = e % bs;
+    const int c = (seat == 0 ? rank : 2 * cs - 1 - rank) * bs + i;
     if (c >= p) continue;
-    double sc = Nl[sl];
+    double sc = *S.n(cur, seat, i);
     if (sc <= cut) sc = 0.0;
     int cnt = 0;
     for (int o = lane; o < p; o += 32) {
-      double so = *cluster.map_shared_rank(Nl + o / cs, o % cs);
+      int oc, os;
+      jb_home(o / bs, cs, &oc, &os);
+      double so = *cluster.map_shared_rank(S.n(cur, os, o % bs), oc);
       if (so <= cut) so = 0.0;
       cnt += (so > sc) || (so == sc && o < c);
     }
     const int r = __reduce_add_sync(0xffffffffu, cnt);
-    const double* w = Wl + sl * p;
+    const double* w = S.w(cur, seat, i);
     double bv = -1.0;
     int bi = p;
     for (int t = lane; t < p; t += 32) {
@@ -258,7 +370,7 @@ jacobi_cluster_kernel(int p, const double* __restrict__ M, int64_t ldm, const do
     const double inv = (sc > 0.0) ? sgn / sc : 0.0;
     double* vs = Vs + static_cast<int64_t>(r) * p;
     double* us = Us + static_cast<int64_t>(r) * p;
-    const double* qc = Ql + sl * p;
+    const double* qc = S.q(cur, seat, i);
     for (int t = lane; t < p; t += 32) {
       vs[t] = w[t] * inv;
       us[t] = sgn * qc[t];
@@ -271,36 +383,32 @@ jacobi_cluster_kernel(int p, const double* __restrict__ M, int64_t ldm, const do
   cluster.sync();   // no CTA leaves while others may still read its shared memory
 }
 
-// The same cyclic one-sided Jacobi on the rows of M in FP32 (the FFMA pipe
-// issues 64x faster than FP64 here): W = s M^T with s an exact power of two
-// that brings ||M||_F near 1 (so FP32 range limits do not bite), Q = I; the
-// sweeps stop at relative tolerance p 2^-24 or after max_sweeps.  The FP32
-// rotations accumulate in Q, written as FP64 to Qg (p x p, ld p); the FP64
-// sweeps then start from W0 = M^T Q after Q is made orthonormal in FP64.
+// The same block-cyclic one-sided Jacobi on the rows of M in FP32 (the FFMA
+// pipe issues 64x faster than FP64 here): W = s M^T with s an exact power of
+// two that brings ||M||_F near 1 (so FP32 range limits do not bite), Q = I;
+// the sweeps stop at relative tolerance p 2^-24 or after max_sweeps.  The
+// FP32 rotations accumulate in Q, written as FP64 to Qg (p x p, ld p); the
+// FP64 sweeps then start from W0 = M^T Q after Q is made orthonormal in FP64.
 template <int NU>
-__global__ void __launch_bounds__(JC_NT)
-jacobi32_cluster_kernel(int p, const double* __restrict__ M, int64_t ldm, double* __restrict__ Qg,
-                        int max_sweeps) {
+__global__ void __launch_bounds__(JC_NT, 1)
+jacobi_block32_kernel(int p, const double* __restrict__ M, int64_t ldm, double* __restrict__ Qg, int max_sweeps) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ float jsm32[];
   const int rank = static_cast<int>(cluster.block_rank());
   const int cs = static_cast<int>(cluster.num_blocks());
-  const int pp = p + (p & 1);
-  const int slots = (pp + cs - 1) / cs;
-  float* Wl = jsm32;
-  float* Ql = jsm32 + static_cast<size_t>(slots) * p;
-  float* Nl = Ql + static_cast<size_t>(slots) * p;
+  const int bs = jb_bs(p, cs);
+  JbSeats<float> S{jsm32, jsm32 + 8ull * bs * p, p, bs};
   __shared__ double s_part[JC_CLUSTER];
   __shared__ double s_scale;
   __shared__ int s_flag[2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  // ||M||_F^2 in FP64 over this CTA's rows of M, then the common scale.
+  // ||M||_F^2 in FP64 over this CTA's rows of M, then the common scale
   if (warp == 0) {
     double f = 0.0;
-    for (int sl = 0; sl < slots; ++sl) {
-      const int c = sl * cs + rank;
+    for (int e = 0; e < 2 * bs; ++e) {
+      const int c = (e < bs ? rank : 2 * cs - 1 - rank) * bs + e % bs;
       if (c >= p) continue;
       for (int t = lane; t < p; t += 32) {
         const double v = M[c + static_cast<int64_t>(t) * ldm];
@@ -321,11 +429,16 @@ jacobi32_cluster_kernel(int p, const double* __restrict__ M, int64_t ldm, double
   }
   __syncthreads();
   const double scale = s_scale;
-  for (int sl = 0; sl < slots; ++sl) {
-    const int c = sl * cs + rank;
-    for (int t = tid; t < p; t += JC_NT) {
-      Wl[sl * p + t] = (c < p) ? static_cast<float>(M[c + static_cast<int64_t>(t) * ldm] * scale) : 0.f;
-      Ql[sl * p + t] = (c < p && t == c) ? 1.f : 0.f;
+  for (int seat = 0; seat < 2; ++seat) {
+    const int B = seat == 0 ? rank : 2 * cs - 1 - rank;
+    for (int i = 0; i < bs; ++i) {
+      const int c = B * bs + i;
+      float* w = S.w(0, seat, i);
+      float* q = S.q(0, seat, i);
+      for (int t = tid; t < p; t += JC_NT) {
+        w[t] = (c < p) ? static_cast<float>(M[c + static_cast<int64_t>(t) * ldm] * scale) : 0.f;
+        q[t] = (c < p && t == c) ? 1.f : 0.f;
+      }
     }
   }
   __syncthreads();
@@ -337,80 +450,16 @@ jacobi32_cluster_kernel(int p, const double* __restrict__ M, int64_t ldm, double
     fro = static_cast<float>(f * scale * scale);
   }
   const float pu = static_cast<float>(p) * 0x1p-24f;
-  const float thr2 = pu * pu * fro;
-  const float tol2 = pu * pu;
-  const int npairs = pp / 2;
-
-  bool converged = false;
-  for (int sw = 0; sw < max_sweeps && !converged; ++sw) {
-    for (int sl = warp; sl < slots; sl += JC_WARPS) {
-      float f = 0.f;
-      for (int t = lane; t < p; t += 32) f = fmaf(Wl[sl * p + t], Wl[sl * p + t], f);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
-      if (lane == 0) Nl[sl] = f;
+  int cur = 0;
+  jb_sweeps<float, NU>(S, &cur, p, cs, rank, max_sweeps, pu * pu * fro, pu * pu, s_flag);
+  for (int seat = 0; seat < 2; ++seat) {
+    const int B = seat == 0 ? rank : 2 * cs - 1 - rank;
+    for (int i = 0; i < bs; ++i) {
+      const int c = B * bs + i;
+      if (c >= p) continue;
+      const float* q = S.q(cur, seat, i);
+      for (int t = tid; t < p; t += JC_NT) Qg[t + static_cast<int64_t>(c) * p] = static_cast<double>(q[t]);
     }
-    if (tid == 0) s_flag[sw & 1] = 0;
-    cluster.sync();
-    for (int r = 0; r < pp - 1; ++r) {
-      for (int k = rank * JC_WARPS + warp; k < npairs; k += cs * JC_WARPS) {
-        int i, j;
-        rr_pair(pp, r, k, &i, &j);
-        if (j >= p) continue;
-        const int oi = i % cs, oj = j % cs, si = i / cs, sj = j / cs;
-        float* wi = cluster.map_shared_rank(Wl + si * p, oi);
-        float* wj = cluster.map_shared_rank(Wl + sj * p, oj);
-        float* ni = cluster.map_shared_rank(Nl + si, oi);
-        float* nj = cluster.map_shared_rank(Nl + sj, oj);
-        float* qi = cluster.map_shared_rank(Ql + si * p, oi);
-        float* qj = cluster.map_shared_rank(Ql + sj * p, oj);
-        float x[NU], y[NU], q1[NU], q2[NU];
-        float g = 0.f;
-#pragma unroll
-        for (int u = 0; u < NU; ++u) {
-          const int t = lane + 32 * u;
-          x[u] = (t < p) ? wi[t] : 0.f;
-          y[u] = (t < p) ? wj[t] : 0.f;
-          q1[u] = (t < p) ? qi[t] : 0.f;
-          q2[u] = (t < p) ? qj[t] : 0.f;
-          g = fmaf(x[u], y[u], g);
-        }
-        const float a = *ni, b = *nj;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-        if (g == 0.f || a <= thr2 || b <= thr2 || !(g * g > tol2 * a * b)) continue;
-        const float zf = (b - a) / (2.0f * g);
-        const float tf = (fabsf(zf) > 0x1p60f) ? 0.5f / zf
-                                                : copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)));
-        const float c = rsqrtf(fmaf(tf, tf, 1.0f));
-        const float sn = c * tf;
-#pragma unroll
-        for (int u = 0; u < NU; ++u) {
-          const int t = lane + 32 * u;
-          if (t < p) {
-            wi[t] = fmaf(c, x[u], -sn * y[u]);
-            wj[t] = fmaf(sn, x[u], c * y[u]);
-            qi[t] = fmaf(c, q1[u], -sn * q2[u]);
-            qj[t] = fmaf(sn, q1[u], c * q2[u]);
-          }
-        }
-        if (lane == 0) {
-          const float cc = c * c, ss = sn * sn, csg = 2.0f * c * sn * g;
-          *ni = fmaf(cc, a, fmaf(ss, b, -csg));
-          *nj = fmaf(ss, a, fmaf(cc, b, csg));
-          s_flag[sw & 1] = 1;
-        }
-      }
-      cluster.sync();
-    }
-    int any = 0;
-    for (int q = 0; q < cs; ++q) any |= *cluster.map_shared_rank(&s_flag[sw & 1], q);
-    converged = (any == 0);
-  }
-  for (int sl = 0; sl < slots; ++sl) {
-    const int c = sl * cs + rank;
-    if (c >= p) continue;
-    for (int t = tid; t < p; t += JC_NT) Qg[t + static_cast<int64_t>(c) * p] = static_cast<double>(Ql[sl * p + t]);
   }
   cluster.sync();
 }
@@ -529,13 +578,15 @@ cudaError_t launch64(cudaStream_t s, int csize, int p, const double* M, int64_t 
                      int* zflag) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = prepare(jacobi_cluster_kernel<NU>, csize, kJcSmemMax);
+    cudaError_t e = prepare(jacobi_block64_kernel<NU>, csize, kJcSmemLimit);
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  const size_t smem = jb_smem(p, csize, sizeof(double));
+  if (smem > kJcSmemLimit) return cudaErrorInvalidConfiguration;   // p > 240 needs the 16-CTA cluster
   cudaLaunchAttribute at[1];
-  cudaLaunchConfig_t cfg = cluster_cfg(s, csize, jc_smem(p, csize), at);
-  return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel<NU>, p, M, ldm, W0, Q0, Us, d, Vs, max_sweeps, tol, err,
+  cudaLaunchConfig_t cfg = cluster_cfg(s, csize, smem, at);
+  return cudaLaunchKernelEx(&cfg, jacobi_block64_kernel<NU>, p, M, ldm, W0, Q0, Us, d, Vs, max_sweeps, tol, err,
                             zflag);
 }
 
@@ -543,13 +594,15 @@ template <int NU>
 cudaError_t launch32(cudaStream_t s, int csize, int p, const double* M, int64_t ldm, double* Qg, int sweeps) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = prepare(jacobi32_cluster_kernel<NU>, csize, jc_smem32(JC_MAXP, 8));
+    cudaError_t e = prepare(jacobi_block32_kernel<NU>, csize, kJcSmemLimit);
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  const size_t smem = jb_smem(p, csize, sizeof(float));
+  if (smem > kJcSmemLimit) return cudaErrorInvalidConfiguration;
   cudaLaunchAttribute at[1];
-  cudaLaunchConfig_t cfg = cluster_cfg(s, csize, jc_smem32(p, csize), at);
-  return cudaLaunchKernelEx(&cfg, jacobi32_cluster_kernel<NU>, p, M, ldm, Qg, sweeps);
+  cudaLaunchConfig_t cfg = cluster_cfg(s, csize, smem, at);
+  return cudaLaunchKernelEx(&cfg, jacobi_block32_kernel<NU>, p, M, ldm, Qg, sweeps);
 }
 
 cudaError_t run64(cudaStream_t s, int csize, int p, const double* M, int64_t ldm, const double* W0, const double* Q0,
@@ -572,11 +625,11 @@ int cluster_size() {
   static int csize = 0;
   if (csize) return csize;
   csize = 8;
-  if (prepare(jacobi_cluster_kernel<8>, JC_CLUSTER, kJcSmemMax) == cudaSuccess) {
+  if (prepare(jacobi_block64_kernel<8>, JC_CLUSTER, kJcSmemLimit) == cudaSuccess) {
     cudaLaunchAttribute qa[1];
-    cudaLaunchConfig_t q = cluster_cfg(nullptr, JC_CLUSTER, jc_smem(JC_MAXP, JC_CLUSTER), qa);
+    cudaLaunchConfig_t q = cluster_cfg(nullptr, JC_CLUSTER, jb_smem(JC_MAXP, JC_CLUSTER, sizeof(double)), qa);
     int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, jacobi_cluster_kernel<8>, &q) == cudaSuccess && nclusters > 0)
+    if (cudaOccupancyMaxActiveClusters(&nclusters, jacobi_block64_kernel<8>, &q) == cudaSuccess && nclusters > 0)
       csize = JC_CLUSTER;
   }
   cudaGetLastError();
