@@ -34,7 +34,7 @@ FP64_PEAK_TFLOPS = NUM_SMS * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
 # Valid only for the kernel source it was taken on (sha256 prefix of
 # csrc/gemm_f64.cu); the per-launch traffic of the bench run is this ratio
 # times its algorithmic bytes per launch.
-GEMM_TRAFFIC = {"20ac287f222de114": 0.928}
+GEMM_TRAFFIC = {"5b25bb34a710a3c2": 0.926}
 
 
 def parse():

@@ -136,22 +136,48 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // lo = rna_tf32(x - hi), both exactly representable in TF32, and the MMA
 // warp accumulates hi*hi + hi*lo + lo*hi (error ~2^-22 relative per product,
 // FP32 level); the lo*lo term is dropped.
+//
+// Promotion (SPLIT): the tensor-core FP32 accumulator truncates at every
+// MMA step, which costs about half an ulp of the running sum per K = 8, a
+// bias that grows linearly with the reduction length (measured 6.5e-6
+// relative at K = 910, 9.7e-7 at K = 146).  So the accumulation restarts
+// every TC_CHUNK_KB k-blocks (K = 128) in the other of two tensor-memory
+// accumulators, and the four splitter warps add each finished chunk into FP32
+// registers (round to nearest) while the MMA warp fills the other one.
+constexpr int TC_CHUNK_KB = 4;
+
 template <bool SPLIT>
 struct TcCfg {
   static constexpr int STAGES = SPLIT ? 3 : 4;
   static constexpr int TILES = SPLIT ? 4 : 2;               // tiles per stage: A, B (, A_lo, B_lo)
   static constexpr int NT = SPLIT ? 192 : 128;
   static constexpr int EPI_WARP0 = SPLIT ? 2 : 0;            // first of the 4 epilogue warps
+  static constexpr uint32_t TMEM_COLS = SPLIT ? 2 * TC_BN : TC_BN;
   static constexpr int SMEM = STAGES * TILES * TC_TILE_BYTES + 1024 + 256;
 };
+
+// Warp-collective load of 32 consecutive FP32 accumulator columns of this
+// warp's 32 tensor-memory lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
 
 template <bool SPLIT, bool AMN, bool BMN>
 __global__ void __launch_bounds__(TcCfg<SPLIT>::NT, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int64_t M,
-                  int64_t N, int64_t K, float alpha, float beta, float* __restrict__ D, int64_t ldd,
-                  float* __restrict__ part, int64_t kchunk, int* __restrict__ err) {
+               int64_t N, int64_t K, float alpha, float beta, float* __restrict__ D, int64_t ldd,
+               float* __restrict__ part, int64_t kchunk, int* __restrict__ err) {
   using C = TcCfg<SPLIT>;
   constexpr int S = C::STAGES;
+  constexpr int CH = TC_CHUNK_KB;
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   // 1024-byte aligned tiles (the 128B swizzle pattern repeats every 1024 bytes)
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -164,7 +190,9 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   uint64_t* split = full + S;
   uint64_t* empty = split + S;
   uint64_t* done = empty + S;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* accf = done + 1;    // [2] accumulator buffer holds a finished chunk (SPLIT)
+  uint64_t* acce = accf + 2;    // [2] accumulator buffer drained into registers (SPLIT)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
   __shared__ int s_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -173,6 +201,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   const int64_t kbeg = static_cast<int64_t>(blockIdx.z) * kchunk;
   const int64_t kend = (kbeg + kchunk < K) ? kbeg + kchunk : K;
   const int nkb = static_cast<int>((kend - kbeg + TC_BK - 1) / TC_BK);
+  const int nch = (nkb + CH - 1) / CH;
 
   if (tid == 0) {
     s_fail = 0;
@@ -182,11 +211,15 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       mbar_init(&empty[st], 1);
     }
     mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 128);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {   // allocate 128 tensor-memory columns (the 128 x 128 FP32 accumulator)
+  if (warp == 0) {   // allocate the FP32 accumulator(s) in tensor memory (128 lanes x 128 columns each)
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TC_BN)
+                 "r"(C::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -196,6 +229,10 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   const uint32_t tmem = *tmem_slot;
   const unsigned long long t0 = global_ns();
   int issued = 0;   // TMA stages issued by the producer
+  const int quarter = warp & 3;   // the 32 tensor-memory lanes this warp may read
+  float racc[SPLIT ? TC_BN : 1];  // promoted sums of this thread's row (SPLIT)
+#pragma unroll
+  for (int j = 0; j < (SPLIT ? TC_BN : 1); ++j) racc[j] = 0.f;
 
   if (warp == 0 && lane == 0) {
     // producer
@@ -220,6 +257,11 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     // MMA issuer
     for (int kb = 0; kb < nkb; ++kb) {
       const int st = kb % S;
+      const int c = kb / CH;
+      const uint32_t buf = SPLIT ? static_cast<uint32_t>(c & 1) : 0u;
+      const bool first = SPLIT ? (kb % CH == 0) : (kb == 0);
+      // (SPLIT) this chunk's accumulator must have been drained two chunks ago
+      if (SPLIT && first && c >= 2 && !mbar_wait(&acce[buf], ((c >> 1) - 1) & 1, t0)) { s_fail = 1; break; }
       if (!mbar_wait(SPLIT ? &split[st] : &full[st], (kb / S) & 1, t0)) { s_fail = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // K = 8 per instruction: a K-major tile advances 32 bytes (+2 in 16 B
@@ -229,24 +271,43 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       const uint64_t dal = AMN ? mnmajor_sw128a32_desc(smem_u32(tileAlo(st))) : kmajor_sw128_desc(smem_u32(tileAlo(st)));
       const uint64_t dbl = BMN ? mnmajor_sw128a32_desc(smem_u32(tileBlo(st))) : kmajor_sw128_desc(smem_u32(tileBlo(st)));
       constexpr uint64_t stepA = AMN ? 64ull : 2ull, stepB = BMN ? 64ull : 2ull;
+      const uint32_t dacc = tmem + buf * static_cast<uint32_t>(TC_BN);
 #pragma unroll
       for (int kk = 0; kk < TC_BK / 8; ++kk) {
-        mma_tf32<AMN, BMN>(tmem, da + stepA * kk, db + stepB * kk, (kb > 0 || kk > 0) ? 1u : 0u);
+        mma_tf32<AMN, BMN>(dacc, da + stepA * kk, db + stepB * kk, (!first || kk > 0) ? 1u : 0u);
         if (SPLIT) {
-          mma_tf32<AMN, BMN>(tmem, da + stepA * kk, dbl + stepB * kk, 1u);
-          mma_tf32<AMN, BMN>(tmem, dal + stepA * kk, db + stepB * kk, 1u);
+          mma_tf32<AMN, BMN>(dacc, da + stepA * kk, dbl + stepB * kk, 1u);
+          mma_tf32<AMN, BMN>(dacc, dal + stepA * kk, db + stepB * kk, 1u);
         }
       }
       mma_commit(&empty[st]);
+      if (SPLIT && (kb % CH == CH - 1 || kb == nkb - 1)) mma_commit(&accf[buf]);   // chunk c complete
     }
-    mma_commit(done);   // arrives once every issued MMA has completed
+    if (!SPLIT) mma_commit(done);   // arrives once every issued MMA has completed
   } else if (SPLIT && warp >= 2) {
     // splitters: hi = rna_tf32(x) in place, lo = rna_tf32(x - hi); the A and B
-    // tiles of a stage are adjacent (8192 floats), and so are their lo tiles
+    // tiles of a stage are adjacent (8192 floats), and so are their lo tiles.
+    // After the last k-block of chunk c they promote chunk c - 1.
     const int w = tid - 64;
-    for (int kb = 0; kb < nkb; ++kb) {
+    bool failed = false;
+    auto promote = [&](int c) {
+      const uint32_t buf = static_cast<uint32_t>(c & 1);
+      const bool waited = mbar_wait(&accf[buf], (c >> 1) & 1, t0);
+      if (__all_sync(0xffffffffu, waited) == 0) { failed = true; return; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + buf * TC_BN + static_cast<uint32_t>(c0), r);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) racc[c0 + j] += __uint_as_float(r[j]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&acce[buf]);
+    };
+    for (int kb = 0; kb < nkb && !failed; ++kb) {
       const int st = kb % S;
-      if (!mbar_wait(&full[st], (kb / S) & 1, t0)) { s_fail = 1; break; }
+      if (!mbar_wait(&full[st], (kb / S) & 1, t0)) { failed = true; break; }
       float4* hi = reinterpret_cast<float4*>(tileA(st));
       float4* lo = reinterpret_cast<float4*>(tileAlo(st));
 #pragma unroll 4
@@ -260,59 +321,61 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor-core reads
       mbar_arrive(&split[st]);
+      if ((kb % CH == CH - 1 || kb == nkb - 1) && kb / CH >= 1) promote(kb / CH - 1);
     }
+    if (!failed && nch > 0) promote(nch - 1);
+    if (failed) s_fail = 1;
   }
   __syncwarp();
-  // epilogue: wait for the accumulator (the decision is made uniform across
-  // the CTA: tcgen05.ld below is a warp-collective instruction)
   const bool epi = warp >= C::EPI_WARP0 && warp < C::EPI_WARP0 + 4;
-  const bool waited = epi ? mbar_wait(done, 0, t0) : true;
-  const bool warp_ok = __all_sync(0xffffffffu, waited) != 0;
-  if (!warp_ok && lane == 0) s_fail = 1;
+  if (!SPLIT) {
+    // wait for the accumulator (the decision is made uniform across the
+    // warp: tcgen05.ld below is a warp-collective instruction)
+    const bool waited = epi ? mbar_wait(done, 0, t0) : true;
+    const bool warp_ok = __all_sync(0xffffffffu, waited) != 0;
+    if (!warp_ok && lane == 0) s_fail = 1;
+  }
   __syncthreads();
   const bool ok = (s_fail == 0);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const int quarter = warp & 3;   // the 32 tensor-memory lanes this warp may read
-  if (epi && ok && nkb > 0) {
+  if (epi && ok) {
     const int row = m0 + quarter * 32 + lane;
-    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-      uint32_t r[32];
-      const uint32_t taddr = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + static_cast<uint32_t>(c0);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    auto put = [&](int64_t col, float v) {
+      if (part) {
+        part[static_cast<int64_t>(blockIdx.z) * M * N + row + col * M] = v;
+      } else {
+        float* dp = D + row + col * ldd;
+        *dp = (beta == 0.f) ? alpha * v : fmaf(alpha, v, beta * *dp);
+      }
+    };
+    if (SPLIT) {
+      // racc holds the sum (zero for an empty K range)
       if (row < M) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int64_t col = n0 + c0 + j;
-          if (col < N) {
-            const float v = __uint_as_float(r[j]);
-            if (part) {
-              part[static_cast<int64_t>(blockIdx.z) * M * N + row + col * M] = v;
-            } else {
-              float* dp = D + row + col * ldd;
-              *dp = (beta == 0.f) ? alpha * v : fmaf(alpha, v, beta * *dp);
-            }
+        for (int j = 0; j < (SPLIT ? TC_BN : 1); ++j) {
+          const int64_t col = n0 + j;
+          if (col < N) put(col, racc[j]);
+        }
+      }
+    } else if (nkb > 0) {
+      for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + static_cast<uint32_t>(c0), r);
+        if (row < M) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int64_t col = n0 + c0 + j;
+            if (col < N) put(col, __uint_as_float(r[j]));
           }
         }
       }
-    }
-  } else if (epi && nkb == 0 && ok) {
-    // empty K range: D = beta D (or zero partials)
-    const int row = m0 + quarter * 32 + lane;
-    if (row < M)
-      for (int j = 0; j < TC_BN; ++j) {
+    } else if (row < M) {
+      for (int j = 0; j < TC_BN; ++j) {   // empty K range: D = beta D (or zero partials)
         const int64_t col = n0 + j;
         if (col >= N) break;
-        if (part) part[static_cast<int64_t>(blockIdx.z) * M * N + row + col * M] = 0.f;
-        else { float* dp = D + row + col * ldd; *dp = (beta == 0.f) ? 0.f : beta * *dp; }
+        put(col, 0.f);
       }
+    }
   }
   if (!ok && tid == 0) atomicOr(err, kDevErrTimeout);
   // drain: the producer's copies in flight must land before the CTA exits
@@ -323,7 +386,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
   }
 }
 
@@ -400,9 +463,10 @@ cudaError_t gemm_tc(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int6
   if (!make_map(&ma, A, amn ? m : k, amn ? k : m, lda, amn) || !make_map(&mb, B, bmn ? n : k, bmn ? k : n, ldb, bmn))
     return cudaErrorInvalidValue;
   const int64_t tiles = ((m + TC_BM - 1) / TC_BM) * ((n + TC_BN - 1) / TC_BN);
-  // split K until the tiles cover the SMs (each CTA uses one SM: >= 130 KB of shared memory)
+  // split K while the CTAs still fit one wave (each CTA takes one SM: >= 130 KB of shared memory)
   int splits = 1;
-  while (tiles * splits < kNumSMs && (k / (splits + 1)) >= 4 * TC_BK && (splits + 1) * m * n <= work_elems) ++splits;
+  while (tiles * (splits + 1) <= kNumSMs && (k / (splits + 1)) >= 4 * TC_BK && (splits + 1) * m * n <= work_elems)
+    ++splits;
   int64_t kc = (k + splits - 1) / splits;
   kc = ((kc + TC_BK - 1) / TC_BK) * TC_BK;
   splits = static_cast<int>((k + kc - 1) / kc);

@@ -119,8 +119,9 @@ def test_tc_3xtf32_at_fp32_level(ready, m, n, k, ta, tb):
     # (<= 2^-22 |a||b|); FP32 accumulation of the chunk
     bound = 1.5 * (4 * 2.0 ** -22 + k * 2.0 ** -23) * (np.abs(opA) @ np.abs(opB)) + 1e-6
     assert np.all(np.abs(out - ref) <= bound)
-    # the tensor-core FP32 accumulator does not round to nearest: its error
-    # grows ~ linearly in the chunk length (measured 1.9e-5 at K = 8000,
-    # 3 chunks) instead of ~ sqrt; plain TF32 gives ~1e-3
+    # the tensor-core FP32 accumulator truncates (about half an ulp of the
+    # running sum per K = 8); the kernel restarts it every K = 128 and adds
+    # the chunks in FP32 registers, so the error stays near 1e-6 at any K
+    # (it grew linearly with K before: 1.9e-5 at K = 8000); plain TF32 ~1e-3
     rel = np.linalg.norm(out - ref) / np.linalg.norm(ref)
-    assert rel < (4e-5 if k > 1000 else 4e-6)
+    assert rel < 2e-6
