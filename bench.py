@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-verify", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--fp64-emulation", type=int, default=1, choices=[0, 1],
+                    help="FP64 form: 1 Ozaki-scheme tensor-core GEMM, 0 FP64 DFMA GEMM")
     ap.add_argument("--overlap", type=int, default=1, choices=[0, 1],
                     help="1: U/V accumulation on a second, low-priority stream")
     ap.add_argument("--tensor-cores", type=int, default=1, choices=[0, 1],
@@ -287,6 +289,7 @@ def run_own(args):
     Ust = torch.empty((n, n), dtype=torch.float64, device="cuda")
     Vst = torch.empty((n, n), dtype=torch.float64, device="cuda")
     opts = native.default_opts()
+    opts.fp64_emulation = args.fp64_emulation
     opts.overlap = args.overlap
     kr = ctypes.c_int64(0)
     stream = torch.cuda.current_stream()

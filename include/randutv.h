@@ -65,10 +65,18 @@ typedef struct randutv_opts {
                            alignment rules; 0 = FP32 CUDA cores.  The
                            block-reflector and rotation products always run
                            on the FP32 CUDA cores (round to nearest).        */
+  int fp64_emulation;   /* FP64 form only: 1 = the sketch products, block-
+                           reflector applications and rotations through the
+                           Ozaki-scheme GEMM (randutv_dgemm_oz: BF16 tensor-
+                           core slice products, FP64-accurate); 0 = FP64
+                           DFMA GEMM.  The Gram matrices of the compact-WY
+                           factors and products too small for its tiles
+                           always use DFMA.  Needs about 24 n^2 bytes of
+                           scratch per lane (n = max(m, n)).                 */
 } randutv_opts;
 
 /* Defaults: FP64, form_uv = 1, max_sweeps = 30, p = 0, seed = 998, no g_inject,
-   overlap = 1, tensor_cores = 1. */
+   overlap = 1, tensor_cores = 1, fp64_emulation = 1. */
 void randutv_opts_default(randutv_opts* opts);
 
 /* Stream used by all later calls in this process (a cudaStream_t; NULL =
@@ -196,6 +204,23 @@ int randutv_sgemm(char transa, char transb, int64_t m, int64_t n, int64_t k, flo
 int randutv_sgemm_tc(char transa, char transb, int64_t m, int64_t n, int64_t k, float alpha,
                      const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
                      float* C, int64_t ldc, int passes);
+
+/* C = alpha op(A) op(B) + beta C in FP64 (column-major; transa, transb as in
+ * randutv_dgemm) from BF16 tensor-core products: the Ozaki scheme, an
+ * implementation choice for the products of Fig. 4 with no counterpart in
+ * the paper.  Each row of op(A) and column of op(B) is split per K chunk of
+ * 128 into a power-of-two scale and 8 slices of 7 bits (56 bits), the 36
+ * slice-pair products with slice indices s + t <= 7 are summed exactly in
+ * FP32 on the tensor cores, combined exactly in 64-bit integers and
+ * rounded once to FP64 per chunk; chunks are summed in FP64.  Error per
+ * chunk <= 128 * 2^-55 * max|op(A) row| * max|op(B) column| over the chunk
+ * plus FP64 rounding.  k = 0 gives C = beta C.  Allocates its scratch
+ * (about 16 (m + n) k bytes of slices, plus 8 m n per chunk when k > 128)
+ * with cudaMallocAsync on the bound stream and synchronises it.  Negative
+ * return: the position of the first invalid argument. */
+int randutv_dgemm_oz(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                     double* C, int64_t ldc);
 
 /* Unpivoted Householder QR of the k x w panel P (k >= w >= 1, ldp >= k), in
  * place (eq. unpivQR; LAPACK dlarfg convention: beta = -sign(alpha)||x||,

@@ -40,9 +40,10 @@ def _bind_stream():
     native.lib().randutv_set_stream(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
-def _opts(seed, form_uv, max_sweeps, g_inject, overlap=True):
+def _opts(seed, form_uv, max_sweeps, g_inject, overlap=True, fp64_emulation=True):
     o = native.default_opts()
     o.overlap = 1 if overlap else 0
+    o.fp64_emulation = 1 if fp64_emulation else 0
     o.seed = int(seed)
     o.form_uv = 1 if form_uv else 0
     o.max_sweeps = int(max_sweeps)
@@ -50,14 +51,17 @@ def _opts(seed, form_uv, max_sweeps, g_inject, overlap=True):
     return o
 
 
-def factor(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sweeps=30, overlap=True):
+def factor(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sweeps=30, overlap=True,
+           fp64_emulation=True):
     """A = U T V^T by randUTV (Fig. 4) on A's CUDA device, FP64.
 
     A: (m, n) float64 CUDA tensor.  g_inject: optional 1-D float64 CUDA tensor
     with every randomized step's Gaussian G concatenated (column-major per
     step, the layout of ``synth.stream_layout``) used instead of the Philox
     stream.  Returns UTV(U, T, V, k_reached) as (m, m), (m, n), (n, n) views
-    (U, V are None when form_uv is False).  ENOCONV raises too."""
+    (U, V are None when form_uv is False).  ENOCONV raises too.
+    fp64_emulation: the large products through the Ozaki-scheme tensor-core
+    GEMM (FP64-accurate) instead of the FP64 DFMA GEMM."""
     torch = _torch()
     _check_cuda64(A, "A")
     m, n = A.shape
@@ -68,7 +72,7 @@ def factor(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sw
         if g_inject is not None:
             if g_inject.dtype != torch.float64 or not g_inject.is_cuda or not g_inject.is_contiguous():
                 raise TypeError("g_inject must be a contiguous float64 CUDA tensor")
-        o = _opts(seed, form_uv, max_sweeps, g_inject, overlap)
+        o = _opts(seed, form_uv, max_sweeps, g_inject, overlap, fp64_emulation)
         kr = ctypes.c_int64(0)
         _bind_stream()
         st = native.lib().randutv_factor_ex(

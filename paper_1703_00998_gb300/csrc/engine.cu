@@ -133,43 +133,60 @@ static cudaError_t sumsq(cudaStream_t s, int64_t m, int64_t n, const double* X, 
 }
 
 // ------------------------------------------------------- block reflectors
+// Where an FP64 product runs: the Ozaki-scheme tensor-core GEMM (gemm_oz.cu)
+// when enabled and the product is large enough for its tiles, else the
+// DFMA GEMM.  Each lane has its own split-K partials and slice workspace.
+struct G64 {
+  bool oz;
+  void* ow;
+  size_t owb;
+  int* err;
+  double* gws;
+  int64_t ge;
+  cudaError_t run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
+                  int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc) const {
+    if (oz && m >= 64 && n >= 32 && k >= 32 && gemm_oz_work_bytes(m, n, k) <= owb)
+      return gemm_oz(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ow, owb, err);
+    return gemm_f64(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, gws, ge);
+  }
+};
 // C (rows x cols) <- C (I - Vx S Vx^T), Vx cols x w.
 static cudaError_t wy_right(cudaStream_t s, int64_t rows, int64_t cols, double* C, int64_t ldc,
                             const double* Vx, const double* S, int w, double* W1, double* W2,
-                            double* gws, int64_t gws_elems) {
+                            const G64& g) {
   if (rows <= 0 || cols <= 0) return cudaSuccess;
   cudaError_t e;
-  if ((e = gemm_f64(s, false, false, rows, w, cols, 1.0, C, ldc, Vx, cols, 0.0, W1, rows, gws, gws_elems))) return e;
-  if ((e = gemm_f64(s, false, false, rows, w, w, 1.0, W1, rows, S, w, 0.0, W2, rows, gws, gws_elems))) return e;
-  return gemm_f64(s, false, true, rows, cols, w, -1.0, W2, rows, Vx, cols, 1.0, C, ldc, gws, gws_elems);
+  if ((e = g.run(s, false, false, rows, w, cols, 1.0, C, ldc, Vx, cols, 0.0, W1, rows))) return e;
+  if ((e = g.run(s, false, false, rows, w, w, 1.0, W1, rows, S, w, 0.0, W2, rows))) return e;
+  return g.run(s, false, true, rows, cols, w, -1.0, W2, rows, Vx, cols, 1.0, C, ldc);
 }
 
 // C (rows x cols) <- (I - Vx S Vx^T)^T C, Vx rows x w.
 static cudaError_t wy_left_t(cudaStream_t s, int64_t rows, int64_t cols, double* C, int64_t ldc,
                              const double* Vx, const double* S, int w, double* W1, double* W2,
-                             double* gws, int64_t gws_elems) {
+                             const G64& g) {
   if (rows <= 0 || cols <= 0) return cudaSuccess;
   cudaError_t e;
-  if ((e = gemm_f64(s, true, false, w, cols, rows, 1.0, Vx, rows, C, ldc, 0.0, W1, w, gws, gws_elems))) return e;
-  if ((e = gemm_f64(s, true, false, w, cols, w, 1.0, S, w, W1, w, 0.0, W2, w, gws, gws_elems))) return e;
-  return gemm_f64(s, false, false, rows, cols, w, -1.0, Vx, rows, W2, w, 1.0, C, ldc, gws, gws_elems);
+  if ((e = g.run(s, true, false, w, cols, rows, 1.0, Vx, rows, C, ldc, 0.0, W1, w))) return e;
+  if ((e = g.run(s, true, false, w, cols, w, 1.0, S, w, W1, w, 0.0, W2, w))) return e;
+  return g.run(s, false, false, rows, cols, w, -1.0, Vx, rows, W2, w, 1.0, C, ldc);
 }
 
 // X (rows x w) <- X Q with Q w x w (through tmp).
 static cudaError_t rot_right(cudaStream_t s, int64_t rows, int w, double* X, int64_t ldx, const double* Q,
-                             double* tmp, double* gws, int64_t gws_elems) {
+                             double* tmp, const G64& g) {
   if (rows <= 0 || w <= 0) return cudaSuccess;
   cudaError_t e;
-  if ((e = gemm_f64(s, false, false, rows, w, w, 1.0, X, ldx, Q, w, 0.0, tmp, rows, gws, gws_elems))) return e;
+  if ((e = g.run(s, false, false, rows, w, w, 1.0, X, ldx, Q, w, 0.0, tmp, rows))) return e;
   return copy_matrix(s, rows, w, tmp, rows, X, ldx);
 }
 
 // X (w x cols) <- Q^T X with Q w x w (through tmp).
 static cudaError_t rot_left_t(cudaStream_t s, int w, int64_t cols, double* X, int64_t ldx, const double* Q,
-                              double* tmp, double* gws, int64_t gws_elems) {
+                              double* tmp, const G64& g) {
   if (cols <= 0 || w <= 0) return cudaSuccess;
   cudaError_t e;
-  if ((e = gemm_f64(s, true, false, w, cols, w, 1.0, Q, w, X, ldx, 0.0, tmp, w, gws, gws_elems))) return e;
+  if ((e = g.run(s, true, false, w, cols, w, 1.0, Q, w, X, ldx, 0.0, tmp, w))) return e;
   return copy_matrix(s, w, cols, tmp, w, X, ldx);
 }
 
@@ -187,7 +204,19 @@ struct Work {
   unsigned* flags;
   void* base;
   size_t bytes;
+  void *ozT, *ozU;   // Ozaki GEMM workspaces of the two lanes (or null)
+  size_t ozb;
 };
+
+// Largest Ozaki workspace any product of the factorization needs: the
+// first step's shapes bound every later one.
+static size_t oz_budget(int64_t m, int64_t n, int b) {
+  const int64_t mx = std::max(m, n);
+  const int64_t sh[][3] = {{mx, b, mx}, {b, mx, mx}, {mx, mx, b}, {mx, b, b}, {b, mx, b}};
+  size_t w = 0;
+  for (auto& x : sh) w = std::max(w, gemm_oz_work_bytes(x[0], x[1], x[2]));
+  return w;
+}
 
 static size_t align_up(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
@@ -261,6 +290,7 @@ void randutv_opts_default(randutv_opts* o) {
   o->g_inject = nullptr;
   o->overlap = 1;
   o->tensor_cores = 1;
+  o->fp64_emulation = 1;
 }
 
 int randutv_set_stream(void* s) {
@@ -324,9 +354,17 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
 
   {
     cudaError_t e = work_alloc(s, m, n, b, uv, &w);
+    if (e == cudaSuccess && opts.fp64_emulation && gemm_oz_supported()) {
+      w.ozb = oz_budget(m, n, b);
+      e = cudaMallocAsync(&w.ozT, w.ozb, s);
+      if (e == cudaSuccess && uv) e = cudaMallocAsync(&w.ozU, w.ozb, s);
+    }
     if (e != cudaSuccess) {
       cudaGetLastError();
       snprintf(g_detail, sizeof(g_detail), "workspace: %s", cudaGetErrorString(e));
+      if (w.ozT) cudaFreeAsync(w.ozT, s);
+      if (w.base) cudaFreeAsync(w.base, s);
+      cudaStreamSynchronize(s);
       return e == cudaErrorMemoryAllocation ? RANDUTV_ENOMEM : RANDUTV_ECUDA;
     }
   }
@@ -342,6 +380,9 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
   {
     cudaStream_t sT = L.t, sU = L.uv;
     const int64_t ge = w.gws_elems;
+    int* oz_err = reinterpret_cast<int*>(slot(w, 3) + 2);
+    const G64 gT{w.ozT != nullptr, w.ozT, w.ozb, oz_err, w.gws, ge};
+    const G64 gU{w.ozU != nullptr, w.ozU, w.ozb, oz_err, w.gwsu, ge};
     RUTV_CK(copy_matrix(sT, m, n, A, lda, T, ldt));
     if (uv) {
       RUTV_CK(set_identity(sU, m, U, ldu));
@@ -379,19 +420,19 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
           RUTV_CK(launch_gaussian(sT, opts.seed, i, kr, b, w.G, kr));
         }
         g_off += kr * b;
-        RUTV_CK(gemm_f64(sT, true, false, kc, b, kr, 1.0, X, ldt, G, kr, 0.0, w.Y, kc, w.gws, ge));
+        RUTV_CK(gT.run(sT, true, false, kc, b, kr, 1.0, X, ldt, G, kr, 0.0, w.Y, kc));
         for (int j = 0; j < q; ++j) {
-          RUTV_CK(gemm_f64(sT, false, false, kr, b, kc, 1.0, X, ldt, w.Y, kc, 0.0, w.Z, kr, w.gws, ge));
-          RUTV_CK(gemm_f64(sT, true, false, kc, b, kr, 1.0, X, ldt, w.Z, kr, 0.0, w.Y, kc, w.gws, ge));
+          RUTV_CK(gT.run(sT, false, false, kr, b, kc, 1.0, X, ldt, w.Y, kc, 0.0, w.Z, kr));
+          RUTV_CK(gT.run(sT, true, false, kc, b, kr, 1.0, X, ldt, w.Z, kr, 0.0, w.Y, kc));
         }
         RUTV_CK(panel_qr(sT, kc, b, w.Y, kc, w.tau, Vv, w.Rt, w.part, slot(w, 0)));
         RUTV_CK(gemm_f64(sT, true, false, b, b, kc, 1.0, Vv, kc, Vv, kc, 0.0, w.gram, b, w.gws, ge));
         RUTV_CK(tfactor_from_gram(sT, b, w.gram, w.tau, Sv));
         RUTV_CK(cudaEventRecord(L.v[sl], sT));
-        RUTV_CK(wy_right(sT, m, kc, T + r0 * ldt, ldt, Vv, Sv, b, w.W1, w.W2, w.gws, ge));
+        RUTV_CK(wy_right(sT, m, kc, T + r0 * ldt, ldt, Vv, Sv, b, w.W1, w.W2, gT));
         if (uv) {
           RUTV_CK(cudaStreamWaitEvent(sU, L.v[sl], 0));
-          RUTV_CK(wy_right(sU, n, kc, V + r0 * ldv, ldv, Vv, Sv, b, w.W1u, w.W2u, w.gwsu, ge));
+          RUTV_CK(wy_right(sU, n, kc, V + r0 * ldv, ldv, Vv, Sv, b, w.W1u, w.W2u, gU));
         }
 
         RUTV_CK(panel_qr(sT, kr, b, X, ldt, w.tau, Vu, w.R, w.part, slot(w, 1)));
@@ -400,9 +441,9 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
         if (uv) {
           RUTV_CK(cudaEventRecord(L.u[sl], sT));
           RUTV_CK(cudaStreamWaitEvent(sU, L.u[sl], 0));
-          RUTV_CK(wy_right(sU, m, kr, U + r0 * ldu, ldu, Vu, Su, b, w.W1u, w.W2u, w.gwsu, ge));
+          RUTV_CK(wy_right(sU, m, kr, U + r0 * ldu, ldu, Vu, Su, b, w.W1u, w.W2u, gU));
         }
-        RUTV_CK(wy_left_t(sT, kr, kc - b, T + r0 + c1 * ldt, ldt, Vu, Su, b, w.W1, w.W2, w.gws, ge));
+        RUTV_CK(wy_left_t(sT, kr, kc - b, T + r0 + c1 * ldt, ldt, Vu, Su, b, w.W1, w.W2, gT));
         RUTV_CK(fill(sT, kr, b, X, ldt, 0.0));
 
         RUTV_CK(jacobi_svd(sT, b, w.R, b, Us, w.d, Vs, opts.max_sweeps, w.jws, slot(w, 2)));
@@ -412,11 +453,11 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
         if (uv) {
           RUTV_CK(cudaEventRecord(L.s[sl], sT));
           RUTV_CK(cudaStreamWaitEvent(sU, L.s[sl], 0));
-          RUTV_CK(rot_right(sU, m, b, U + r0 * ldu, ldu, Us, w.tmpu, w.gwsu, ge));
-          RUTV_CK(rot_right(sU, n, b, V + r0 * ldv, ldv, Vs, w.tmpu, w.gwsu, ge));
+          RUTV_CK(rot_right(sU, m, b, U + r0 * ldu, ldu, Us, w.tmpu, gU));
+          RUTV_CK(rot_right(sU, n, b, V + r0 * ldv, ldv, Vs, w.tmpu, gU));
         }
-        RUTV_CK(rot_left_t(sT, b, kc - b, T + r0 + c1 * ldt, ldt, Us, w.tmp, w.gws, ge));
-        RUTV_CK(rot_right(sT, r0, b, T + r0 * ldt, ldt, Vs, w.tmp, w.gws, ge));
+        RUTV_CK(rot_left_t(sT, b, kc - b, T + r0 + c1 * ldt, ldt, Us, w.tmp, gT));
+        RUTV_CK(rot_right(sT, r0, b, T + r0 * ldt, ldt, Vs, w.tmp, gT));
       } else {
         // ---- last block: full SVD, economically through a QR when not square
         int p;
@@ -431,7 +472,7 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
           if (uv) {
             RUTV_CK(cudaEventRecord(L.u[sl], sT));
             RUTV_CK(cudaStreamWaitEvent(sU, L.u[sl], 0));
-            RUTV_CK(wy_right(sU, m, kr, U + r0 * ldu, ldu, Vu, Su, p, w.W1u, w.W2u, w.gwsu, ge));
+            RUTV_CK(wy_right(sU, m, kr, U + r0 * ldu, ldu, Vu, Su, p, w.W1u, w.W2u, gU));
           }
         } else {
           p = static_cast<int>(kr);
@@ -439,11 +480,11 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
           RUTV_CK(panel_qr(sT, kc, p, w.W1, kc, w.tau, Vv, w.Rt, w.part, slot(w, 0)));
           RUTV_CK(gemm_f64(sT, true, false, p, p, kc, 1.0, Vv, kc, Vv, kc, 0.0, w.gram, p, w.gws, ge));
           RUTV_CK(tfactor_from_gram(sT, p, w.gram, w.tau, Sv));
-          RUTV_CK(wy_right(sT, m, kc, T + r0 * ldt, ldt, Vv, Sv, p, w.W2, w.tmp, w.gws, ge));
+          RUTV_CK(wy_right(sT, m, kc, T + r0 * ldt, ldt, Vv, Sv, p, w.W2, w.tmp, gT));
           if (uv) {
             RUTV_CK(cudaEventRecord(L.v[sl], sT));
             RUTV_CK(cudaStreamWaitEvent(sU, L.v[sl], 0));
-            RUTV_CK(wy_right(sU, n, kc, V + r0 * ldv, ldv, Vv, Sv, p, w.W1u, w.W2u, w.gwsu, ge));
+            RUTV_CK(wy_right(sU, n, kc, V + r0 * ldv, ldv, Vv, Sv, p, w.W1u, w.W2u, gU));
           }
           RUTV_CK(transpose(sT, p, p, w.Rt, p, w.R, p));
         }
@@ -455,10 +496,10 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
         if (uv) {
           RUTV_CK(cudaEventRecord(L.s[sl], sT));
           RUTV_CK(cudaStreamWaitEvent(sU, L.s[sl], 0));
-          RUTV_CK(rot_right(sU, m, p, U + r0 * ldu, ldu, Us, w.tmpu, w.gwsu, ge));
-          RUTV_CK(rot_right(sU, n, p, V + r0 * ldv, ldv, Vs, w.tmpu, w.gwsu, ge));
+          RUTV_CK(rot_right(sU, m, p, U + r0 * ldu, ldu, Us, w.tmpu, gU));
+          RUTV_CK(rot_right(sU, n, p, V + r0 * ldv, ldv, Vs, w.tmpu, gU));
         }
-        RUTV_CK(rot_right(sT, r0, p, T + r0 * ldt, ldt, Vs, w.tmp, w.gws, ge));
+        RUTV_CK(rot_right(sT, r0, p, T + r0 * ldt, ldt, Vs, w.tmp, gT));
       }
       if (uv) RUTV_CK(cudaEventRecord(L.done[sl], sU));
     }
@@ -470,6 +511,8 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
 
 done:
   L.join(s);
+  if (w.ozT) cudaFreeAsync(w.ozT, s);
+  if (w.ozU) cudaFreeAsync(w.ozU, s);
   if (w.base) {
     cudaFreeAsync(w.base, s);
     cudaStreamSynchronize(s);

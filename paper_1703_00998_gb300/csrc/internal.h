@@ -18,7 +18,7 @@ constexpr int kFlagSlots = 8;
 
 // ---- prof.cu ----
 enum ProfClass { kProfGemm = 0, kProfPanel = 1, kProfTfactor = 2, kProfJacobi = 3, kProfGauss = 4,
-                 kProfOther = 5, kProfGemm32 = 6, kProfGemmTc = 7, kProfClasses = 8 };
+                 kProfOther = 5, kProfGemm32 = 6, kProfGemmTc = 7, kProfGemmOz = 8, kProfClasses = 9 };
 struct ProfTotals { double ms = 0.0; int64_t launches = 0; double flops = 0.0; double bytes = 0.0; };
 struct ProfToken { int idx; };
 void note_launch(int n = 1);
@@ -59,6 +59,13 @@ cudaError_t gemm_tc_tn(cudaStream_t s, int64_t m, int64_t n, int64_t k, float al
 cudaError_t gemm_tc(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, float alpha, const float* A,
                     int64_t lda, const float* B, int64_t ldb, float beta, float* D, int64_t ldd, float* work,
                     int64_t work_elems, int* err, bool split);
+// FP64 GEMM from BF16 tensor-core slice products (Ozaki scheme); work holds
+// gemm_oz_work_bytes(m, n, k) bytes (slices, scales, chunk partials).
+cudaError_t gemm_oz(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
+                    const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* D, int64_t ldd,
+                    void* work, size_t work_bytes, int* err);
+size_t gemm_oz_work_bytes(int64_t m, int64_t n, int64_t k);
+bool gemm_oz_supported();
 // Whether gemm_tc can take these operands (TMA alignment rules, driver entry point).
 bool gemm_tc_supported(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t m, int64_t n, int64_t k);
 

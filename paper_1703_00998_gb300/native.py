@@ -33,6 +33,7 @@ class Opts(ctypes.Structure):
         ("g_inject", ctypes.c_void_p),
         ("overlap", ctypes.c_int),
         ("tensor_cores", ctypes.c_int),
+        ("fp64_emulation", ctypes.c_int),
     ]
 
 
@@ -61,6 +62,8 @@ SIGNATURES = {
                              ctypes.c_float, _vp, _i64]),
     "randutv_sgemm_tc": (_i32, [ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, ctypes.c_float, _vp, _i64, _vp,
                                 _i64, ctypes.c_float, _vp, _i64, _i32]),
+    "randutv_dgemm_oz": (_i32, [ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, _f64, _vp, _i64, _vp, _i64, _f64,
+                                _vp, _i64]),
     "randutv_panel_qr": (_i32, [_i64, _i64, _vp, _i64, _vp, _vp, _vp]),
     "randutv_small_svd": (_i32, [_i64, _vp, _i64, _vp, _vp, _vp, _i32]),
     "randutv_profile_enable": (_i32, [_i32]),
@@ -72,7 +75,7 @@ SIGNATURES = {
 }
 
 PROF_GEMM, PROF_PANEL, PROF_TFACTOR, PROF_JACOBI, PROF_GAUSS, PROF_OTHER, PROF_GEMM32, PROF_GEMMTC = range(8)
-PROF_NAMES = ["gemm", "panel_qr", "tfactor", "jacobi", "gauss", "other", "gemm32", "gemm_tc"]
+PROF_NAMES = ["gemm", "panel_qr", "tfactor", "jacobi", "gauss", "other", "gemm32", "gemm_tc", "gemm_oz"]
 
 
 def profile_read(cls):

@@ -43,7 +43,8 @@ def test_strerror_and_defaults(lib):
     assert lib.randutv_strerror(0) == b"success"
     assert b"max_sweeps" in lib.randutv_strerror(2)
     o = native.default_opts()
-    assert (o.precision, o.form_uv, o.max_sweeps, o.p, o.seed, o.overlap, o.tensor_cores) == (0, 1, 30, 0, 998, 1, 1)
+    assert (o.precision, o.form_uv, o.max_sweeps, o.p, o.seed, o.overlap, o.tensor_cores, o.fp64_emulation) == (
+        0, 1, 30, 0, 998, 1, 1, 1)
     assert o.g_inject is None
 
 

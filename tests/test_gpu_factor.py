@@ -218,3 +218,15 @@ def test_fp64_overlap_off_matches(R):
     c = R.factor(dev(A), b=64, q=1, g_inject=g, overlap=False)
     for x, y in ((a.T, c.T), (a.U, c.U), (a.V, c.V)):
         assert float((x - y).abs().max()) <= 1e-10
+
+
+def test_fp64_emulation_matches_dfma(R):
+    # the Ozaki-scheme products are FP64-accurate: the same factorization as
+    # the DFMA GEMM to FP64 rounding (both against the same injected G)
+    A = synth.make_matrix("exp50", 700, 700, 41)
+    g = dev(synth.gaussian_stream(SEED, 700, 700, 64))
+    a = R.factor(dev(A), b=64, q=1, g_inject=g, fp64_emulation=True)
+    c = R.factor(dev(A), b=64, q=1, g_inject=g, fp64_emulation=False)
+    da, dc = host(a.T).diagonal(), host(c.T).diagonal()
+    nA = np.linalg.norm(A, 2)
+    assert np.max(np.abs(np.abs(da) - np.abs(dc)) / (np.abs(dc) + 700 * 2.0 ** -53 * nA / 1e-10)) <= 1e-10
