@@ -45,15 +45,15 @@ namespace {
 
 constexpr int OZ_S = 8;            // slices per operand, 7 bits each
 constexpr int OZ_KC = 128;         // K chunk: exact FP32 group sums
-constexpr int OZ_BM = 128, OZ_BN = 64;
+constexpr int OZ_BM = 128, OZ_BN = 32;   // 128 x 32 tiles: two CTAs per SM
 constexpr int OZ_KB = 64;          // K sub-block: 64 BF16 = 128 bytes = one swizzle row
-constexpr int OZ_ASTAGES = 4;
+constexpr int OZ_ASTAGES = 2;
 constexpr int OZ_A_BYTES = OZ_BM * OZ_KB * 2;   // 16 KB: one A slice, one sub-block
-constexpr int OZ_B_BYTES = OZ_BN * OZ_KB * 2;   // 8 KB: one B slice, one sub-block
+constexpr int OZ_B_BYTES = OZ_BN * OZ_KB * 2;   // 4 KB: one B slice, one sub-block
 constexpr int OZ_NT = 192;
-constexpr int OZ_B_ALL = 2 * OZ_S * OZ_B_BYTES; // 128 KB
+constexpr int OZ_B_ALL = 2 * OZ_S * OZ_B_BYTES; // 64 KB
 constexpr int OZ_SMEM = OZ_B_ALL + OZ_ASTAGES * OZ_A_BYTES + 1024 + 256;
-constexpr uint32_t OZ_TMEM_COLS = OZ_S * OZ_BN; // 8 groups x 64 columns = 512
+constexpr uint32_t OZ_TMEM_COLS = OZ_S * OZ_BN; // 8 groups x 32 columns = 256 (half of an SM's)
 static_assert(OZ_KC == 2 * OZ_KB, "two sub-blocks per chunk");
 static_assert(OZ_S * OZ_KC * 127 * 127 < (1 << 24), "group sums exact in FP32");
 
@@ -140,7 +140,7 @@ oz_slice_kernel(int64_t R, int64_t K, const double* __restrict__ X, int64_t ldx,
   }
 }
 
-__global__ void __launch_bounds__(OZ_NT, 1)
+__global__ void __launch_bounds__(OZ_NT, 2)
 gemm_oz_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                const int* __restrict__ eA, const int* __restrict__ eB, int MApad, int NBpad, int64_t M, int64_t N,
                double alpha, double beta, double* __restrict__ D, int64_t ldd, double* __restrict__ part,

@@ -47,7 +47,9 @@ def ready():
 
 
 @pytest.mark.parametrize("ta,tb", FORMS)
-@pytest.mark.parametrize("m,n,k", [(128, 64, 128), (300, 130, 64), (97, 45, 300), (256, 200, 1000), (5, 3, 1)])
+# (n < m <= ... runs the transposed-tile path; m <= n or n > 256 the direct one)
+@pytest.mark.parametrize("m,n,k", [(128, 64, 128), (300, 130, 64), (97, 45, 300), (256, 200, 1000), (5, 3, 1),
+                                   (64, 300, 200), (200, 333, 129), (700, 300, 100)])
 def test_oz_exact_on_small_integers(ready, m, n, k, ta, tb):
     rng = np.random.default_rng(m + 7 * n + k + 2 * ta + tb)
     A, B, oA, oB = operands(rng, m, n, k, ta, tb, lambda r, s: r.integers(-100, 101, s).astype(np.float64))
