@@ -199,13 +199,14 @@ struct Work {
   double *G, *Y, *Z, *tau, *R, *Rt, *gram, *W1, *W2, *d, *tmp;
   double *Vvr[kR], *Vur[kR], *Svr[kR], *Sur[kR], *Usr[kR], *Vsr[kR];
   double *W1u, *W2u, *tmpu, *gwsu;
+  double *tmps, *gwss;   // the SVD lane's rotation buffer and GEMM partials
   double *gws, *part, *jws, *red, *scal;
   int64_t gws_elems;
   unsigned* flags;
   void* base;
   size_t bytes;
-  void *ozT, *ozU;   // Ozaki GEMM workspaces of the two lanes (or null)
-  size_t ozb;
+  void *ozT, *ozU, *ozS;   // Ozaki GEMM workspaces of the T, U/V and SVD lanes (or null)
+  size_t ozb, ozbS;
 };
 
 // Largest Ozaki workspace any product of the factorization needs: the
@@ -239,6 +240,7 @@ static cudaError_t work_alloc(cudaStream_t s, int64_t m, int64_t n, int b, bool 
       {&w->Svr[0], bb}, {&w->Svr[1], bb}, {&w->Svr[2], bb}, {&w->Sur[0], bb}, {&w->Sur[1], bb}, {&w->Sur[2], bb},
       {&w->Usr[0], bb}, {&w->Usr[1], bb}, {&w->Usr[2], bb}, {&w->Vsr[0], bb}, {&w->Vsr[1], bb}, {&w->Vsr[2], bb},
       {&w->W1u, ux * mx * b}, {&w->W2u, ux * mx * b}, {&w->tmpu, ux * mx * b}, {&w->gwsu, ux * w->gws_elems},
+      {&w->tmps, mx * b}, {&w->gwss, w->gws_elems},
       {&w->gws, w->gws_elems}, {&w->part, panel_qr_part_elems(mx, b)}, {&w->jws, jacobi_work_elems(b)},
       {&w->red, kSumsqBlocks}, {&w->scal, 8},
   };
@@ -356,13 +358,17 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
     cudaError_t e = work_alloc(s, m, n, b, uv, &w);
     if (e == cudaSuccess && opts.fp64_emulation && gemm_oz_supported()) {
       w.ozb = oz_budget(m, n, b);
+      const int64_t mx = std::max(m, n);
+      w.ozbS = std::max(gemm_oz_work_bytes(b, mx, b), gemm_oz_work_bytes(mx, b, b));   // the rotations
       e = cudaMallocAsync(&w.ozT, w.ozb, s);
       if (e == cudaSuccess && uv) e = cudaMallocAsync(&w.ozU, w.ozb, s);
+      if (e == cudaSuccess) e = cudaMallocAsync(&w.ozS, w.ozbS, s);
     }
     if (e != cudaSuccess) {
       cudaGetLastError();
       snprintf(g_detail, sizeof(g_detail), "workspace: %s", cudaGetErrorString(e));
       if (w.ozT) cudaFreeAsync(w.ozT, s);
+      if (w.ozU) cudaFreeAsync(w.ozU, s);
       if (w.base) cudaFreeAsync(w.base, s);
       cudaStreamSynchronize(s);
       return e == cudaErrorMemoryAllocation ? RANDUTV_ENOMEM : RANDUTV_ECUDA;
@@ -376,13 +382,15 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
   // them, filling the SMs that the latency-bound panel QR and Jacobi SVD
   // leave idle.  No step of the T lane reads U or V, so only the ring slots
   // order the lanes.  overlap = 0 puts both on the caller's stream.
-  RUTV_CK(L.open(s, opts.overlap != 0 && uv));
+  RUTV_CK(L.open(s, opts.overlap != 0));
   {
-    cudaStream_t sT = L.t, sU = L.uv;
+    cudaStream_t sT = L.t, sU = L.uv, sS = L.sv;
     const int64_t ge = w.gws_elems;
     int* oz_err = reinterpret_cast<int*>(slot(w, 3) + 2);
     const G64 gT{w.ozT != nullptr, w.ozT, w.ozb, oz_err, w.gws, ge};
     const G64 gU{w.ozU != nullptr, w.ozU, w.ozb, oz_err, w.gwsu, ge};
+    const G64 gS{w.ozS != nullptr, w.ozS, w.ozbS, oz_err, w.gwss, ge};
+    int prev_sl = -1;   // ring slot of the previous randomized step (its rotations of T run on the SVD lane)
     RUTV_CK(copy_matrix(sT, m, n, A, lda, T, ldt));
     if (uv) {
       RUTV_CK(set_identity(sU, m, U, ldu));
@@ -429,6 +437,8 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
         RUTV_CK(gemm_f64(sT, true, false, b, b, kc, 1.0, Vv, kc, Vv, kc, 0.0, w.gram, b, w.gws, ge));
         RUTV_CK(tfactor_from_gram(sT, b, w.gram, w.tau, Sv));
         RUTV_CK(cudaEventRecord(L.v[sl], sT));
+        // rows I2 of the previous step are rotated on the SVD lane: wait for it
+        if (prev_sl >= 0) RUTV_CK(cudaStreamWaitEvent(sT, L.g[prev_sl], 0));
         RUTV_CK(wy_right(sT, m, kc, T + r0 * ldt, ldt, Vv, Sv, b, w.W1, w.W2, gT));
         if (uv) {
           RUTV_CK(cudaStreamWaitEvent(sU, L.v[sl], 0));
@@ -445,21 +455,28 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
         }
         RUTV_CK(wy_left_t(sT, kr, kc - b, T + r0 + c1 * ldt, ldt, Vu, Su, b, w.W1, w.W2, gT));
         RUTV_CK(fill(sT, kr, b, X, ldt, 0.0));
+        RUTV_CK(cudaEventRecord(L.e[sl], sT));
 
-        RUTV_CK(jacobi_svd(sT, b, w.R, b, Us, w.d, Vs, opts.max_sweeps, w.jws, slot(w, 2)));
-        set_diag_kernel<<<(b + 127) / 128, 128, 0, sT>>>(b, w.d, X, ldt);
+        // small SVD and the rotations of T on the SVD lane (they touch rows
+        // I2 and columns J2 only; the next step's sketch reads neither)
+        RUTV_CK(cudaStreamWaitEvent(sS, L.e[sl], 0));
+        RUTV_CK(jacobi_svd(sS, b, w.R, b, Us, w.d, Vs, opts.max_sweeps, w.jws, slot(w, 2)));
+        set_diag_kernel<<<(b + 127) / 128, 128, 0, sS>>>(b, w.d, X, ldt);
         note_launch();
         RUTV_CK(cudaGetLastError());
+        RUTV_CK(cudaEventRecord(L.s[sl], sS));
         if (uv) {
-          RUTV_CK(cudaEventRecord(L.s[sl], sT));
           RUTV_CK(cudaStreamWaitEvent(sU, L.s[sl], 0));
           RUTV_CK(rot_right(sU, m, b, U + r0 * ldu, ldu, Us, w.tmpu, gU));
           RUTV_CK(rot_right(sU, n, b, V + r0 * ldv, ldv, Vs, w.tmpu, gU));
         }
-        RUTV_CK(rot_left_t(sT, b, kc - b, T + r0 + c1 * ldt, ldt, Us, w.tmp, gT));
-        RUTV_CK(rot_right(sT, r0, b, T + r0 * ldt, ldt, Vs, w.tmp, gT));
+        RUTV_CK(rot_left_t(sS, b, kc - b, T + r0 + c1 * ldt, ldt, Us, w.tmps, gS));
+        RUTV_CK(rot_right(sS, r0, b, T + r0 * ldt, ldt, Vs, w.tmps, gS));
+        RUTV_CK(cudaEventRecord(L.g[sl], sS));
+        prev_sl = sl;
       } else {
         // ---- last block: full SVD, economically through a QR when not square
+        if (prev_sl >= 0) RUTV_CK(cudaStreamWaitEvent(sT, L.g[prev_sl], 0));
         int p;
         if (kr >= kc) {
           // QR first, also for a square block: one-sided Jacobi converges in a
@@ -513,6 +530,7 @@ done:
   L.join(s);
   if (w.ozT) cudaFreeAsync(w.ozT, s);
   if (w.ozU) cudaFreeAsync(w.ozU, s);
+  if (w.ozS) cudaFreeAsync(w.ozS, s);
   if (w.base) {
     cudaFreeAsync(w.base, s);
     cudaStreamSynchronize(s);

@@ -142,6 +142,7 @@ struct MWork {
   float *G, *Y, *Z, *Vv, *Vu, *S, *Us, *Vs, *W1, *W2, *tmp, *gws;
   float *Vvr[kRing], *Vur[kRing], *Svr[kRing], *Sur[kRing], *Usr[kRing], *Vsr[kRing];
   float *W1u, *W2u, *tmpu, *gwsu;
+  float *tmps, *gwss;   // the SVD lane's rotation buffer and GEMM partials
   // FP64
   double *G64, *Y64, *P64, *Vv64, *Vu64, *tau, *R, *Rt, *gram, *S64, *Us64, *Vs64, *d, *part, *jws, *gws64,
       *red, *scal;
@@ -182,7 +183,8 @@ cudaError_t mwork_alloc(cudaStream_t s, int64_t m, int64_t n, int b, MWork* w) {
              {&w->Svr[0], bb}, {&w->Svr[1], bb}, {&w->Svr[2], bb}, {&w->Sur[0], bb}, {&w->Sur[1], bb},
              {&w->Sur[2], bb}, {&w->Usr[0], bb}, {&w->Usr[1], bb}, {&w->Usr[2], bb}, {&w->Vsr[0], bb},
              {&w->Vsr[1], bb}, {&w->Vsr[2], bb},
-             {&w->W1u, mx * b}, {&w->W2u, mx * b}, {&w->tmpu, mx * b}, {&w->gwsu, w->gws_elems}};
+             {&w->W1u, mx * b}, {&w->W2u, mx * b}, {&w->tmpu, mx * b}, {&w->gwsu, w->gws_elems},
+             {&w->tmps, mx * b}, {&w->gwss, w->gws_elems}};
   static_assert(kRing == 3, "ring buffers listed above");
   I64 d[] = {{&w->G64, m * b}, {&w->Y64, mx * b}, {&w->P64, mx * b}, {&w->Vv64, mx * b}, {&w->Vu64, mx * b},
              {&w->tau, b}, {&w->R, bb}, {&w->Rt, bb}, {&w->gram, bb}, {&w->S64, bb}, {&w->Us64, bb},
@@ -340,9 +342,11 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
     gT = Mg{tcl, tc_err, w.gws, w.gws_elems};
     gU = Mg{tcl, tc_err, w.gwsu, w.gws_elems};
   }
-  RUTV_MCK(L.open(s, opts.overlap != 0 && uv));
+  RUTV_MCK(L.open(s, opts.overlap != 0));
   {
-    cudaStream_t sT = L.t, sU = L.uv;
+    cudaStream_t sT = L.t, sU = L.uv, sS = L.sv;
+    const Mg gS{false, gT.err, w.gwss, w.gws_elems};   // SVD lane: the rotations (CUDA cores)
+    int prev_sl = -1;   // ring slot of the previous randomized step (its rotations of T run on the SVD lane)
     RUTV_MCK(copy32(sT, m, n, A, lda, T, ldt));
     if (uv) {
       f32_identity_kernel<<<blocks_for(m * m), 256, 0, sU>>>(m, U, ldu);
@@ -391,6 +395,8 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
         RUTV_MCK(up(sT, kc, b, w.Y, kc, w.Y64, kc));
         RUTV_MCK(panel_wy(sT, kc, b, w.Y64, w.tau, w.Vv64, w.Rt, w.gram, w.S64, Vv, Sv, w, slot_of(w.flags, 0)));
         RUTV_MCK(cudaEventRecord(L.v[sl], sT));
+        // rows I2 of the previous step are rotated on the SVD lane: wait for it
+        if (prev_sl >= 0) RUTV_MCK(cudaStreamWaitEvent(sT, L.g[prev_sl], 0));
         RUTV_MCK(wy_right32(sT, gT, m, kc, T + r0 * ldt, ldt, Vv, Sv, b, w.W1, w.W2));
         if (uv) {
           RUTV_MCK(cudaStreamWaitEvent(sU, L.v[sl], 0));
@@ -406,23 +412,29 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
         }
         RUTV_MCK(wy_left_t32(sT, gT, kr, kc - b, T + r0 + c1 * ldt, ldt, Vu, Su, b, w.W1, w.W2));
         RUTV_MCK(fill32(sT, kr, b, X, ldt));
-        // small SVD in FP64
-        RUTV_MCK(jacobi_svd(sT, b, w.R, b, w.Us64, w.d, w.Vs64, opts.max_sweeps, w.jws, slot_of(w.flags, 2)));
-        f32_set_diag_kernel<<<(b + 127) / 128, 128, 0, sT>>>(b, w.d, X, ldt);
+        RUTV_MCK(cudaEventRecord(L.e[sl], sT));
+        // small SVD in FP64 and the rotations of T on the SVD lane (they touch
+        // rows I2 and columns J2 only; the next step's sketch reads neither)
+        RUTV_MCK(cudaStreamWaitEvent(sS, L.e[sl], 0));
+        RUTV_MCK(jacobi_svd(sS, b, w.R, b, w.Us64, w.d, w.Vs64, opts.max_sweeps, w.jws, slot_of(w.flags, 2)));
+        f32_set_diag_kernel<<<(b + 127) / 128, 128, 0, sS>>>(b, w.d, X, ldt);
         note_launch();
         RUTV_MCK(cudaGetLastError());
-        RUTV_MCK(down(sT, b, b, w.Us64, b, Us, b));
-        RUTV_MCK(down(sT, b, b, w.Vs64, b, Vs, b));
+        RUTV_MCK(down(sS, b, b, w.Us64, b, Us, b));
+        RUTV_MCK(down(sS, b, b, w.Vs64, b, Vs, b));
+        RUTV_MCK(cudaEventRecord(L.s[sl], sS));
         if (uv) {
-          RUTV_MCK(cudaEventRecord(L.s[sl], sT));
           RUTV_MCK(cudaStreamWaitEvent(sU, L.s[sl], 0));
           RUTV_MCK(rot_right32(sU, gU, m, b, U + r0 * ldu, ldu, Us, w.tmpu));
           RUTV_MCK(rot_right32(sU, gU, n, b, V + r0 * ldv, ldv, Vs, w.tmpu));
         }
-        RUTV_MCK(rot_left_t32(sT, gT, b, kc - b, T + r0 + c1 * ldt, ldt, Us, w.tmp));
-        RUTV_MCK(rot_right32(sT, gT, r0, b, T + r0 * ldt, ldt, Vs, w.tmp));
+        RUTV_MCK(rot_left_t32(sS, gS, b, kc - b, T + r0 + c1 * ldt, ldt, Us, w.tmps));
+        RUTV_MCK(rot_right32(sS, gS, r0, b, T + r0 * ldt, ldt, Vs, w.tmps));
+        RUTV_MCK(cudaEventRecord(L.g[sl], sS));
+        prev_sl = sl;
       } else {
         // last block: QR first (tall or square) or QR of the rows (wide), then the FP64 SVD
+        if (prev_sl >= 0) RUTV_MCK(cudaStreamWaitEvent(sT, L.g[prev_sl], 0));
         int p;
         if (kr >= kc) {
           p = static_cast<int>(kc);

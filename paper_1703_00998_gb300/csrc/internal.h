@@ -104,70 +104,76 @@ cudaError_t set_identity(cudaStream_t s, int64_t n, double* X, int64_t ldx);
 cudaError_t copy_matrix(cudaStream_t s, int64_t m, int64_t n, const double* A, int64_t lda,
                         double* B, int64_t ldb);
 
-// Streams of one factorization: the T chain (high priority) and the U/V
-// accumulation (low priority), forked from and joined back into the caller's
-// stream with events.  With overlap off both are the caller's stream.  The
-// per-step events v, u, s (reflectors of Y, of the panel, small factors
-// ready) and done (U/V stream finished that step's ring slot) are indexed by
-// ring slot.
+// Streams of one factorization, forked from and joined back into the
+// caller's stream with events: the T chain (high priority), the U/V
+// accumulation (low priority) and the small-SVD lane (high priority: the
+// SVD of step i and its rotations of T overlap step i+1's sketch and QR of
+// Y, which read only the trailing block).  With overlap off all three are
+// the caller's stream.  The per-step events are indexed by ring slot:
+// v, u, s (reflectors of Y, of the panel, small factors ready), e (the T
+// chain finished step i's left application: R and the trailing block are
+// final), g (the SVD lane finished step i's rotations of T), done (the U/V
+// stream finished that step's ring slot).
 struct Lanes {
   static constexpr int kSlots = 3;
-  cudaStream_t t = nullptr, uv = nullptr;
-  cudaEvent_t v[kSlots] = {}, u[kSlots] = {}, s[kSlots] = {}, done[kSlots] = {};
-  cudaEvent_t fork_ev = nullptr, join_t = nullptr, join_u = nullptr;
+  cudaStream_t t = nullptr, uv = nullptr, sv = nullptr;
+  cudaEvent_t v[kSlots] = {}, u[kSlots] = {}, s[kSlots] = {}, e[kSlots] = {}, g[kSlots] = {}, done[kSlots] = {};
+  cudaEvent_t fork_ev = nullptr, join_t = nullptr, join_u = nullptr, join_v = nullptr;
   bool own = false;
 
   cudaError_t open(cudaStream_t caller, bool overlap) {
-    cudaError_t e = cudaSuccess;
-    for (int i = 0; i < kSlots && e == cudaSuccess; ++i) {
-      e = cudaEventCreateWithFlags(&v[i], cudaEventDisableTiming);
-      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&u[i], cudaEventDisableTiming);
-      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s[i], cudaEventDisableTiming);
-      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming);
-    }
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join_t, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join_u, cudaEventDisableTiming);
-    if (e != cudaSuccess) return e;
+    cudaError_t err = cudaSuccess;
+    cudaEvent_t* sets[] = {v, u, s, e, g, done};
+    for (cudaEvent_t* set : sets)
+      for (int i = 0; i < kSlots && err == cudaSuccess; ++i) err = cudaEventCreateWithFlags(&set[i], cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&join_t, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&join_u, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&join_v, cudaEventDisableTiming);
+    if (err != cudaSuccess) return err;
     if (!overlap) {
-      t = uv = caller;
+      t = uv = sv = caller;
       return cudaSuccess;
     }
     int lo = 0, hi = 0;
-    e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&t, cudaStreamNonBlocking, hi);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&uv, cudaStreamNonBlocking, lo);
-    if (e != cudaSuccess) return e;
+    err = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (err == cudaSuccess) err = cudaStreamCreateWithPriority(&t, cudaStreamNonBlocking, hi);
+    if (err == cudaSuccess) err = cudaStreamCreateWithPriority(&uv, cudaStreamNonBlocking, lo);
+    if (err == cudaSuccess) err = cudaStreamCreateWithPriority(&sv, cudaStreamNonBlocking, hi);
+    if (err != cudaSuccess) return err;
     own = true;
-    e = cudaEventRecord(fork_ev, caller);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(t, fork_ev, 0);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(uv, fork_ev, 0);
-    return e;
+    err = cudaEventRecord(fork_ev, caller);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(t, fork_ev, 0);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(uv, fork_ev, 0);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(sv, fork_ev, 0);
+    return err;
   }
-  // Make the caller's stream wait for everything queued on t and uv.
+  // Make the caller's stream wait for everything queued on the lanes.
   cudaError_t join(cudaStream_t caller) {
     if (!own) return cudaSuccess;
-    cudaError_t e = cudaEventRecord(join_t, t);
-    if (e == cudaSuccess) e = cudaEventRecord(join_u, uv);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, join_t, 0);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, join_u, 0);
-    return e;
+    cudaError_t err = cudaEventRecord(join_t, t);
+    if (err == cudaSuccess) err = cudaEventRecord(join_u, uv);
+    if (err == cudaSuccess) err = cudaEventRecord(join_v, sv);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(caller, join_t, 0);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(caller, join_u, 0);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(caller, join_v, 0);
+    return err;
   }
   void close() {
     if (own) {
       cudaStreamDestroy(t);
       cudaStreamDestroy(uv);
+      cudaStreamDestroy(sv);
       own = false;
     }
-    for (int i = 0; i < kSlots; ++i) {
-      if (v[i]) cudaEventDestroy(v[i]);
-      if (u[i]) cudaEventDestroy(u[i]);
-      if (s[i]) cudaEventDestroy(s[i]);
-      if (done[i]) cudaEventDestroy(done[i]);
-    }
+    cudaEvent_t* sets[] = {v, u, s, e, g, done};
+    for (cudaEvent_t* set : sets)
+      for (int i = 0; i < kSlots; ++i)
+        if (set[i]) cudaEventDestroy(set[i]);
     if (fork_ev) cudaEventDestroy(fork_ev);
     if (join_t) cudaEventDestroy(join_t);
     if (join_u) cudaEventDestroy(join_u);
+    if (join_v) cudaEventDestroy(join_v);
   }
 };
 

@@ -5,7 +5,7 @@
 // whose reflector product is applied from the right, and the new b-column
 // panel T([I2,I3], J2), whose product is applied from the left (Fig. 4).
 //
-// GB300 design: one cooperative launch over up to 152 CTAs; each CTA keeps
+// GB300 design: one cooperative launch over up to 136 CTAs; each CTA keeps
 // its slice of rows of the panel in shared memory for the whole
 // factorization, so HBM is read and written once.  Column j needs, from all
 // rows, ||x(2:)||^2 and x^T P(:, c) for c > j; every CTA adds its partial
@@ -26,7 +26,9 @@ namespace rutv {
 
 constexpr int PQ_NT = 256;
 constexpr int PQ_WARPS = PQ_NT / 32;
-constexpr int kMaxCoopBlocks = kNumSMs;
+// 136 = 152 - 16: the panel QR of the next step's Y runs while the previous
+// step's small SVD holds one 16-CTA cluster
+constexpr int kMaxCoopBlocks = kNumSMs - 16;
 constexpr size_t kPqSmemBudget = 226 * 1024;   // of the 227 KB a CTA may use
 
 __global__ void __launch_bounds__(PQ_NT, 1)
