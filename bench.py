@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--no-verify", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--probe-oz", action="store_true",
+                    help="profiling aid: run two isolated Ozaki-scheme FP64 products (8192 x 8192 x 128 and "
+                         "8192 x 128 x 4096) once and exit")
     ap.add_argument("--fp64-emulation", type=int, default=1, choices=[0, 1],
                     help="FP64 form: 1 Ozaki-scheme tensor-core GEMM, 0 FP64 DFMA GEMM")
     ap.add_argument("--overlap", type=int, default=1, choices=[0, 1],
@@ -283,6 +286,29 @@ def run_mixed(args, lib, native, A, Tst64, n, b, q, stream, dist):
         del eye, A64, U, T, V
     out["speedup_vs_fp64"] = None
     return out
+
+
+def probe_oz():
+    """Two isolated products through randutv_dgemm_oz (Gaussian operands, beta = 0): a rank-128 update
+    D = A B^T (8192 x 8192 x 128) and a long-K product (8192 x 128 x 4096)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1703_00998_gb300 import native
+    lib = native.lib()
+    lib.randutv_set_stream(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    for m, n, k, ta, tb in ((8192, 8192, 128, False, True), (8192, 128, 4096, False, False)):
+        g = torch.Generator(device="cuda").manual_seed(m + n + k)
+        A = torch.randn((k, m) if ta else (m, k), dtype=torch.float64, device="cuda", generator=g)
+        B = torch.randn((n, k) if tb else (k, n), dtype=torch.float64, device="cuda", generator=g)
+        Ac, Bc = A.t().contiguous(), B.t().contiguous()
+        C = torch.zeros((n, m), dtype=torch.float64, device="cuda")
+        native.check(lib.randutv_dgemm_oz(b"T" if ta else b"N", b"T" if tb else b"N", m, n, k, 1.0, Ac.data_ptr(),
+                                          A.shape[0], Bc.data_ptr(), B.shape[0], 0.0, C.data_ptr(), m),
+                     "randutv_dgemm_oz")
+    torch.cuda.synchronize()
+    print(json.dumps({"probe_oz": "ok"}), flush=True)
+    return 0
 
 
 def run_own(args):
@@ -505,6 +531,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.probe_oz:
+        return probe_oz()
     return run_own(args)
 
 
