@@ -5,7 +5,7 @@
 // whose reflector product is applied from the right, and the new b-column
 // panel T([I2,I3], J2), whose product is applied from the left (Fig. 4).
 //
-// GB300 design: one cooperative launch over up to 136 CTAs; each CTA keeps
+// GB300 design: one cooperative launch over up to 152 CTAs; each CTA keeps
 // its slice of rows of the panel in shared memory for the whole
 // factorization, so HBM is read and written once.  Column j needs, from all
 // rows, ||x(2:)||^2 and x^T P(:, c) for c > j; every CTA adds its partial
@@ -26,9 +26,11 @@ namespace rutv {
 
 constexpr int PQ_NT = 256;
 constexpr int PQ_WARPS = PQ_NT / 32;
-// 136 = 152 - 16: the panel QR of the next step's Y runs while the previous
-// step's small SVD holds one 16-CTA cluster
-constexpr int kMaxCoopBlocks = kNumSMs - 16;
+constexpr int kMaxCoopBlocks = kNumSMs;
+// Preferred grid: 136 = 152 - 16, so the panel QR of the next step's Y runs
+// beside the previous step's small SVD (one 16-CTA cluster); a panel whose
+// rows do not fit 136 CTAs' shared memory takes up to 152.
+constexpr int kPreferredCoopBlocks = kNumSMs - 16;
 constexpr size_t kPqSmemBudget = 226 * 1024;   // of the 227 KB a CTA may use
 
 __global__ void __launch_bounds__(PQ_NT, 1)
@@ -149,7 +151,7 @@ struct PqGeom { int rpb; int nb; size_t smem; };
 
 PqGeom pq_geometry(int64_t k, int w) {
   const int64_t max_rows = static_cast<int64_t>(kPqSmemBudget / sizeof(double) - 3 * w) / w;
-  int64_t rpb = std::max<int64_t>(32, (k + kMaxCoopBlocks - 1) / kMaxCoopBlocks);
+  int64_t rpb = std::max<int64_t>(32, (k + kPreferredCoopBlocks - 1) / kPreferredCoopBlocks);
   rpb = std::min<int64_t>(rpb, std::max<int64_t>(1, max_rows));
   int64_t nb = (k + rpb - 1) / rpb;
   PqGeom g;
