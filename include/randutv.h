@@ -222,6 +222,22 @@ int randutv_dgemm_oz(char transa, char transb, int64_t m, int64_t n, int64_t k, 
                      const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                      double* C, int64_t ldc);
 
+/* FP32 counterpart of randutv_dgemm_oz (the mixed form's block-reflector
+ * applications and rotations): FP32 operands and result, 4 slices of 7 bits
+ * (28 bits) per row / column and K chunk of 128, the 10 slice pairs with
+ * s + t <= 3 summed exactly on the tensor cores, one rounding to FP32 per
+ * chunk, chunks summed in FP64.  Error per chunk <= 128 * 2^-27 * max|a| *
+ * max|b| over the chunk plus FP32 rounding: the accuracy class of an FP32
+ * GEMM with round-to-nearest accumulation on operands of even magnitude
+ * (the fixed point is relative to each row's chunk maximum).  A building
+ * block, not used by the factorization: there it was slower than the FP32
+ * CUDA-core GEMM and, on graded operands, less accurate.  Scratch: about
+ * 8 (m + n) k bytes plus 4 m n per chunk when k > 128 (cudaMallocAsync,
+ * synchronised). */
+int randutv_sgemm_oz(char transa, char transb, int64_t m, int64_t n, int64_t k, float alpha,
+                     const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
+                     float* C, int64_t ldc);
+
 /* Unpivoted Householder QR of the k x w panel P (k >= w >= 1, ldp >= k), in
  * place (eq. unpivQR; LAPACK dlarfg convention: beta = -sign(alpha)||x||,
  * tau = 0 when the part below the diagonal is zero).  On return P holds R on

@@ -1,6 +1,7 @@
-// FP64 GEMM from BF16 tensor-core products (the Ozaki scheme): D = alpha
-// op(A) op(B) + beta D, column-major FP64, for the FP64 form's sketch
-// products, block-reflector applications and rotations (Fig. 4).
+// FP64 and FP32 GEMMs from BF16 tensor-core products (the Ozaki scheme):
+// D = alpha op(A) op(B) + beta D, column-major, for the FP64 form's sketch
+// products, block-reflector applications and rotations, and for the mixed
+// form's block-reflector applications and rotations (Fig. 4).
 //
 // FP64 issues at ~4 flop/clk/SM on this GPU (1.2 TFLOP/s), BF16 tensor-core
 // products at ~1.9 PFLOP/s.  The scheme trades the FP64 multiply-adds for
@@ -22,6 +23,13 @@
 // length 128 with 56-bit inputs (error <= 128 * 2^-55 * max|a| * max|b| over
 // the chunk, plus one rounding); longer K is split into chunks whose FP64
 // results are summed in FP64 by a reduction kernel.
+// The FP32 form (FP32 operands and result) takes 4 slices of 7 bits (28
+// bits, above FP32's 24), the 10 pairs with s + t <= 3 in 4 group
+// accumulators (128 x 64 tiles), W = g0 2^21 + g1 2^14 + g2 2^7 + g3 and one
+// rounding to FP32 per chunk: error <= 128 * 2^-27 * max|a| * max|b| over the
+// chunk plus FP32 rounding, the accuracy class of an FP32 GEMM with round-to-
+// nearest accumulation (the tensor-core FP32 accumulator's truncation never
+// acts: every partial sum is an exact integer below 2^24).
 //
 // MMA kernel, one CTA per 128 x 64 tile of D and K chunk (192 threads):
 //   warp 0 (one thread): TMA loads (128B swizzle, K-major) of the 8 B slices
@@ -36,6 +44,8 @@
 // and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cstdio>
+#include <type_traits>
 #include "common.cuh"
 #include "internal.h"
 #include "tcgen05.cuh"
@@ -43,44 +53,73 @@
 namespace rutv {
 namespace {
 
-constexpr int OZ_S = 8;            // slices per operand, 7 bits each
 constexpr int OZ_KC = 128;         // K chunk: exact FP32 group sums
-constexpr int OZ_BM = 128, OZ_BN = 32;   // 128 x 32 tiles: two CTAs per SM
+constexpr int OZ_BM = 128;         // rows of a tile
 constexpr int OZ_KB = 64;          // K sub-block: 64 BF16 = 128 bytes = one swizzle row
 constexpr int OZ_ASTAGES = 2;
 constexpr int OZ_A_BYTES = OZ_BM * OZ_KB * 2;   // 16 KB: one A slice, one sub-block
-constexpr int OZ_B_BYTES = OZ_BN * OZ_KB * 2;   // 4 KB: one B slice, one sub-block
 constexpr int OZ_NT = 192;
-constexpr int OZ_B_ALL = 2 * OZ_S * OZ_B_BYTES; // 64 KB
-constexpr int OZ_SMEM = OZ_B_ALL + OZ_ASTAGES * OZ_A_BYTES + 1024 + 256;
-constexpr uint32_t OZ_TMEM_COLS = OZ_S * OZ_BN; // 8 groups x 32 columns = 256 (half of an SM's)
 static_assert(OZ_KC == 2 * OZ_KB, "two sub-blocks per chunk");
-static_assert(OZ_S * OZ_KC * 127 * 127 < (1 << 24), "group sums exact in FP32");
 
-// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major,
-// N = 64, M = 128.
-constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((OZ_BN >> 3) << 17) | ((OZ_BM >> 4) << 24);
+// One form of the scheme: S slices of 7 bits per operand, tiles of 128 x BN,
+// operands and result of type T.  S groups x BN columns of tensor memory
+// (256 in both forms, so two CTAs share an SM and one's epilogue overlaps
+// the other's products).
+template <int S_, int BN_, typename T_>
+struct OzCfg {
+  static constexpr int S = S_, BN = BN_;
+  using T = T_;
+  static constexpr bool F32 = std::is_same<T_, float>::value;
+  static constexpr int W = 7 * S;                           // fixed-point bits of the slices
+  static constexpr int B_BYTES = BN * OZ_KB * 2;            // one B slice, one sub-block
+  static constexpr int B_ALL = 2 * S * B_BYTES;
+  static constexpr int SMEM = B_ALL + OZ_ASTAGES * OZ_A_BYTES + 1024 + 256;
+  static constexpr uint32_t TMEM_COLS = S * BN;
+  // instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, N = BN, M = 128
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((BN >> 3) << 17) | ((OZ_BM >> 4) << 24);
+  static_assert(S * OZ_KC * 127 * 127 < (1 << 24), "group sums exact in FP32");
+  static_assert(SMEM <= 113 * 1024 && TMEM_COLS <= 256, "two CTAs per SM");
+};
+using Oz64 = OzCfg<8, 32, double>;   // 56-bit slices: FP64 products
+using Oz32 = OzCfg<4, 64, float>;    // 28-bit slices: FP32 products
 
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-      ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(kIdescBf16), "r"(accumulate)
+      ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+
+// Bit layout of the element types: exponent field position and width, and
+// (bias + mantissa bits), so that |x| = mant 2^(max(bexp, 1) - BM) with the
+// implicit bit in mant.
+template <typename T> struct FBits;
+template <> struct FBits<double> {
+  static constexpr int MB = 52, EB = 11, BM = 1075, EBIAS = 1022;
+  __device__ static long long bits(double x) { return __double_as_longlong(x); }
+};
+template <> struct FBits<float> {
+  static constexpr int MB = 23, EB = 8, BM = 150, EBIAS = 126;
+  __device__ static long long bits(float x) { return static_cast<long long>(__float_as_int(x)); }
+};
 
 // Slices of an R x K operand X (element (r, k) at X[r + k ldx], or at
 // X[k + r ldx] when kcontig), per K chunk: S[(j Rpad + r) Kpad + k] (BF16,
 // K contiguous) and e[c Rpad + r].  Rows r >= R and columns k >= K are zero.
 // One CTA of 128 threads per 32 rows x one chunk, staged through shared
-// memory so that both the FP64 reads and the BF16 writes are coalesced.
+// memory so that both the reads and the BF16 writes are coalesced.
 // Integer arithmetic only (FP64 is the slow pipe here): the scale e is the
-// largest biased exponent of the row's chunk minus 1022 (so |x| < 2^e), and
-// the slices are the 7-bit groups of the 56-bit fixed-point magnitude
-// trunc(|x| 2^(56 - e)), each with the sign of x.
+// largest biased exponent of the row's chunk minus the bias (so |x| < 2^e),
+// and the slices are the 7-bit groups of the W-bit fixed-point magnitude
+// trunc(|x| 2^(W - e)), each with the sign of x.
+template <int S, typename T>
 __global__ void __launch_bounds__(128)
-oz_slice_kernel(int64_t R, int64_t K, const double* __restrict__ X, int64_t ldx, bool kcontig, int64_t Rpad,
-                int64_t Kpad, __nv_bfloat16* __restrict__ S, int* __restrict__ E) {
+oz_slice_kernel(int64_t R, int64_t K, const T* __restrict__ X, int64_t ldx, bool kcontig, int64_t Rpad,
+                int64_t Kpad, __nv_bfloat16* __restrict__ Sl, int* __restrict__ E) {
+  using F = FBits<T>;
+  constexpr int W = 7 * S;
   __shared__ long long tile[32][OZ_KC + 1];
   __shared__ int s_e[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -91,16 +130,17 @@ oz_slice_kernel(int64_t R, int64_t K, const double* __restrict__ X, int64_t ldx,
     if (kcontig) { kk = idx % OZ_KC; i = idx / OZ_KC; }
     else { i = idx % 32; kk = idx / 32; }
     const int64_t r = r0 + i, k = k0 + kk;
-    double v = 0.0;
+    T v = T(0);
     if (r < R && k < K) v = kcontig ? X[k + r * ldx] : X[r + k * ldx];
-    tile[i][kk] = __double_as_longlong(v);
+    tile[i][kk] = F::bits(v);
   }
   __syncthreads();
+  constexpr long long EMASK = (1ll << F::EB) - 1;
   for (int i = warp; i < 32; i += 4) {
     int be = 0;   // largest biased exponent of the row's chunk
-    for (int kk = lane; kk < OZ_KC; kk += 32) be = max(be, static_cast<int>((tile[i][kk] >> 52) & 0x7ff));
+    for (int kk = lane; kk < OZ_KC; kk += 32) be = max(be, static_cast<int>((tile[i][kk] >> F::MB) & EMASK));
     be = __reduce_max_sync(0xffffffffu, be);
-    if (lane == 0) s_e[i] = (be == 0) ? 0 : be - 1022;   // zero (or subnormal-only) row: e = 0
+    if (lane == 0) s_e[i] = (be == 0) ? 0 : be - F::EBIAS;   // zero (or subnormal-only) row: e = 0
   }
   __syncthreads();
   if (tid < 32 && r0 + tid < Rpad) E[static_cast<int64_t>(blockIdx.y) * Rpad + r0 + tid] = s_e[tid];
@@ -113,21 +153,21 @@ oz_slice_kernel(int64_t R, int64_t K, const double* __restrict__ X, int64_t ldx,
     bool neg[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const long long bits = tile[i][lane * 4 + q];
-      const int bexp = static_cast<int>((bits >> 52) & 0x7ff);
-      neg[q] = bits < 0;
+      const long long b = tile[i][lane * 4 + q];
+      const int bexp = static_cast<int>((b >> F::MB) & EMASK);
+      neg[q] = (b >> (F::MB + F::EB)) & 1;
       const unsigned long long mant =
-          (static_cast<unsigned long long>(bits) & 0xFFFFFFFFFFFFFull) | (bexp ? (1ull << 52) : 0ull);
-      // |x| = mant 2^(max(bexp,1) - 1075); magnitude in units of 2^(e - 56)
-      const int sh = max(bexp, 1) - 1019 - e;   // <= 3 because |x| < 2^e
+          (static_cast<unsigned long long>(b) & ((1ull << F::MB) - 1)) | (bexp ? (1ull << F::MB) : 0ull);
+      // |x| = mant 2^(max(bexp,1) - BM); magnitude in units of 2^(e - W)
+      const int sh = max(bexp, 1) - (F::BM - W) - e;   // <= 3 (FP64) / 4 (FP32) because |x| < 2^e
       mag[q] = (sh >= 0) ? (mant << sh) : (sh > -64 ? (mant >> (-sh)) : 0ull);
     }
 #pragma unroll
-    for (int j = 0; j < OZ_S; ++j) {
+    for (int j = 0; j < S; ++j) {
       __nv_bfloat16 out[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int v = static_cast<int>((mag[q] >> (49 - 7 * j)) & 127ull);
+        const int v = static_cast<int>((mag[q] >> (W - 7 * (j + 1))) & 127ull);
         out[q] = __float2bfloat16_rn(static_cast<float>(neg[q] ? -v : v));   // exact: 7 bits
       }
       uint2 pk;
@@ -135,34 +175,37 @@ oz_slice_kernel(int64_t R, int64_t K, const double* __restrict__ X, int64_t ldx,
              (static_cast<uint32_t>(__bfloat16_as_ushort(out[1])) << 16);
       pk.y = static_cast<uint32_t>(__bfloat16_as_ushort(out[2])) |
              (static_cast<uint32_t>(__bfloat16_as_ushort(out[3])) << 16);
-      *reinterpret_cast<uint2*>(S + (static_cast<int64_t>(j) * Rpad + r) * Kpad + k0 + lane * 4) = pk;
+      *reinterpret_cast<uint2*>(Sl + (static_cast<int64_t>(j) * Rpad + r) * Kpad + k0 + lane * 4) = pk;
     }
   }
 }
 
+template <class C>
 __global__ void __launch_bounds__(OZ_NT, 2)
 gemm_oz_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                const int* __restrict__ eA, const int* __restrict__ eB, int MApad, int NBpad, int64_t M, int64_t N,
-               double alpha, double beta, double* __restrict__ D, int64_t ldd, double* __restrict__ part,
-               int* __restrict__ err) {
+               typename C::T alpha, typename C::T beta, typename C::T* __restrict__ D, int64_t ldd,
+               typename C::T* __restrict__ part, int* __restrict__ err) {
+  using T = typename C::T;
+  constexpr int S = C::S, BN = C::BN;
   extern __shared__ __align__(1024) unsigned char oz_smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(oz_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  auto tileB = [&](int kb, int t) { return base + (kb * OZ_S + t) * OZ_B_BYTES; };
-  auto tileA = [&](int st) { return base + OZ_B_ALL + st * OZ_A_BYTES; };
-  uint64_t* bfull = reinterpret_cast<uint64_t*>(base + OZ_B_ALL + OZ_ASTAGES * OZ_A_BYTES);   // [2]
+  auto tileB = [&](int kb, int t) { return base + (kb * S + t) * C::B_BYTES; };
+  auto tileA = [&](int st) { return base + C::B_ALL + st * OZ_A_BYTES; };
+  uint64_t* bfull = reinterpret_cast<uint64_t*>(base + C::B_ALL + OZ_ASTAGES * OZ_A_BYTES);   // [2]
   uint64_t* afull = bfull + 2;                 // [OZ_ASTAGES]
   uint64_t* aempty = afull + OZ_ASTAGES;       // [OZ_ASTAGES]
   uint64_t* done = aempty + OZ_ASTAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   __shared__ int s_fail;
-  __shared__ int s_eB[OZ_BN];
+  __shared__ int s_eB[BN];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = static_cast<int>(blockIdx.x) * OZ_BM;
-  const int n0 = static_cast<int>(blockIdx.y) * OZ_BN;
+  const int n0 = static_cast<int>(blockIdx.y) * BN;
   const int z = static_cast<int>(blockIdx.z);
-  constexpr int NA = 2 * OZ_S;   // A slice sub-blocks per CTA
+  constexpr int NA = 2 * S;   // A slice sub-blocks per CTA
 
   if (tid == 0) {
     s_fail = 0;
@@ -174,10 +217,10 @@ gemm_oz_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (tid < OZ_BN) s_eB[tid] = eB[static_cast<int64_t>(z) * NBpad + n0 + tid];
-  if (warp == 0) {   // all 512 columns: the 8 group accumulators
+  if (tid < BN) s_eB[tid] = eB[static_cast<int64_t>(z) * NBpad + n0 + tid];
+  if (warp == 0) {   // the S group accumulators: half of tensor memory, so two CTAs share an SM
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(OZ_TMEM_COLS)
+                 "r"(C::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -190,12 +233,12 @@ gemm_oz_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   const int kx0 = z * OZ_KC;
 
   if (warp == 0 && lane == 0) {
-    // producer: B slices of a sub-block, then its 8 A slices through the ring
+    // producer: B slices of a sub-block, then its S A slices through the ring
     for (int i = 0; i < NA; ++i) {
-      const int kb = i / OZ_S, s = i % OZ_S, st = i % OZ_ASTAGES;
+      const int kb = i / S, s = i % S, st = i % OZ_ASTAGES;
       if (s == 0) {
-        mbar_expect_tx(&bfull[kb], OZ_S * OZ_B_BYTES);
-        for (int t = 0; t < OZ_S; ++t) tma_load_2d(tileB(kb, t), &mapB, kx0 + kb * OZ_KB, t * NBpad + n0, &bfull[kb]);
+        mbar_expect_tx(&bfull[kb], S * C::B_BYTES);
+        for (int t = 0; t < S; ++t) tma_load_2d(tileB(kb, t), &mapB, kx0 + kb * OZ_KB, t * NBpad + n0, &bfull[kb]);
         ++issued_b;
       }
       if (!mbar_wait(&aempty[st], ((i / OZ_ASTAGES) & 1) ^ 1, t0)) { s_fail = 1; break; }
@@ -207,18 +250,18 @@ gemm_oz_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     // MMA issuer
     uint32_t inited = 0;   // groups that have received their first product
     for (int i = 0; i < NA; ++i) {
-      const int kb = i / OZ_S, s = i % OZ_S, st = i % OZ_ASTAGES;
+      const int kb = i / S, s = i % S, st = i % OZ_ASTAGES;
       if (s == 0 && !mbar_wait(&bfull[kb], 0, t0)) { s_fail = 1; break; }
       if (!mbar_wait(&afull[st], (i / OZ_ASTAGES) & 1, t0)) { s_fail = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint64_t da = kmajor_sw128_desc(smem_u32(tileA(st)));
-      for (int t = 0; t + s < OZ_S; ++t) {
+      for (int t = 0; t + s < S; ++t) {
         const int g = s + t;
         const uint64_t db = kmajor_sw128_desc(smem_u32(tileB(kb, t)));
-        const uint32_t dacc = tmem + static_cast<uint32_t>(g * OZ_BN);
+        const uint32_t dacc = tmem + static_cast<uint32_t>(g * BN);
 #pragma unroll
         for (int kk = 0; kk < OZ_KB / 16; ++kk)   // K = 16 per instruction: 32 bytes (+2 in 16 B units)
-          mma_bf16(dacc, da + 2ull * kk, db + 2ull * kk, (((inited >> g) & 1u) || kk > 0) ? 1u : 0u);
+          mma_bf16(dacc, da + 2ull * kk, db + 2ull * kk, C::IDESC, (((inited >> g) & 1u) || kk > 0) ? 1u : 0u);
         inited |= 1u << g;
       }
       mma_commit(&aempty[st]);
@@ -238,30 +281,40 @@ gemm_oz_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     const int quarter = warp & 3;   // the 32 tensor-memory lanes this warp may read
     const int64_t row = m0 + quarter * 32 + lane;
     const int ea = eA[static_cast<int64_t>(z) * MApad + m0 + quarter * 32 + lane];
-    for (int c0 = 0; c0 < OZ_BN; c0 += 8) {
-      uint32_t r[OZ_S][8];
+    for (int c0 = 0; c0 < BN; c0 += 8) {
+      uint32_t r[S][8];
 #pragma unroll
-      for (int g = 0; g < OZ_S; ++g)
-        tmem_ld8(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + static_cast<uint32_t>(g * OZ_BN + c0), r[g]);
+      for (int g = 0; g < S; ++g)
+        tmem_ld8(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + static_cast<uint32_t>(g * BN + c0), r[g]);
       if (row < M) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int64_t col = n0 + c0 + j;
           if (col >= N) break;
-          long long gi[OZ_S];
+          long long gi[S];
 #pragma unroll
-          for (int g = 0; g < OZ_S; ++g) gi[g] = static_cast<long long>(__float2int_rn(__uint_as_float(r[g][j])));
-          const long long H = (gi[0] << 14) + (gi[1] << 7) + gi[2];
-          const long long L = (gi[3] << 28) + (gi[4] << 21) + (gi[5] << 14) + (gi[6] << 7) + gi[7];
-          double v = fma(static_cast<double>(H), 0x1p35, static_cast<double>(L));   // one rounding
-          const int sc = ea + s_eB[c0 + j] - 63;
-          v = (sc > -1022 && sc < 1023) ? v * __longlong_as_double(static_cast<long long>(1023 + sc) << 52)
-                                        : ldexp(v, sc);
+          for (int g = 0; g < S; ++g) gi[g] = static_cast<long long>(__float2int_rn(__uint_as_float(r[g][j])));
+          const int sc0 = ea + s_eB[c0 + j];
+          T v;
+          if constexpr (C::F32) {
+            // W 2^-35 = g0 2^-14 + g1 2^-21 + g2 2^-28 + g3 2^-35, |W| < 2^45: one rounding to FP32
+            const long long Wv = (gi[0] << 21) + (gi[1] << 14) + (gi[2] << 7) + gi[3];
+            v = __ll2float_rn(Wv);
+            const int sc = sc0 - 35;
+            v = (sc > -126 && sc < 128) ? v * __int_as_float((127 + sc) << 23) : ldexpf(v, sc);
+          } else {
+            const long long H = (gi[0] << 14) + (gi[1] << 7) + gi[2];
+            const long long L = (gi[3] << 28) + (gi[4] << 21) + (gi[5] << 14) + (gi[6] << 7) + gi[7];
+            v = fma(static_cast<double>(H), 0x1p35, static_cast<double>(L));   // one rounding
+            const int sc = sc0 - 63;
+            v = (sc > -1022 && sc < 1023) ? v * __longlong_as_double(static_cast<long long>(1023 + sc) << 52)
+                                          : ldexp(v, sc);
+          }
           if (part) {
             part[static_cast<int64_t>(z) * M * N + row + col * M] = v;
           } else {
-            double* dp = D + row + col * ldd;
-            *dp = (beta == 0.0) ? alpha * v : fma(alpha, v, beta * *dp);
+            T* dp = D + row + col * ldd;
+            *dp = (beta == T(0)) ? alpha * v : fma(alpha, v, beta * *dp);
           }
         }
       }
@@ -277,26 +330,28 @@ gemm_oz_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
   }
 }
 
-// D = alpha sum_z part[z] + beta D (FP64, chunks in order).
-__global__ void oz_reduce_kernel(int64_t M, int64_t N, int nch, double alpha, const double* __restrict__ part,
-                                 double beta, double* __restrict__ D, int64_t ldd) {
+// D = alpha sum_z part[z] + beta D (chunks in order, summed in FP64).
+template <typename T>
+__global__ void oz_reduce_kernel(int64_t M, int64_t N, int nch, T alpha, const T* __restrict__ part, T beta,
+                                 T* __restrict__ D, int64_t ldd) {
   const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (t >= M * N) return;
   double s = 0.0;
-  for (int z = 0; z < nch; ++z) s += part[static_cast<int64_t>(z) * M * N + t];
-  double* dp = D + (t % M) + (t / M) * ldd;
-  *dp = (beta == 0.0) ? alpha * s : fma(alpha, s, beta * *dp);
+  for (int z = 0; z < nch; ++z) s += static_cast<double>(part[static_cast<int64_t>(z) * M * N + t]);
+  T* dp = D + (t % M) + (t / M) * ldd;
+  *dp = (beta == T(0)) ? static_cast<T>(alpha * s) : static_cast<T>(fma(static_cast<double>(alpha), s, static_cast<double>(beta) * static_cast<double>(*dp)));
 }
 
-__global__ void oz_scale_kernel(int64_t M, int64_t N, double beta, double* __restrict__ D, int64_t ldd) {
+template <typename T>
+__global__ void oz_scale_kernel(int64_t M, int64_t N, T beta, T* __restrict__ D, int64_t ldd) {
   const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (t >= M * N) return;
-  double* dp = D + (t % M) + (t / M) * ldd;
-  *dp = (beta == 0.0) ? 0.0 : beta * *dp;
+  T* dp = D + (t % M) + (t / M) * ldd;
+  *dp = (beta == T(0)) ? T(0) : beta * *dp;
 }
 
 // 2-D map of a slice array: rows = slices x Rpad, Kpad BF16 per row, box
@@ -322,97 +377,121 @@ struct OzLayout {
   size_t sa, ea, sb, eb, pt, total;   // byte sizes
 };
 
+template <class C>
 OzLayout oz_layout(int64_t m, int64_t n, int64_t k) {
   OzLayout L;
   L.nch = static_cast<int>((k + OZ_KC - 1) / OZ_KC);
   L.MApad = rup(m, OZ_BM);
-  L.NBpad = rup(n, OZ_BN);
+  L.NBpad = rup(n, C::BN);
   L.Kpad = static_cast<int64_t>(L.nch) * OZ_KC;
-  L.sa = al256(static_cast<size_t>(OZ_S) * L.MApad * L.Kpad * 2);
+  L.sa = al256(static_cast<size_t>(C::S) * L.MApad * L.Kpad * 2);
   L.ea = al256(static_cast<size_t>(L.nch) * L.MApad * 4);
-  L.sb = al256(static_cast<size_t>(OZ_S) * L.NBpad * L.Kpad * 2);
+  L.sb = al256(static_cast<size_t>(C::S) * L.NBpad * L.Kpad * 2);
   L.eb = al256(static_cast<size_t>(L.nch) * L.NBpad * 4);
-  L.pt = L.nch > 1 ? al256(static_cast<size_t>(L.nch) * m * n * 8) : 0;
+  L.pt = L.nch > 1 ? al256(static_cast<size_t>(L.nch) * m * n * sizeof(typename C::T)) : 0;
   L.total = L.sa + L.ea + L.sb + L.eb + L.pt;
   return L;
+}
+
+// D (m x n) = alpha op(A) op(B) + beta D, column-major: op(A) = A^T with A
+// k x m (ta) or A (m x k); op(B) = B (k x n, !tb) or B^T with B n x k.
+// work: oz_layout<C>(m, n, k).total bytes of device memory.
+template <class C>
+cudaError_t oz_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, typename C::T alpha,
+                   const typename C::T* A, int64_t lda, const typename C::T* B, int64_t ldb, typename C::T beta,
+                   typename C::T* D, int64_t ldd, void* work, size_t work_bytes, int* err, int prof_class) {
+  using T = typename C::T;
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  const ProfToken tok = prof_begin(s, prof_class);
+  cudaError_t e = cudaSuccess;
+  if (k <= 0) {
+    oz_scale_kernel<T><<<static_cast<unsigned>((m * n + 255) / 256), 256, 0, s>>>(m, n, beta, D, ldd);
+    note_launch();
+    e = cudaGetLastError();
+    prof_end(s, tok, 0.0, 2.0 * sizeof(T) * m * n);
+    return e;
+  }
+  const OzLayout L = oz_layout<C>(m, n, k);
+  if (work_bytes < L.total || !work) return cudaErrorInvalidValue;
+  if (L.MApad * C::S >= (1ll << 31) || L.NBpad * C::S >= (1ll << 31) || L.nch > 65535) return cudaErrorInvalidValue;
+  char* w = static_cast<char*>(work);
+  auto* SA = reinterpret_cast<__nv_bfloat16*>(w);
+  int* EA = reinterpret_cast<int*>(w + L.sa);
+  auto* SB = reinterpret_cast<__nv_bfloat16*>(w + L.sa + L.ea);
+  int* EB = reinterpret_cast<int*>(w + L.sa + L.ea + L.sb);
+  T* part = L.nch > 1 ? reinterpret_cast<T*>(w + L.sa + L.ea + L.sb + L.eb) : nullptr;
+  // op(A) rows = the m dimension, K contiguous when ta; op(B) columns = the n
+  // dimension, K contiguous when !tb
+  oz_slice_kernel<C::S, T><<<dim3(static_cast<unsigned>(L.MApad / 32), static_cast<unsigned>(L.nch)), 128, 0, s>>>(
+      m, k, A, lda, ta, L.MApad, L.Kpad, SA, EA);
+  oz_slice_kernel<C::S, T><<<dim3(static_cast<unsigned>(L.NBpad / 32), static_cast<unsigned>(L.nch)), 128, 0, s>>>(
+      n, k, B, ldb, !tb, L.NBpad, L.Kpad, SB, EB);
+  note_launch(2);
+  e = cudaGetLastError();
+  CUtensorMap ma, mb;
+  if (e == cudaSuccess && (!make_slice_map(&ma, SA, L.Kpad, C::S * L.MApad, OZ_BM) ||
+                           !make_slice_map(&mb, SB, L.Kpad, C::S * L.NBpad, C::BN)))
+    e = cudaErrorInvalidValue;
+  static bool attr = false;
+  if (e == cudaSuccess && !attr) {
+    e = cudaFuncSetAttribute(gemm_oz_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e == cudaSuccess) attr = true;
+  }
+  if (e == cudaSuccess) {
+    dim3 grid(static_cast<unsigned>(L.MApad / OZ_BM), static_cast<unsigned>(L.NBpad / C::BN),
+              static_cast<unsigned>(L.nch));
+    gemm_oz_kernel<C><<<grid, OZ_NT, C::SMEM, s>>>(ma, mb, EA, EB, static_cast<int>(L.MApad),
+                                                   static_cast<int>(L.NBpad), m, n, alpha, beta, D, ldd, part, err);
+    note_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && part) {
+    oz_reduce_kernel<T><<<static_cast<unsigned>((m * n + 255) / 256), 256, 0, s>>>(m, n, L.nch, alpha, part, beta,
+                                                                                  D, ldd);
+    note_launch();
+    e = cudaGetLastError();
+  }
+  // flops of the product it stands for; bytes: operands once, slices written and read
+  prof_end(s, tok, 2.0 * m * n * k,
+           sizeof(T) * (m * k + k * n + m * n * (beta != T(0) ? 2.0 : 1.0)) + 2.0 * static_cast<double>(L.sa + L.sb));
+  return e;
 }
 
 }  // namespace
 
 size_t gemm_oz_work_bytes(int64_t m, int64_t n, int64_t k) {
   if (m <= 0 || n <= 0 || k <= 0) return 0;
-  return oz_layout(m, n, k).total;
+  return oz_layout<Oz64>(m, n, k).total;
+}
+
+size_t gemm_oz32_work_bytes(int64_t m, int64_t n, int64_t k) {
+  if (m <= 0 || n <= 0 || k <= 0) return 0;
+  return oz_layout<Oz32>(m, n, k).total;
 }
 
 bool gemm_oz_supported() { return encode_fn() != nullptr; }
 
-// D (m x n) = alpha op(A) op(B) + beta D, FP64 column-major: op(A) = A^T with
-// A k x m (ta) or A (m x k); op(B) = B (k x n, !tb) or B^T with B n x k.
-// work: gemm_oz_work_bytes(m, n, k) bytes of device memory.
 cudaError_t gemm_oz(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* D, int64_t ldd,
                     void* work, size_t work_bytes, int* err) {
-  if (m <= 0 || n <= 0) return cudaSuccess;
-  const ProfToken tok = prof_begin(s, kProfGemmOz);
-  cudaError_t e = cudaSuccess;
-  if (k <= 0) {
-    oz_scale_kernel<<<static_cast<unsigned>((m * n + 255) / 256), 256, 0, s>>>(m, n, beta, D, ldd);
-    note_launch();
-    e = cudaGetLastError();
-    prof_end(s, tok, 0.0, 16.0 * m * n);
-    return e;
-  }
-  const OzLayout L = oz_layout(m, n, k);
-  if (work_bytes < L.total || !work) return cudaErrorInvalidValue;
-  if (L.MApad * OZ_S >= (1ll << 31) || L.NBpad * OZ_S >= (1ll << 31) || L.nch > 65535) return cudaErrorInvalidValue;
-  char* w = static_cast<char*>(work);
-  auto* SA = reinterpret_cast<__nv_bfloat16*>(w);
-  int* EA = reinterpret_cast<int*>(w + L.sa);
-  auto* SB = reinterpret_cast<__nv_bfloat16*>(w + L.sa + L.ea);
-  int* EB = reinterpret_cast<int*>(w + L.sa + L.ea + L.sb);
-  double* part = L.nch > 1 ? reinterpret_cast<double*>(w + L.sa + L.ea + L.sb + L.eb) : nullptr;
-  // op(A) rows = the m dimension, K contiguous when ta; op(B) columns = the n
-  // dimension, K contiguous when !tb
-  oz_slice_kernel<<<dim3(static_cast<unsigned>(L.MApad / 32), static_cast<unsigned>(L.nch)), 128, 0, s>>>(
-      m, k, A, lda, ta, L.MApad, L.Kpad, SA, EA);
-  oz_slice_kernel<<<dim3(static_cast<unsigned>(L.NBpad / 32), static_cast<unsigned>(L.nch)), 128, 0, s>>>(
-      n, k, B, ldb, !tb, L.NBpad, L.Kpad, SB, EB);
-  note_launch(2);
-  e = cudaGetLastError();
-  CUtensorMap ma, mb;
-  if (e == cudaSuccess && (!make_slice_map(&ma, SA, L.Kpad, OZ_S * L.MApad, OZ_BM) ||
-                           !make_slice_map(&mb, SB, L.Kpad, OZ_S * L.NBpad, OZ_BN)))
-    e = cudaErrorInvalidValue;
-  static bool attr = false;
-  if (e == cudaSuccess && !attr) {
-    e = cudaFuncSetAttribute(gemm_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
-    if (e == cudaSuccess) attr = true;
-  }
-  if (e == cudaSuccess) {
-    dim3 grid(static_cast<unsigned>(L.MApad / OZ_BM), static_cast<unsigned>(L.NBpad / OZ_BN),
-              static_cast<unsigned>(L.nch));
-    gemm_oz_kernel<<<grid, OZ_NT, OZ_SMEM, s>>>(ma, mb, EA, EB, static_cast<int>(L.MApad), static_cast<int>(L.NBpad),
-                                                m, n, alpha, beta, D, ldd, part, err);
-    note_launch();
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess && part) {
-    oz_reduce_kernel<<<static_cast<unsigned>((m * n + 255) / 256), 256, 0, s>>>(m, n, L.nch, alpha, part, beta, D,
-                                                                               ldd);
-    note_launch();
-    e = cudaGetLastError();
-  }
-  // flops of the FP64 product it stands for; bytes: FP64 operands once, slices written and read
-  prof_end(s, tok, 2.0 * m * n * k,
-           8.0 * (m * k + k * n + m * n * (beta != 0.0 ? 2.0 : 1.0)) + 2.0 * static_cast<double>(L.sa + L.sb));
-  return e;
+  return oz_run<Oz64>(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, D, ldd, work, work_bytes, err, kProfGemmOz);
+}
+
+cudaError_t gemm_oz32(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, float alpha,
+                      const float* A, int64_t lda, const float* B, int64_t ldb, float beta, float* D, int64_t ldd,
+                      void* work, size_t work_bytes, int* err) {
+  return oz_run<Oz32>(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, D, ldd, work, work_bytes, err, kProfGemmOz32);
 }
 
 }  // namespace rutv
 
-extern "C" int randutv_dgemm_oz(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
-                                const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
-                                int64_t ldc) {
+namespace {
+
+// The ABI entry points: argument checks, scratch from cudaMallocAsync on the
+// bound stream, synchronised.
+template <typename T>
+int oz_abi(const char* name, char transa, char transb, int64_t m, int64_t n, int64_t k, T alpha, const T* A,
+           int64_t lda, const T* B, int64_t ldb, T beta, T* C, int64_t ldc) {
   using namespace rutv;
   const bool ta = (transa == 'T' || transa == 't'), tb = (transb == 'T' || transb == 't');
   if (!ta && transa != 'N' && transa != 'n') return -1;
@@ -427,18 +506,25 @@ extern "C" int randutv_dgemm_oz(char transa, char transb, int64_t m, int64_t n, 
   if (!C) return -12;
   if (ldc < m) return -13;
   if (!gemm_oz_supported()) {
-    set_last_error("randutv_dgemm_oz: cuTensorMapEncodeTiled is not available");
+    char msg[128];
+    snprintf(msg, sizeof(msg), "%s: cuTensorMapEncodeTiled is not available", name);
+    set_last_error(msg);
     return RANDUTV_EUNSUPPORTED;
   }
   cudaStream_t s = current_stream();
-  const size_t wb = gemm_oz_work_bytes(m, n, k);
+  const size_t wb = std::is_same<T, double>::value ? gemm_oz_work_bytes(m, n, k) : gemm_oz32_work_bytes(m, n, k);
   void* ws = nullptr;
   int herr = 0;
   cudaError_t e = cudaMallocAsync(&ws, wb + 256, s);
   if (e != cudaSuccess) { cudaGetLastError(); return RANDUTV_ENOMEM; }
   int* err = reinterpret_cast<int*>(static_cast<char*>(ws) + wb);
   e = cudaMemsetAsync(err, 0, sizeof(int), s);
-  if (e == cudaSuccess) e = gemm_oz(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, wb, err);
+  if (e == cudaSuccess) {
+    if constexpr (std::is_same<T, double>::value)
+      e = gemm_oz(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, wb, err);
+    else
+      e = gemm_oz32(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, wb, err);
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaError_t e2 = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = e2;
@@ -449,4 +535,18 @@ extern "C" int randutv_dgemm_oz(char transa, char transb, int64_t m, int64_t n, 
     return RANDUTV_ECUDA;
   }
   return (herr & kDevErrTimeout) ? RANDUTV_ETIMEOUT : RANDUTV_OK;
+}
+
+}  // namespace
+
+extern "C" int randutv_dgemm_oz(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+                                const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                                int64_t ldc) {
+  return oz_abi<double>("randutv_dgemm_oz", transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+extern "C" int randutv_sgemm_oz(char transa, char transb, int64_t m, int64_t n, int64_t k, float alpha,
+                                const float* A, int64_t lda, const float* B, int64_t ldb, float beta, float* C,
+                                int64_t ldc) {
+  return oz_abi<float>("randutv_sgemm_oz", transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
 }

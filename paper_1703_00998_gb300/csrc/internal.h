@@ -18,7 +18,8 @@ constexpr int kFlagSlots = 8;
 
 // ---- prof.cu ----
 enum ProfClass { kProfGemm = 0, kProfPanel = 1, kProfTfactor = 2, kProfJacobi = 3, kProfGauss = 4,
-                 kProfOther = 5, kProfGemm32 = 6, kProfGemmTc = 7, kProfGemmOz = 8, kProfClasses = 9 };
+                 kProfOther = 5, kProfGemm32 = 6, kProfGemmTc = 7, kProfGemmOz = 8, kProfGemmOz32 = 9,
+                 kProfClasses = 10 };
 struct ProfTotals { double ms = 0.0; int64_t launches = 0; double flops = 0.0; double bytes = 0.0; };
 struct ProfToken { int idx; };
 void note_launch(int n = 1);
@@ -65,6 +66,11 @@ cudaError_t gemm_oz(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int6
                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* D, int64_t ldd,
                     void* work, size_t work_bytes, int* err);
 size_t gemm_oz_work_bytes(int64_t m, int64_t n, int64_t k);
+// The FP32 form (4 slices, FP32-accurate): the mixed form's updates.
+cudaError_t gemm_oz32(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, float alpha,
+                      const float* A, int64_t lda, const float* B, int64_t ldb, float beta, float* D, int64_t ldd,
+                      void* work, size_t work_bytes, int* err);
+size_t gemm_oz32_work_bytes(int64_t m, int64_t n, int64_t k);
 bool gemm_oz_supported();
 // Whether gemm_tc can take these operands (TMA alignment rules, driver entry point).
 bool gemm_tc_supported(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t m, int64_t n, int64_t k);

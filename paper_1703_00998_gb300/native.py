@@ -64,6 +64,8 @@ SIGNATURES = {
                                 _i64, ctypes.c_float, _vp, _i64, _i32]),
     "randutv_dgemm_oz": (_i32, [ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, _f64, _vp, _i64, _vp, _i64, _f64,
                                 _vp, _i64]),
+    "randutv_sgemm_oz": (_i32, [ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, ctypes.c_float, _vp, _i64, _vp,
+                                _i64, ctypes.c_float, _vp, _i64]),
     "randutv_panel_qr": (_i32, [_i64, _i64, _vp, _i64, _vp, _vp, _vp]),
     "randutv_small_svd": (_i32, [_i64, _vp, _i64, _vp, _vp, _vp, _i32]),
     "randutv_profile_enable": (_i32, [_i32]),
@@ -75,7 +77,8 @@ SIGNATURES = {
 }
 
 PROF_GEMM, PROF_PANEL, PROF_TFACTOR, PROF_JACOBI, PROF_GAUSS, PROF_OTHER, PROF_GEMM32, PROF_GEMMTC = range(8)
-PROF_NAMES = ["gemm", "panel_qr", "tfactor", "jacobi", "gauss", "other", "gemm32", "gemm_tc", "gemm_oz"]
+PROF_NAMES = ["gemm", "panel_qr", "tfactor", "jacobi", "gauss", "other", "gemm32", "gemm_tc", "gemm_oz",
+              "gemm_oz32"]
 
 
 def profile_read(cls):
