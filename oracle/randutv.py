@@ -22,6 +22,14 @@ economically through a QR first when the block is tall (Section 5.2, third
 modification, with Remark 1) or through a QR of its rows when it is wide
 (Remark "The case m < n").
 
+Over-sampling (Remark "Oversampling", Section 4.3 and its appendix): with
+p > 0, G has b + p columns, Y = (X^T X)^q X^T G is n_k x (b+p), and the
+step's reflectors come from a Householder QR of Z, the b dominant left
+singular vectors of Y, instead of Y itself.  Z is formed as Q_Y Us(:, 1:b)
+from the Householder QR Y = Q_Y R_Y and the SVD R_Y = Us Ds Vs^T (an SVD of Y
+with the small-SVD sign convention; the choice of basis within span(Z)
+changes the trailing basis, so it is fixed identically on the GPU).
+
 Readings where the paper is silent (each is fixed identically on the GPU):
   * tolerance: before step i, stop if ||X||_F <= tol * ||A||_F; then
     k_reached = r0 and the trailing block is left as is (A = U T V^T still
@@ -49,13 +57,26 @@ def flops_randutv(m, n, b, q, form_uv=True):
     return float(f)
 
 
-def randutv(A, b, q, gauss, tol=0.0, form_uv=True, max_steps=None):
-    """Factor A = U T V^T by Fig. 4.
+def oversampled_basis(Y, b):
+    """Z (k x b): the b dominant left singular vectors of Y (k x (b+p)), as
+    Q_Y Us(:, 1:b) with Y = Q_Y R_Y (Householder) and R_Y = Us Ds Vs^T."""
+    k, w = Y.shape
+    Vq, tq, Rq = householder_qr(Y)
+    Sq = tfactor(Vq, tq)
+    Us, _, _ = svd_small(Rq[:w, :w])
+    E = np.zeros((k, b))
+    E[:w, :] = Us[:, :b]
+    return E - Vq @ (Sq @ (Vq.T @ E))
 
-    gauss(step, k, b) -> k x b array: the Gaussian matrix of global step
-    ``step`` (1-based).  Returns (U, T, V, k_reached); U and V are None when
-    form_uv is False.  ``max_steps`` stops after that many steps (a partial
-    factorization, used to time a bounded sample)."""
+
+def randutv(A, b, q, gauss, tol=0.0, form_uv=True, max_steps=None, p=0):
+    """Factor A = U T V^T by Fig. 4 (with over-sampling p, the variant of
+    Remark "Oversampling").
+
+    gauss(step, k, w) -> k x w array: the Gaussian matrix of global step
+    ``step`` (1-based), w = b + p.  Returns (U, T, V, k_reached); U and V are
+    None when form_uv is False.  ``max_steps`` stops after that many steps (a
+    partial factorization, used to time a bounded sample)."""
     T = np.array(A, dtype=np.float64, copy=True)
     m, n = T.shape
     U = np.eye(m) if form_uv else None
@@ -75,10 +96,12 @@ def randutv(A, b, q, gauss, tol=0.0, form_uv=True, max_steps=None):
             break
         if r1 < m and c1 < n:      # I3 and J3 both non-empty
             X = T[r0:, r0:]
-            G = np.asarray(gauss(i, m - r0, b), dtype=np.float64)
+            G = np.asarray(gauss(i, m - r0, b + p), dtype=np.float64)
             Y = X.T @ G
             for _ in range(q):
                 Y = X.T @ (X @ Y)
+            if p > 0:
+                Y = oversampled_basis(Y, b)
             Vv, tv, _ = householder_qr(Y)
             Sv = tfactor(Vv, tv)
             T[:, r0:] = wy_apply_right(T[:, r0:], Vv, Sv)

@@ -44,24 +44,25 @@ def step_gaussian(seed, step, k, b):
     return g[:k]
 
 
-def stream_layout(m, n, b):
+def stream_layout(m, n, b, p=0):
     """(step, k, offset) for every step of an m x n factorization with block b
     that draws a Gaussian, i.e. steps i with b*i < min(m, n) (both I3 and J3
     non-empty in Fig. 4).  ``offset`` counts doubles in the concatenated stream
-    where step i's k x b matrix is stored column-major (leading dimension k)."""
+    where step i's k x (b+p) matrix is stored column-major (leading dimension k)."""
     out, off, i = [], 0, 1
     while b * i < min(m, n):
         k = m - b * (i - 1)
         out.append((i, k, off))
-        off += k * b
+        off += k * (b + p)
         i += 1
     return out, off
 
 
-def gaussian_stream(seed, m, n, b):
+def gaussian_stream(seed, m, n, b, p=0):
     """All steps' G concatenated column-major in the layout of ``stream_layout``."""
-    layout, total = stream_layout(m, n, b)
+    layout, total = stream_layout(m, n, b, p)
     buf = np.empty(total)
+    w = b + p
     for step, k, off in layout:
-        buf[off:off + k * b] = step_gaussian(seed, step, k, b).ravel(order="F")
+        buf[off:off + k * w] = step_gaussian(seed, step, k, w).ravel(order="F")
     return buf

@@ -102,8 +102,49 @@ def pin_dense_equivalence(f, m=72, n=60, b=8, q=1):
                 and np.max(np.abs(V1 - V2)) < 1e-11)
 
 
+def pin_oversampling_theorem1(f, n=80, b=8, p=6):
+    # Over-sampling (Remark "Oversampling"): after one step the captured space
+    # is that of Q = the b dominant left singular vectors of Y = (A^T A)^q A^T G
+    # (G with b + p columns), computed here by numpy's SVD; Theorem 1's two
+    # identities then hold with Q and W = orth(A Q).
+    ok = True
+    for q in (0, 1):
+        A = synth.make_matrix("exp50", n, n, 91 + q)
+        _, T, _, _ = f(A, b, q, gauss, max_steps=1, p=p)
+        Y = A.T @ gauss(1, n, b + p)
+        for _ in range(q):
+            Y = A.T @ (A @ Y)
+        Q = np.linalg.svd(Y, full_matrices=False)[0][:, :b]
+        W = _orth(A @ Q)
+        e1 = np.linalg.norm(A - A @ Q @ Q.T, 2)
+        e2 = np.linalg.norm(A - W @ (W.T @ A), 2)
+        t1 = np.linalg.norm(T[:, b:], 2)
+        t2 = np.linalg.norm(T[b:, b:], 2)
+        ok &= abs(t1 - e1) <= 1e-11 * e1 and abs(t2 - e2) <= 1e-11 * e2
+    return bool(ok)
+
+
+def pin_oversampling_invariants(f, n=96, b=16, q=1, p=5):
+    # structure, residual and orthogonality, log|det| and ||T||_F with p > 0;
+    # and over-sampling never loses the captured space of an exact rank r <= b
+    A = synth.make_matrix("exp50", n, n, 1703001)
+    s = synth.spectrum("exp50", n)
+    U, T, V, kr = f(A, b, q, gauss, p=p)
+    ok = kr == n and checks.residual(A, U, T, V) < 1e-13
+    ok &= checks.orth_err(U) < 1e-13 and checks.orth_err(V) < 1e-13
+    ok &= checks.lower_max(T) == 0.0 and checks.block_offdiag_max(T, b) == 0.0
+    ok &= abs(np.sum(np.log(np.abs(np.diag(T)))) - np.sum(np.log(s))) < 1e-11 * n
+    Ar = synth.make_matrix("lowrank", 64, 64, 5, r=10)
+    sr = synth.spectrum("lowrank", 64, r=10)
+    _, Tr, _, _ = f(Ar, 16, 1, gauss, max_steps=1, p=p)
+    ok &= np.linalg.norm(Tr[16:, 16:]) <= 1e-13 * np.linalg.norm(Ar)
+    ok &= np.allclose(np.diag(Tr)[:10], sr[:10], rtol=1e-12)
+    return bool(ok)
+
+
 PINS = [pin_structure_and_residual, pin_logdet_and_frobenius, pin_full_svd_case,
-        pin_theorem1, pin_low_rank, pin_dense_equivalence]
+        pin_theorem1, pin_low_rank, pin_dense_equivalence, pin_oversampling_theorem1,
+        pin_oversampling_invariants]
 
 
 def run_battery(f):

@@ -34,6 +34,13 @@ MUTATIONS = {
     "no_zero_below_panel": (R, "T[r0:, r0:c1] = 0.0\n", "pass\n"),
     # panel QR taken before the right application (stale panel)
     "stale_panel": (R, "            Vv, tv, _ = householder_qr(Y)\n", "            Vv, tv, _ = householder_qr(Y)\n            _stale = T[r0:, r0:c1].copy()\n"),
+    # over-sampling: the trailing (not the dominant) singular vectors of Y
+    "oversampling_wrong_vectors": (R, "E[:w, :] = Us[:, :b]", "E[:w, :] = Us[:, w - b:]"),
+    # over-sampling: Z without the Householder Q of Y (just Us padded with zeros)
+    "oversampling_no_q": (R, "return E - Vq @ (Sq @ (Vq.T @ E))", "return E"),
+    # over-sampling: G drawn b wide, the extra samples dropped
+    "oversampling_no_extra_samples": (R, "G = np.asarray(gauss(i, m - r0, b + p), dtype=np.float64)",
+                                      "G = np.asarray(gauss(i, m - r0, b + p), dtype=np.float64)[:, :b]"),
     # wrong partition: J2 one column short
     "J2_short": (R, "c1 = min(r0 + b, n)        # end of J2", "c1 = min(r0 + b, n) - (1 if n - r0 > b else 0)"),
 }
