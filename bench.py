@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--no-verify", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-t-only", action="store_true", help="skip the T-only (no U, V) FP64 timing")
     ap.add_argument("--probe-oz", action="store_true",
                     help="profiling aid: run two isolated Ozaki-scheme FP64 products (8192 x 8192 x 128 and "
                          "8192 x 128 x 4096) once and exit")
@@ -412,6 +413,33 @@ def run_own(args):
         verify["tril_max"] = float(torch.tril(T, -1).abs().max())
         del eye
 
+    # T only (Table 4 analogue): the same FP64 factorization without forming U and V
+    t_only = None
+    if not args.no_t_only:
+        opts.form_uv = 0
+        for _ in range(args.warmup):
+            lib.randutv_factor_ex(n, n, Ast.data_ptr(), n, b, q, 0.0, None, n, Tst.data_ptr(), n, None, n,
+                                  ctypes.byref(kr), ctypes.byref(opts))
+        torch.cuda.synchronize()
+        t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0e.record(stream)
+        for _ in range(args.steps):
+            native.check(lib.randutv_factor_ex(n, n, Ast.data_ptr(), n, b, q, 0.0, None, n, Tst.data_ptr(), n, None, n,
+                                               ctypes.byref(kr), ctypes.byref(opts)), "randutv_factor_ex")
+        t1e.record(stream)
+        torch.cuda.synchronize()
+        ms_t = t0e.elapsed_time(t1e) / args.steps
+        opts.form_uv = 1
+        t_only = {"ms_per_step": ms_t, "value": total_flops(n, q, form_uv=False) / (ms_t * 1e-3) / 1e12,
+                  "unit": "TFLOP/s", "flops_per_step": total_flops(n, q, form_uv=False),
+                  "note": "FP64 form without U and V ((12+4q)/3 n^3 flop), same K/W; the T of this run is not "
+                          "the one verified"}
+        # restore the verified factorization's T for the mixed comparison below
+        native.check(lib.randutv_factor_ex(n, n, Ast.data_ptr(), n, b, q, 0.0, Ust.data_ptr(), n, Tst.data_ptr(),
+                                           n, Vst.data_ptr(), n, ctypes.byref(kr), ctypes.byref(opts)),
+                     "randutv_factor_ex")
+        torch.cuda.synchronize()
+
     mixed = None if (args.no_mixed or "mixed" not in args.forms) else run_mixed(args, lib, native, A, Tst, n, b, q,
                                                                               stream, dist)
     if mixed is not None:
@@ -516,7 +544,7 @@ def run_own(args):
                        "flops_per_step": total_flops(n, q)},
             "seconds_per_factorization": ms / 1e3, "verify": verify, "roofline": roofline,
             "breakdown": breakdown, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
-            "mixed": mixed}
+            "t_only": t_only, "mixed": mixed}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_sample(A.cpu().numpy(), b, q, args.cpu_seconds)
     if rank == 0:

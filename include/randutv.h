@@ -48,11 +48,16 @@ typedef struct randutv_opts {
   int form_uv;          /* 1: form U and V (Table 1); 0: T only (Table 4),
                            U and V may then be NULL                            */
   int max_sweeps;       /* cap on cyclic Jacobi sweeps of each small SVD (30)  */
-  int p;                /* over-sampling (Remark "Oversampling"); must be 0    */
+  int p;                /* over-sampling (Remark "Oversampling"): each step
+                           sketches b + p columns and takes the b dominant left
+                           singular vectors of the sketch (a Householder QR and
+                           an SVD of its R); FP64 form: p >= 0 with b + p <=
+                           256; the mixed form requires 0.  With g_inject,
+                           step i stores (m - b(i-1)) x (b + p) values.       */
   uint64_t seed;        /* Philox4x32-10 key of the Gaussian matrices G        */
   const double* g_inject; /* NULL, or a device buffer holding every randomized
                            step's G, concatenated: step i (1-based, b*i <
-                           min(m,n)) stores its (m - b(i-1)) x b matrix
+                           min(m,n)) stores its (m - b(i-1)) x (b + p) matrix
                            column-major (ld = m - b(i-1)) right after step
                            i-1's.  Used instead of the Philox stream.          */
   int overlap;          /* 1: accumulate U and V on a second, lower-priority

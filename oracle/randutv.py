@@ -28,7 +28,9 @@ step's reflectors come from a Householder QR of Z, the b dominant left
 singular vectors of Y, instead of Y itself.  Z is formed as Q_Y Us(:, 1:b)
 from the Householder QR Y = Q_Y R_Y and the SVD R_Y = Us Ds Vs^T (an SVD of Y
 with the small-SVD sign convention; the choice of basis within span(Z)
-changes the trailing basis, so it is fixed identically on the GPU).
+changes the trailing basis, so it is fixed identically on the GPU).  A step
+whose trailing block has fewer than b + p columns uses the first n - r0
+columns of G.
 
 Readings where the paper is silent (each is fixed identically on the GPU):
   * tolerance: before step i, stop if ||X||_F <= tol * ||A||_F; then
@@ -96,7 +98,9 @@ def randutv(A, b, q, gauss, tol=0.0, form_uv=True, max_steps=None, p=0):
             break
         if r1 < m and c1 < n:      # I3 and J3 both non-empty
             X = T[r0:, r0:]
-            G = np.asarray(gauss(i, m - r0, b + p), dtype=np.float64)
+            # a step whose trailing block has fewer than b + p columns uses the
+            # first n - r0 columns of G (a wider sketch adds nothing)
+            G = np.asarray(gauss(i, m - r0, b + p), dtype=np.float64)[:, :min(b + p, n - r0)]
             Y = X.T @ G
             for _ in range(q):
                 Y = X.T @ (X @ Y)

@@ -40,8 +40,9 @@ def _bind_stream():
     native.lib().randutv_set_stream(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
-def _opts(seed, form_uv, max_sweeps, g_inject, overlap=True, fp64_emulation=True):
+def _opts(seed, form_uv, max_sweeps, g_inject, overlap=True, fp64_emulation=True, p=0):
     o = native.default_opts()
+    o.p = int(p)
     o.overlap = 1 if overlap else 0
     o.fp64_emulation = 1 if fp64_emulation else 0
     o.seed = int(seed)
@@ -52,7 +53,7 @@ def _opts(seed, form_uv, max_sweeps, g_inject, overlap=True, fp64_emulation=True
 
 
 def factor(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sweeps=30, overlap=True,
-           fp64_emulation=True):
+           fp64_emulation=True, p=0):
     """A = U T V^T by randUTV (Fig. 4) on A's CUDA device, FP64.
 
     A: (m, n) float64 CUDA tensor.  g_inject: optional 1-D float64 CUDA tensor
@@ -61,7 +62,8 @@ def factor(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sw
     stream.  Returns UTV(U, T, V, k_reached) as (m, m), (m, n), (n, n) views
     (U, V are None when form_uv is False).  ENOCONV raises too.
     fp64_emulation: the large products through the Ozaki-scheme tensor-core
-    GEMM (FP64-accurate) instead of the FP64 DFMA GEMM."""
+    GEMM (FP64-accurate) instead of the FP64 DFMA GEMM.  p: over-sampling
+    (each step sketches b + p columns; g_inject then holds (k, b + p) per step)."""
     torch = _torch()
     _check_cuda64(A, "A")
     m, n = A.shape
@@ -72,7 +74,7 @@ def factor(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sw
         if g_inject is not None:
             if g_inject.dtype != torch.float64 or not g_inject.is_cuda or not g_inject.is_contiguous():
                 raise TypeError("g_inject must be a contiguous float64 CUDA tensor")
-        o = _opts(seed, form_uv, max_sweeps, g_inject, overlap, fp64_emulation)
+        o = _opts(seed, form_uv, max_sweeps, g_inject, overlap, fp64_emulation, p)
         kr = ctypes.c_int64(0)
         _bind_stream()
         st = native.lib().randutv_factor_ex(

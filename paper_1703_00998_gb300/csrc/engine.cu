@@ -200,6 +200,9 @@ struct Work {
   double *Vvr[kR], *Vur[kR], *Svr[kR], *Sur[kR], *Usr[kR], *Vsr[kR];
   double *W1u, *W2u, *tmpu, *gwsu;
   double *tmps, *gwss;   // the SVD lane's rotation buffer and GEMM partials
+  // over-sampling (p > 0): the Householder QR of the (b+p)-wide sketch, the
+  // SVD of its R, the basis Z of the b dominant left singular vectors
+  double *Vq, *Rq, *Sq, *Usq, *Vsq, *dq, *Eb, *jws2;
   double *gws, *part, *jws, *red, *scal;
   int64_t gws_elems;
   unsigned* flags;
@@ -225,15 +228,20 @@ static int64_t gemm_budget(int64_t mx, int b) {
   return std::max<int64_t>(24 * mx * b, 64ll * b * b);
 }
 
-static cudaError_t work_alloc(cudaStream_t s, int64_t m, int64_t n, int b, bool uv, Work* w) {
+static cudaError_t work_alloc(cudaStream_t s, int64_t m, int64_t n, int b, int pov, bool uv, Work* w) {
   const int64_t mx = std::max(m, n);
   const int64_t bb = static_cast<int64_t>(b) * b;
+  const int64_t wv = b + pov;                  // sketch width
+  const int64_t ww = wv * wv;
+  const int64_t ov = pov > 0 ? 1 : 0;          // over-sampling buffers only when p > 0
   const int64_t ux = uv ? 1 : 0;   // the U/V lane's scratch only when U and V are formed
   struct Item { double** p; int64_t n; };
-  w->gws_elems = gemm_budget(mx, b);
+  w->gws_elems = gemm_budget(mx, static_cast<int>(wv));
   Item items[] = {
-      {&w->G, m * b}, {&w->Y, n * b}, {&w->Z, m * b},
-      {&w->tau, b}, {&w->R, bb}, {&w->Rt, bb}, {&w->gram, bb}, {&w->W1, mx * b},
+      {&w->G, m * wv}, {&w->Y, n * wv}, {&w->Z, m * wv},
+      {&w->tau, wv}, {&w->R, bb}, {&w->Rt, bb}, {&w->gram, ww}, {&w->W1, mx * b},
+      {&w->Vq, ov * mx * wv}, {&w->Rq, ov * ww}, {&w->Sq, ov * ww}, {&w->Usq, ov * ww}, {&w->Vsq, ov * ww},
+      {&w->dq, ov * wv}, {&w->Eb, ov * mx * b}, {&w->jws2, ov * jacobi_work_elems(static_cast<int>(wv))},
       {&w->W2, mx * b}, {&w->d, b}, {&w->tmp, mx * b},
       {&w->Vvr[0], mx * b}, {&w->Vvr[1], mx * b}, {&w->Vvr[2], mx * b},
       {&w->Vur[0], mx * b}, {&w->Vur[1], mx * b}, {&w->Vur[2], mx * b},
@@ -241,7 +249,8 @@ static cudaError_t work_alloc(cudaStream_t s, int64_t m, int64_t n, int b, bool 
       {&w->Usr[0], bb}, {&w->Usr[1], bb}, {&w->Usr[2], bb}, {&w->Vsr[0], bb}, {&w->Vsr[1], bb}, {&w->Vsr[2], bb},
       {&w->W1u, ux * mx * b}, {&w->W2u, ux * mx * b}, {&w->tmpu, ux * mx * b}, {&w->gwsu, ux * w->gws_elems},
       {&w->tmps, mx * b}, {&w->gwss, w->gws_elems},
-      {&w->gws, w->gws_elems}, {&w->part, panel_qr_part_elems(mx, b)}, {&w->jws, jacobi_work_elems(b)},
+      {&w->gws, w->gws_elems}, {&w->part, panel_qr_part_elems(mx, static_cast<int>(wv))},
+      {&w->jws, jacobi_work_elems(b)},
       {&w->red, kSumsqBlocks}, {&w->scal, 8},
   };
   static_assert(Work::kR == 3, "ring buffers listed above");
@@ -339,11 +348,16 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
   if (opts.form_uv && !V) return -12;
   if (opts.form_uv && ldv < n) return -13;
   if (!k_reached) return -14;
-  if (opts.precision != RANDUTV_FP64 || opts.p != 0 || opts.max_sweeps < 1) return -15;
+  if (opts.precision != RANDUTV_FP64 || opts.p < 0 || opts.max_sweeps < 1) return -15;
 
   const int64_t mn = std::min(m, n);
   if (b > mn) b = static_cast<int>(mn);
   if (b > 256) { snprintf(g_detail, sizeof(g_detail), "block size above 256"); return RANDUTV_EUNSUPPORTED; }
+  const int pov = opts.p;   // over-sampling
+  if (b + pov > 256) {
+    snprintf(g_detail, sizeof(g_detail), "block size plus over-sampling above 256");
+    return RANDUTV_EUNSUPPORTED;
+  }
   const bool uv = opts.form_uv != 0;
   cudaStream_t s = g_stream;
   Work w{};
@@ -355,9 +369,9 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
   const int64_t nsteps = std::min((m + b - 1) / b, (n + b - 1) / b);
 
   {
-    cudaError_t e = work_alloc(s, m, n, b, uv, &w);
+    cudaError_t e = work_alloc(s, m, n, b, pov, uv, &w);
     if (e == cudaSuccess && opts.fp64_emulation && gemm_oz_supported()) {
-      w.ozb = oz_budget(m, n, b);
+      w.ozb = oz_budget(m, n, b + pov);
       const int64_t mx = std::max(m, n);
       w.ozbS = std::max(gemm_oz_work_bytes(b, mx, b), gemm_oz_work_bytes(mx, b, b));   // the rotations
       e = cudaMallocAsync(&w.ozT, w.ozb, s);
@@ -421,19 +435,39 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
       double *Vv = w.Vvr[sl], *Vu = w.Vur[sl], *Sv = w.Svr[sl], *Su = w.Sur[sl], *Us = w.Usr[sl], *Vs = w.Vsr[sl];
       if (r1 < m && c1 < n) {
         // ---- randomized step: sketch, QR(Y) -> VV, QR(panel) -> UU, small SVD
+        // G has b + p columns (over-sampling); a step whose trailing block has
+        // fewer than b + p columns uses the first kc of them
+        const int wv = static_cast<int>(std::min<int64_t>(b + pov, kc));
         const double* G = w.G;
         if (opts.g_inject) {
           G = opts.g_inject + g_off;
         } else {
-          RUTV_CK(launch_gaussian(sT, opts.seed, i, kr, b, w.G, kr));
+          RUTV_CK(launch_gaussian(sT, opts.seed, i, kr, b + pov, w.G, kr));
         }
-        g_off += kr * b;
-        RUTV_CK(gT.run(sT, true, false, kc, b, kr, 1.0, X, ldt, G, kr, 0.0, w.Y, kc));
+        g_off += kr * (b + pov);
+        RUTV_CK(gT.run(sT, true, false, kc, wv, kr, 1.0, X, ldt, G, kr, 0.0, w.Y, kc));
         for (int j = 0; j < q; ++j) {
-          RUTV_CK(gT.run(sT, false, false, kr, b, kc, 1.0, X, ldt, w.Y, kc, 0.0, w.Z, kr));
-          RUTV_CK(gT.run(sT, true, false, kc, b, kr, 1.0, X, ldt, w.Z, kr, 0.0, w.Y, kc));
+          RUTV_CK(gT.run(sT, false, false, kr, wv, kc, 1.0, X, ldt, w.Y, kc, 0.0, w.Z, kr));
+          RUTV_CK(gT.run(sT, true, false, kc, wv, kr, 1.0, X, ldt, w.Z, kr, 0.0, w.Y, kc));
         }
-        RUTV_CK(panel_qr(sT, kc, b, w.Y, kc, w.tau, Vv, w.Rt, w.part, slot(w, 0)));
+        double* Ysk = w.Y;   // the n_k x b matrix whose Householder QR gives VV
+        if (pov > 0) {
+          // Z = Q_Y Us(:, 1:b): Householder QR Y = Q_Y R_Y, SVD R_Y = Us Ds Vs^T
+          // (its own Jacobi scratch and barrier slot: the SVD lane may be
+          // running the previous step's), then Z = E - Vq (Sq (Vq^T E)) with
+          // E = [Us(:, 1:b); 0]
+          RUTV_CK(panel_qr(sT, kc, wv, w.Y, kc, w.tau, w.Vq, w.Rq, w.part, slot(w, 0)));
+          RUTV_CK(gemm_f64(sT, true, false, wv, wv, kc, 1.0, w.Vq, kc, w.Vq, kc, 0.0, w.gram, wv, w.gws, ge));
+          RUTV_CK(tfactor_from_gram(sT, wv, w.gram, w.tau, w.Sq));
+          RUTV_CK(jacobi_svd(sT, wv, w.Rq, wv, w.Usq, w.dq, w.Vsq, opts.max_sweeps, w.jws2, slot(w, 4)));
+          RUTV_CK(fill(sT, kc, b, w.Eb, kc, 0.0));
+          RUTV_CK(copy_matrix(sT, wv, b, w.Usq, wv, w.Eb, kc));
+          RUTV_CK(gemm_f64(sT, true, false, wv, b, wv, 1.0, w.Vq, kc, w.Usq, wv, 0.0, w.W1, wv, w.gws, ge));
+          RUTV_CK(gemm_f64(sT, false, false, wv, b, wv, 1.0, w.Sq, wv, w.W1, wv, 0.0, w.W2, wv, w.gws, ge));
+          RUTV_CK(gT.run(sT, false, false, kc, b, wv, -1.0, w.Vq, kc, w.W2, wv, 1.0, w.Eb, kc));
+          Ysk = w.Eb;
+        }
+        RUTV_CK(panel_qr(sT, kc, b, Ysk, kc, w.tau, Vv, w.Rt, w.part, slot(w, 0)));
         RUTV_CK(gemm_f64(sT, true, false, b, b, kc, 1.0, Vv, kc, Vv, kc, 0.0, w.gram, b, w.gws, ge));
         RUTV_CK(tfactor_from_gram(sT, b, w.gram, w.tau, Sv));
         RUTV_CK(cudaEventRecord(L.v[sl], sT));

@@ -75,6 +75,12 @@ def test_opts_validation(lib):
     k = ctypes.c_int64(0)
     dummy = ctypes.c_void_p(16)
     o = native.default_opts()
-    o.p = 5
+    o.p = -1                      # over-sampling must be >= 0
     assert lib.randutv_factor_ex(4, 4, dummy, 4, 2, 1, 0.0, dummy, 4, dummy, 4, dummy, 4, ctypes.byref(k),
                                  ctypes.byref(o)) == -15
+    o.p = 300                     # b + p above 256: refused before any device work
+    assert lib.randutv_factor_ex(4, 4, dummy, 4, 2, 1, 0.0, dummy, 4, dummy, 4, dummy, 4, ctypes.byref(k),
+                                 ctypes.byref(o)) == native.EUNSUPPORTED
+    o.p = 5                       # the mixed form has no over-sampling
+    assert lib.randutv_factor_mixed(4, 4, dummy, 4, 2, 1, 0.0, dummy, 4, dummy, 4, dummy, 4, ctypes.byref(k),
+                                    ctypes.byref(o)) == -15

@@ -230,3 +230,21 @@ def test_fp64_emulation_matches_dfma(R):
     da, dc = host(a.T).diagonal(), host(c.T).diagonal()
     nA = np.linalg.norm(A, 2)
     assert np.max(np.abs(np.abs(da) - np.abs(dc)) / (np.abs(dc) + 700 * 2.0 ** -53 * nA / 1e-10)) <= 1e-10
+
+
+@pytest.mark.parametrize("m,n,b,p,q", [(500, 500, 32, 5, 1), (400, 300, 32, 10, 0), (300, 400, 64, 8, 2),
+                                       (1000, 1000, 128, 16, 1), (200, 200, 32, 100, 1)])
+def test_oversampling_against_oracle(R, m, n, b, p, q):
+    """Over-sampling p (Remark "Oversampling") on the same injected G of
+    width b + p: |diag T| to the oracle, FP64 residual and orthogonality;
+    the last case has b + p above the trailing width of late steps."""
+    A = synth.make_matrix("exp50", m, n, 1703005 + m + p)
+    g = dev(synth.gaussian_stream(SEED, m, n, b, p)) if synth.stream_layout(m, n, b, p)[1] > 0 else None
+    f = R.factor(dev(A), b=b, q=q, g_inject=g, p=p)
+    U, T, V = host(f.U), host(f.T), host(f.V)
+    assert f.k_reached == min(m, n)
+    assert checks.residual(A, U, T, V) <= 1e-13
+    assert checks.orth_err(U) <= 1e-13 and checks.orth_err(V) <= 1e-13
+    assert checks.lower_max(T) == 0.0
+    _, To, _, _ = oracle.randutv(A, b, q, gauss, form_uv=False, p=p)
+    assert diag_rel(T, To, float(np.linalg.norm(A, 2))) <= 1e-10

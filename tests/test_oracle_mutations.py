@@ -39,7 +39,7 @@ MUTATIONS = {
     # over-sampling: Z without the Householder Q of Y (just Us padded with zeros)
     "oversampling_no_q": (R, "return E - Vq @ (Sq @ (Vq.T @ E))", "return E"),
     # over-sampling: G drawn b wide, the extra samples dropped
-    "oversampling_no_extra_samples": (R, "G = np.asarray(gauss(i, m - r0, b + p), dtype=np.float64)",
+    "oversampling_no_extra_samples": (R, "G = np.asarray(gauss(i, m - r0, b + p), dtype=np.float64)[:, :min(b + p, n - r0)]",
                                       "G = np.asarray(gauss(i, m - r0, b + p), dtype=np.float64)[:, :b]"),
     # wrong partition: J2 one column short
     "J2_short": (R, "c1 = min(r0 + b, n)        # end of J2", "c1 = min(r0 + b, n) - (1 if n - r0 > b else 0)"),
