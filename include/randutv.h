@@ -279,6 +279,84 @@ int randutv_small_svd(int64_t p, const double* M, int64_t ldm, double* Us, doubl
 int randutv_small_svd_noalloc(int64_t p, const double* M, int64_t ldm, double* Us, double* d,
                               double* Vs, int max_sweeps);
 
+/* ---- Batched form: many small FP32 matrices in one launch ----------------
+ *
+ * Fig. 4 (with the economic final steps of Section 5.2 for m > n and of the
+ * Remark on m < n) applied independently to each matrix of a batch, with the
+ * early stop of Section 1.1 (ii): before each step, a matrix whose trailing
+ * block has ||T(I2 I3, J2 J3)||_F <= tol ||A||_F stops there (k_reached = the
+ * number of finished columns; T's trailing block is left as is and
+ * A = U T V^T still holds).  Every matrix is m x n with 1 <= m, n <= 512,
+ * FP32 in and out, one CTA per matrix at a time in a single persistent
+ * kernel that takes matrices from a device queue, largest first.
+ *
+ * Packed layout (element offsets, see randutv_batched_layout): matrix i is
+ * column-major with ld m[i] at offset sum_{j<i} m[j] n[j] of A and T, U_i
+ * (m[i] x m[i]) at sum_{j<i} m[j]^2 of U, V_i (n[i] x n[i]) at
+ * sum_{j<i} n[j]^2 of V; with g_inject, matrix i's Gaussian stream starts at
+ * off_g[i] and holds step s's (m - b(s-1)) x b matrix column-major for every
+ * step with b s < min(m, n), in step order.  Drawn in the kernel, G uses
+ * Philox4x32-10 with key (seed mod 2^32, seed div 2^32) and counter
+ * (row div 2, column, step, i), and FP32 Box-Muller on u1, u2 taken from
+ * the top 23 bits of words x1, x3 as (floor(x / 2^9) + 1/2) 2^-23. */
+typedef struct randutv_batched_plan randutv_batched_plan;
+
+typedef struct randutv_batched_opts {
+  int form_uv;          /* 1: form U and V; 0: T only (U, V may be NULL)       */
+  int max_sweeps;       /* Jacobi sweep cap of each small SVD (30)             */
+  uint64_t seed;        /* Philox key of the Gaussian matrices                 */
+  const float* g_inject;/* NULL, or the device Gaussian streams (layout above) */
+  int graph;            /* 1: launch through a CUDA graph the plan captures on
+                           first use (re-captured when an argument changes)    */
+  int async;            /* 1: return after queueing (no status from the device)*/
+} randutv_batched_opts;
+
+void randutv_batched_opts_default(randutv_batched_opts* opts);
+
+/* Plan a batch: count matrices of sizes m[i] x n[i] (HOST arrays).  b is the
+ * block size of every matrix (1..32, capped at min(m, n)), or 0 for the
+ * per-size-class choice (classes by min(m, n): 1-64, 65-128, ..., 449-512),
+ * 32 until randutv_batched_autotune or randutv_batched_set_classes sets it.
+ * Allocates the device work table; EUNSUPPORTED when a size exceeds 512.
+ * The plan serves one launch at a time. */
+int randutv_batched_plan_create(int64_t count, const int32_t* m, const int32_t* n, int b,
+                                randutv_batched_plan** plan);
+int randutv_batched_plan_destroy(randutv_batched_plan* plan);
+
+/* Host arrays of count entries (any may be NULL): element offsets of each
+ * matrix in A/T, U, V and the Gaussian streams, its block size; totals[4]
+ * receives the total element counts {A, U, V, G}. */
+int randutv_batched_layout(const randutv_batched_plan* plan, int64_t* off_a, int64_t* off_u,
+                           int64_t* off_v, int64_t* off_g, int32_t* b, int64_t* totals);
+
+/* Factor every matrix of the plan: A (device, packed, read only) -> T
+ * (device, packed; T == A factors in place), U, V (device, packed, written
+ * in full), k_reached (device int32, count), info (device int32, count, may
+ * be NULL: 0, RANDUTV_ENOCONV when a small SVD hit max_sweeps, RANDUTV_ENAN
+ * for a non-finite A, which is then left with k_reached = 0).  q >= 0 power
+ * steps, tol >= 0 (0: never stop early).  Returns RANDUTV_ENOCONV /
+ * RANDUTV_ENAN when any matrix reported it (unless opts->async). */
+int randutv_factor_batched(randutv_batched_plan* plan, const float* A, float* T, float* U, float* V,
+                           int q, double tol, int32_t* k_reached, int32_t* info,
+                           const randutv_batched_opts* opts);
+
+/* Choose b in {16, 32} per size class by running the whole batch A (device,
+ * packed) once with each (into scratch; A is not modified) and comparing
+ * the per-matrix device times summed over each class; the plan keeps the
+ * choice.  choice (HOST, 8 entries, may be NULL) receives it.  The plan must
+ * have been created with b = 0 for the choice to take effect. */
+int randutv_batched_autotune(randutv_batched_plan* plan, const float* A, int q, double tol,
+                             const randutv_batched_opts* opts, int32_t* choice);
+
+/* Set the per-class block sizes (HOST, 8 entries in 1..32) directly. */
+int randutv_batched_set_classes(randutv_batched_plan* plan, const int32_t* b_per_class);
+
+/* The k x w Gaussian matrix the batched kernel draws for matrix `index` at
+ * step `step` (FP32, column-major, ld ldg): the generator's own output, for
+ * checking it against its definition. */
+int randutv_batched_gaussian(uint64_t seed, int64_t index, int64_t step, int64_t k, int64_t w,
+                             float* G, int64_t ldg);
+
 #ifdef __cplusplus
 }
 #endif

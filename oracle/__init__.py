@@ -16,6 +16,8 @@ Contents
   randutv       the efficient blocked algorithm of Fig. 4 (Section 5.2).
   randutv_dense the simplistic dense version of Section 5.1 (all unitary
                 matrices stored densely), used to pin the efficient one.
+  randutv_batched  a batch of independent problems, each by Fig. 4 with the
+                early stop of Section 1.1 (ii).
   checks        residual / orthogonality / structure measures.
 
 Parity status: every function is pinned by tests/test_oracle_*.py against
@@ -26,8 +28,9 @@ from .householder import house, householder_qr, tfactor, wy_apply_right, wy_appl
 from .small_svd import svd_small, jacobi_svd, sign_fix
 from .randutv import randutv, flops_randutv
 from .randutv_dense import randutv_dense
+from .randutv_batched import randutv_batched
 from . import checks
 
 __all__ = ["house", "householder_qr", "tfactor", "wy_apply_right", "wy_apply_left_t",
            "svd_small", "jacobi_svd", "sign_fix", "randutv", "flops_randutv",
-           "randutv_dense", "checks"]
+           "randutv_dense", "randutv_batched", "checks"]

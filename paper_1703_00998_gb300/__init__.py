@@ -12,9 +12,10 @@ from collections import namedtuple
 
 from . import native
 from .native import RandutvError
+from .batched import BatchedPlan, BatchedUTV, batched_gaussian
 
 __all__ = ["factor", "factor_mixed", "factor_host", "gaussian", "philox_words", "dgemm", "sgemm", "panel_qr", "small_svd",
-           "RandutvError", "UTV"]
+           "RandutvError", "UTV", "BatchedPlan", "BatchedUTV", "batched_gaussian"]
 
 UTV = namedtuple("UTV", ["U", "T", "V", "k_reached"])
 

@@ -37,6 +37,17 @@ class Opts(ctypes.Structure):
     ]
 
 
+class BatchedOpts(ctypes.Structure):
+    _fields_ = [
+        ("form_uv", ctypes.c_int),
+        ("max_sweeps", ctypes.c_int),
+        ("seed", ctypes.c_uint64),
+        ("g_inject", ctypes.c_void_p),
+        ("graph", ctypes.c_int),
+        ("async_", ctypes.c_int),
+    ]
+
+
 _lib = None
 _i64, _i32, _f64, _vp = ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
 
@@ -74,6 +85,15 @@ SIGNATURES = {
                                     ctypes.POINTER(_f64)]),
     "randutv_launch_count": (ctypes.c_uint64, []),
     "randutv_small_svd_noalloc": (_i32, [_i64, _vp, _i64, _vp, _vp, _vp, _i32]),
+    "randutv_batched_opts_default": (None, [ctypes.POINTER(BatchedOpts)]),
+    "randutv_batched_plan_create": (_i32, [_i64, _vp, _vp, _i32, ctypes.POINTER(_vp)]),
+    "randutv_batched_plan_destroy": (_i32, [_vp]),
+    "randutv_batched_layout": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "randutv_factor_batched": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, _f64, _vp, _vp,
+                                      ctypes.POINTER(BatchedOpts)]),
+    "randutv_batched_autotune": (_i32, [_vp, _vp, _i32, _f64, ctypes.POINTER(BatchedOpts), _vp]),
+    "randutv_batched_set_classes": (_i32, [_vp, _vp]),
+    "randutv_batched_gaussian": (_i32, [ctypes.c_uint64, _i64, _i64, _i64, _i64, _vp, _i64]),
 }
 
 PROF_GEMM, PROF_PANEL, PROF_TFACTOR, PROF_JACOBI, PROF_GAUSS, PROF_OTHER, PROF_GEMM32, PROF_GEMMTC = range(8)
@@ -114,6 +134,12 @@ def check(status, func):
     if status not in (OK,):
         raise RandutvError(status, func, lib().randutv_last_error().decode())
     return status
+
+
+def default_batched_opts():
+    o = BatchedOpts()
+    lib().randutv_batched_opts_default(ctypes.byref(o))
+    return o
 
 
 def default_opts():

@@ -9,11 +9,12 @@ This package holds no arithmetic of randUTV itself.  It provides
     prescribed spectrum (the construction of Section 6.2, "Matrix 1").
 """
 from .philox import philox4x32_10, PHILOX_M0, PHILOX_M1, PHILOX_W0, PHILOX_W1
-from .gauss import step_gaussian, gaussian_stream, stream_layout, uniform52
+from .gauss import step_gaussian, step_gaussian_f32, gaussian_stream, stream_layout, uniform52, uniform23
 from .matrices import make_matrix, spectrum, haar_orthogonal
+from . import batch
 
 __all__ = [
     "philox4x32_10", "PHILOX_M0", "PHILOX_M1", "PHILOX_W0", "PHILOX_W1",
-    "step_gaussian", "gaussian_stream", "stream_layout", "uniform52",
+    "step_gaussian", "step_gaussian_f32", "gaussian_stream", "stream_layout", "uniform52", "uniform23", "batch",
     "make_matrix", "spectrum", "haar_orthogonal",
 ]

@@ -84,3 +84,40 @@ def test_opts_validation(lib):
     o.p = 5                       # the mixed form has no over-sampling
     assert lib.randutv_factor_mixed(4, 4, dummy, 4, 2, 1, 0.0, dummy, 4, dummy, 4, dummy, 4, ctypes.byref(k),
                                     ctypes.byref(o)) == -15
+
+
+def test_batched_argument_validation(lib):
+    import numpy as np
+    h = ctypes.c_void_p()
+    m = np.array([64, 80], dtype=np.int32)
+    n = np.array([70, 64], dtype=np.int32)
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    f = lib.randutv_batched_plan_create
+    assert f(-1, vp(m), vp(n), 0, ctypes.byref(h)) == -1
+    assert f(2, None, vp(n), 0, ctypes.byref(h)) == -2
+    assert f(2, vp(m), None, 0, ctypes.byref(h)) == -3
+    assert f(2, vp(m), vp(n), 33, ctypes.byref(h)) == -4
+    assert f(2, vp(m), vp(n), -1, ctypes.byref(h)) == -4
+    assert f(2, vp(m), vp(n), 0, None) == -5
+    bad = np.array([64, 0], dtype=np.int32)
+    assert f(2, vp(bad), vp(n), 0, ctypes.byref(h)) == -2
+    assert f(2, vp(m), vp(bad), 0, ctypes.byref(h)) == -3
+    big = np.array([64, 513], dtype=np.int32)
+    from paper_1703_00998_gb300 import native
+    assert f(2, vp(big), vp(n), 0, ctypes.byref(h)) == native.EUNSUPPORTED
+    assert b"512" in lib.randutv_last_error()
+    dummy = ctypes.c_void_p(16)
+    o = native.default_batched_opts()
+    assert (o.form_uv, o.max_sweeps, o.seed, o.graph, o.async_) == (1, 30, 998, 0, 0)
+    assert lib.randutv_factor_batched(None, dummy, dummy, dummy, dummy, 1, 1e-5, dummy, None, ctypes.byref(o)) == -1
+    assert lib.randutv_batched_layout(None, None, None, None, None, None, None) == -1
+    assert lib.randutv_batched_autotune(None, dummy, 1, 1e-5, None, None) == -1
+    assert lib.randutv_batched_set_classes(None, None) == -1
+    assert lib.randutv_batched_plan_destroy(None) == -1
+    g = lib.randutv_batched_gaussian
+    assert g(1, -1, 1, 4, 4, dummy, 4) == -2
+    assert g(1, 0, 0, 4, 4, dummy, 4) == -3
+    assert g(1, 0, 1, -1, 4, dummy, 4) == -4
+    assert g(1, 0, 1, 4, -1, dummy, 4) == -5
+    assert g(1, 0, 1, 4, 4, None, 4) == -6
+    assert g(1, 0, 1, 4, 4, dummy, 3) == -7
