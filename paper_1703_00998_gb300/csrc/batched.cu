@@ -212,15 +212,15 @@ __device__ __noinline__ void fill_gaussian(float* P, int kr, int b, uint32_t k0,
 }
 
 // Thread layout of the skinny products C (M x NB) = op(A) B: one output row
-// per thread, rows in warps of 32, and KS groups of warps splitting K.
+// per thread, rows in warps of 32, and KS = floor(16 / warps per row set)
+// groups of warps splitting K (KS * Mp <= 512).
 struct SkinnyMap {
   int Mp, nwr, KS, kg, i;
   bool act;
   __device__ SkinnyMap(int M) {
     Mp = (M + 31) & ~31;
     nwr = Mp >> 5;
-    const int q = BT_NW / nwr;
-    KS = q >= 16 ? 16 : q >= 8 ? 8 : q >= 4 ? 4 : q >= 2 ? 2 : 1;
+    KS = BT_NW / nwr;
     const int w = threadIdx.x >> 5;
     kg = w / nwr;
     i = (w % nwr) * 32 + (threadIdx.x & 31);
@@ -282,13 +282,28 @@ __device__ __noinline__ void gemm_tn_small(BtSmem& sm, const float* A, int lda, 
   float acc[NB];
 #pragma unroll
   for (int c = 0; c < NB; ++c) acc[c] = 0.f;
+  // each thread stages at most KCH * 512 / BT_NT = 16 elements per chunk;
+  // the next chunk is loaded into registers while the current one is used
+  constexpr int PER = KCH * BT_MAXD / BT_NT;
+  float pre[PER];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = threadIdx.x + u * BT_NT;
+      const int kk = e % KCH, ii = e / KCH, k = k0 + kk;
+      pre[u] = (e < KCH * M && k < K) ? A[k + static_cast<int64_t>(ii) * lda] : 0.f;
+    }
+  };
+  fetch(0);
   for (int k0 = 0; k0 < K; k0 += KCH) {
     __syncthreads();
-    for (int e = threadIdx.x; e < KCH * M; e += BT_NT) {
-      const int kk = e % KCH, ii = e / KCH, k = k0 + kk;
-      sm.At[kk * LDAT + ii] = (k < K) ? A[k + static_cast<int64_t>(ii) * lda] : 0.f;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = threadIdx.x + u * BT_NT;
+      if (e < KCH * M) sm.At[(e % KCH) * LDAT + e / KCH] = pre[u];
     }
     __syncthreads();
+    if (k0 + KCH < K) fetch(k0 + KCH);
     if (mp.act && mp.i < M) {
       for (int kk = mp.kg; kk < KCH; kk += mp.KS) {
         const int k = k0 + kk;
@@ -324,13 +339,20 @@ __device__ __noinline__ void gemm_nn_small(const float* A, int lda, int M, int K
     const int kper = (K + mp.KS - 1) / mp.KS;
     const int kb = mp.kg * kper, ke = min(K, kb + kper);
     const float* a = A + mp.i;
-    int k = kb;
-    for (; k + 4 <= ke; k += 4) {
-      float av[4];
+    // eight loads in flight per thread: the next group of columns is
+    // fetched while the current one is multiplied
+    float nxt[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) av[u] = a[static_cast<int64_t>(k + u) * lda];
+    for (int u = 0; u < 8; ++u) nxt[u] = (kb + u < ke) ? a[static_cast<int64_t>(kb + u) * lda] : 0.f;
+    for (int k = kb; k < ke; k += 8) {
+      float av[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) av[u] = nxt[u];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) nxt[u] = (k + 8 + u < ke) ? a[static_cast<int64_t>(k + 8 + u) * lda] : 0.f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (k + u >= ke) break;
         const float4* b4 = reinterpret_cast<const float4*>(B + (k + u) * LDW);
 #pragma unroll
         for (int j = 0; j < NB / 4; ++j) {
@@ -340,18 +362,6 @@ __device__ __noinline__ void gemm_nn_small(const float* A, int lda, int M, int K
           acc[4 * j + 2] = fmaf(av[u], bb.z, acc[4 * j + 2]);
           acc[4 * j + 3] = fmaf(av[u], bb.w, acc[4 * j + 3]);
         }
-      }
-    }
-    for (; k < ke; ++k) {
-      const float av = a[static_cast<int64_t>(k) * lda];
-      const float4* b4 = reinterpret_cast<const float4*>(B + k * LDW);
-#pragma unroll
-      for (int j = 0; j < NB / 4; ++j) {
-        const float4 bb = b4[j];
-        acc[4 * j] = fmaf(av, bb.x, acc[4 * j]);
-        acc[4 * j + 1] = fmaf(av, bb.y, acc[4 * j + 1]);
-        acc[4 * j + 2] = fmaf(av, bb.z, acc[4 * j + 2]);
-        acc[4 * j + 3] = fmaf(av, bb.w, acc[4 * j + 3]);
       }
     }
   }
@@ -379,6 +389,14 @@ __device__ __noinline__ double gemm_update(BtSmem& sm, Red& rd, float* C, int ld
       for (int s = 0; s < 4; ++s) ii[s] = tm + lane + 32 * s;
 #pragma unroll
       for (int t = 0; t < 4; ++t) jj[t] = tn + warp + 16 * t;
+      // the tile's old values are fetched before the products so that
+      // their latency overlaps the FMA loop
+      float cold[4][4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          cold[s][t] = (beta != 0.f && ii[s] < M && jj[t] < N) ? C[ii[s] + static_cast<int64_t>(jj[t]) * ldc] : 0.f;
       for (int k = 0; k < K4; k += 4) {
         float4 a[4], bq[4];
 #pragma unroll
@@ -408,7 +426,7 @@ __device__ __noinline__ double gemm_update(BtSmem& sm, Red& rd, float* C, int ld
         for (int s = 0; s < 4; ++s) {
           if (ii[s] >= M) continue;
           float v = alpha * acc[s][t];
-          if (beta != 0.f) v = fmaf(beta, col[ii[s]], v);
+          if (beta != 0.f) v = fmaf(beta, cold[s][t], v);
           col[ii[s]] = v;
           if (ii[s] >= srow) ss = fmaf(v, v, ss);
         }
@@ -674,15 +692,27 @@ __device__ __noinline__ bool small_svd(BtSmem& sm, int p, int max_sweeps, float*
     sm.Vs[e] = (e % LDQ < 32) ? Vt[e] : 0.f;
   }
   __syncthreads();
-  if (warp == 0) {
-    for (int k = 0; k < p; ++k) {
+  // two Gram-Schmidt passes per column in the sorted order; the products
+  // with the earlier columns are spread over the warps (tmp holds them)
+  float* dots = tmp;
+  for (int k = 0; k < p; ++k) {
+    float n0 = 0.f;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int j = warp; j < k; j += BT_NW) {
+        const float dj = warp_sum(sm.R[j * LDQ + lane] * sm.R[k * LDQ + lane]);
+        if (lane == 0) dots[j] = dj;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        float u = sm.R[k * LDQ + lane];
+        if (pass == 0) n0 = sqrtf(warp_sum(u * u));
+        for (int j = 0; j < k; ++j) u = fmaf(-dots[j], sm.R[j * LDQ + lane], u);
+        sm.R[k * LDQ + lane] = u;
+      }
+      __syncthreads();
+    }
+    if (warp == 0) {
       float u = sm.R[k * LDQ + lane];
-      const float n0 = sqrtf(warp_sum(u * u));
-      for (int pass = 0; pass < 2; ++pass)
-        for (int j = 0; j < k; ++j) {
-          const float qv = sm.R[j * LDQ + lane];
-          u = fmaf(-warp_sum(qv * u), qv, u);
-        }
       float n1 = sqrtf(warp_sum(u * u));
       if (!(n0 > 0.f) || !(n1 > 0.01f * n0)) {
         // basis completion: the unit vector e_t (t < p) with the largest
@@ -710,8 +740,8 @@ __device__ __noinline__ bool small_svd(BtSmem& sm, int p, int max_sweeps, float*
         n1 = sqrtf(warp_sum(u * u));
       }
       sm.R[k * LDQ + lane] = (lane < p) ? u / n1 : 0.f;
-      __syncwarp();
     }
+    __syncthreads();
   }
   __syncthreads();
   return conv;
