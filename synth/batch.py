@@ -54,7 +54,14 @@ def batch_matrices_torch(m, n, r, seed, device):
         for sz in np.unique(dims):
             idx = np.nonzero(dims == sz)[0]
             Z = torch.randn((len(idx), int(sz), int(sz)), generator=gen, dtype=torch.float32, device=device)
-            Q, R = torch.linalg.qr(Z)
+            try:
+                Q, R = torch.linalg.qr(Z)
+            except RuntimeError:
+                # torch's linear-algebra library can be unavailable (e.g. under
+                # a profiler that intercepts its loading): QR on the host
+                q_, r_ = np.linalg.qr(Z.cpu().numpy().astype(np.float64))
+                Q = torch.from_numpy(q_.astype(np.float32)).to(device)
+                R = torch.from_numpy(r_.astype(np.float32)).to(device)
             Q = Q * torch.where(torch.diagonal(R, dim1=1, dim2=2) < 0, -1.0, 1.0)[:, None, :]
             for j, i in enumerate(idx):
                 qs[i] = Q[j]
