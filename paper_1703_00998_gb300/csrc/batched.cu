@@ -638,10 +638,17 @@ __device__ __noinline__ bool small_svd(BtSmem& sm, int p, int max_sweeps, float*
         const float xa = sm.R[a * LDQ + lane], xb = sm.R[b * LDQ + lane];
         const float al = warp_sum(xa * xa), be = warp_sum(xb * xb), ga = warp_sum(xa * xb);
         if (ga != 0.f && fabsf(ga) > tolj * sqrtf(al) * sqrtf(be)) {
-          const float zeta = (be - al) / (2.f * ga);
-          const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+          // any t gives an exact rotation as long as c and s agree, so the
+          // angle uses the fast division; c = (1 + t^2)^(-1/2) from the
+          // hardware reciprocal square root and one Newton step (as accurate
+          // as a division by sqrtf)
+          const float zeta = __fdividef(be - al, 2.f * ga);
+          const float t = __fdividef(copysignf(1.f, zeta), fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
           if (t != 0.f) {
-            const float c = 1.f / sqrtf(fmaf(t, t, 1.f)), s = c * t;
+            const float x1 = fmaf(t, t, 1.f);
+            float c = rsqrtf(x1);
+            c = c * fmaf(-0.5f * x1 * c, c, 1.5f);
+            const float s = c * t;
             sm.R[a * LDQ + lane] = c * xa - s * xb;
             sm.R[b * LDQ + lane] = s * xa + c * xb;
             const float va = sm.Vs[a * LDQ + lane], vb = sm.Vs[b * LDQ + lane];
