@@ -47,6 +47,11 @@ def measured_peaks():
 # csrc/gemm_f64.cu); the per-launch traffic of the bench run is this ratio
 # times its algorithmic bytes per launch.
 GEMM_TRAFFIC = {"5b25bb34a710a3c2": 0.926}
+# DRAM traffic of the batched kernel per matrix from one ncu capture of a
+# 512-matrix batch of the same size law (dram read + write / 512), valid for
+# the kernel source with this sha256 prefix of csrc/batched.cu; a launch over
+# the whole batch is scaled by its matrix count.
+BATCHED_TRAFFIC = {"438f06db0f444904": 7.227e9 / 512}
 
 
 def parse():
@@ -218,6 +223,7 @@ def run_batched(args, native, stream):
     bs = plan.b
     fl = sum(batched_flops(int(m[i]), int(n[i]), int(bs[i]), q, int(ks[i])) for i in range(count))
     ach = fl / (ms * 1e-3) / 1e12
+    kh = kernel_hash(os.path.join(ROOT, "paper_1703_00998_gb300", "csrc", "batched.cu"))
     res = {"workload": f"batched randUTV: {count} FP32 matrices, m, n uniform in [64, 512], sigma_j = exp(-j/r), "
                        f"r uniform in [4, 64], b in {{16, 32}} autotuned, q = 1, tol 1e-5, U and V formed",
            "count": count, "ms_per_step": ms, "matrices_per_s": count / (ms * 1e-3), "value": ach,
@@ -227,7 +233,9 @@ def run_batched(args, native, stream):
            "bytes_resident": 4 * (plan.total_a * 2 + plan.total_u + plan.total_v),
            "roofline": {"bound": "alu", "kernel": "batched_kernel (persistent, one CTA per matrix)",
                         "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
-                        "traffic": None, "peak_source": "derived: 152 SMs x 128 FFMA lanes x 2 flop x 2070 MHz",
+                        "traffic": (BATCHED_TRAFFIC[kh] * count) if kh in BATCHED_TRAFFIC else None,
+                        "traffic_note": "ncu dram read+write per matrix of a 512-matrix capture, x matrices per launch",
+                        "peak_source": "derived: 152 SMs x 128 FFMA lanes x 2 flop x 2070 MHz",
                         "measured_in": "the timed region (the kernel is the step's only launch)"}}
     # sampled accuracy (FP64 on the GPU)
     rng = np.random.default_rng(3)
