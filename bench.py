@@ -88,6 +88,23 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(dist, x, device="cuda"):
+    """The largest x over all ranks (x itself without a process group): the
+    job's time is that of its slowest rank."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, seconds):
+    """Units processed by all ranks per second (weak scaling: every rank
+    factors its own matrix)."""
+    return world * units_per_rank / seconds
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
@@ -398,13 +415,9 @@ def run_mixed(args, lib, native, A, Tst64, n, b, q, stream, dist):
     torch.cuda.synchronize()
     lib.randutv_profile_enable(0)
     prof = {name: native.profile_read(i) for i, name in enumerate(native.PROF_NAMES)}
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(dist, e0.elapsed_time(e1) / args.steps)
     world = dist.get_world_size() if dist else 1
-    out = {"value": world * total_flops(n, q) / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
+    out = {"value": whole_job_rate(world, total_flops(n, q), ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
            "dtype": "f32 storage and products, f64 panel QR and small SVD", "tensor_cores": args.tensor_cores,
            "breakdown": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
                          for k, v in prof.items()}}
@@ -520,13 +533,10 @@ def run_own(args):
     lib.randutv_profile_enable(0)
     prof = {name: native.profile_read(i) for i, name in enumerate(native.PROF_NAMES)}
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(dist, e0.elapsed_time(e1) / args.steps)
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    value = world * total_flops(n, q) / (ms * 1e-3) / 1e12
+    value = whole_job_rate(world, total_flops(n, q), ms * 1e-3) / 1e12
 
     # Roofline of the dominant kernel from one more factorization with the
     # U/V lane serialised (overlap = 0): there each launch's CUDA-event
@@ -616,12 +626,8 @@ def run_own(args):
         for _ in range(e2e_steps):
             step_host()
         torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
-        if dist:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * total_flops(n, q) / e2e_s / 1e12, "unit": "TFLOP/s",
+        e2e_s = max_over_ranks(dist, (time.perf_counter() - t0) / e2e_steps)
+        e2e = {"value": whole_job_rate(world, total_flops(n, q), e2e_s) / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 3 * 8 * n * n,
                "ms_per_step": e2e_s * 1e3, "steps": e2e_steps}
 
