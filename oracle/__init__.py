@@ -18,6 +18,9 @@ Contents
                 matrices stored densely), used to pin the efficient one.
   randutv_batched  a batch of independent problems, each by Fig. 4 with the
                 early stop of Section 1.1 (ii).
+  randutv_adjoint  the rank-k approximation A_k = U(:,1:k) T(1:k,:) V^T
+                (eq. Ak_randUTV) and its vector-Jacobian product at fixed G
+                (reverse mode of the same steps, torch.autograd on CPU).
   checks        residual / orthogonality / structure measures.
 
 Parity status: every function is pinned by tests/test_oracle_*.py against
@@ -29,8 +32,9 @@ from .small_svd import svd_small, jacobi_svd, sign_fix
 from .randutv import randutv, flops_randutv
 from .randutv_dense import randutv_dense
 from .randutv_batched import randutv_batched
+from .randutv_adjoint import rank_k_approx, rank_k_vjp, loss_grad
 from . import checks
 
 __all__ = ["house", "householder_qr", "tfactor", "wy_apply_right", "wy_apply_left_t",
            "svd_small", "jacobi_svd", "sign_fix", "randutv", "flops_randutv",
-           "randutv_dense", "randutv_batched", "checks"]
+           "randutv_dense", "randutv_batched", "rank_k_approx", "rank_k_vjp", "loss_grad", "checks"]
