@@ -85,6 +85,9 @@ def parse():
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched-form leg (4096 small FP32 matrices) and print its object")
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the rank-k map / adjoint leg")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the rank-k map and its reverse pass (m = n = 1024) and print its object")
     return ap.parse_args()
 
 
@@ -307,6 +310,54 @@ def run_batched(args, native, stream):
                                "kind": "oracle", "sample": f"the first {done} of the {count} matrices, one by one, "
                                                           f"{dt:.1f} s; numpy/OpenBLAS default threads"}
     plan.close()
+    return res
+
+
+def run_adjoint(args, stream):
+    """The rank-k map A_k = U(:,1:k) T(1:k,:) V^T and its hand-written reverse
+    pass, FP64, m = n = 1024, sigma_j = exp(-j/40), b = 32, q = 1, k = 64:
+    time per forward (state kept) and per vector-Jacobian product, CUDA
+    events over K of each after W warm-ups; the gradient of one random
+    cotangent against the oracle (reverse mode on the host cores, timed)."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_1703_00998_gb300 as R
+    m = n = 1024
+    b, q, k = 32, 1, 64
+    A = synth.make_matrix("exp40", m, n, 1703005)
+    Ad = torch.from_numpy(A).cuda()
+    C = np.random.default_rng(21).standard_normal((m, n))
+    Cd = torch.from_numpy(C).cuda()
+    for _ in range(args.warmup):
+        F, st = R.rank_k_forward(Ad, b=b, q=q, k=k, keep=True)
+        R.rank_k_vjp(st, Cd)
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    for _ in range(args.steps):
+        F, st = R.rank_k_forward(Ad, b=b, q=q, k=k, keep=True)
+    e1.record(stream)
+    for _ in range(args.steps):
+        g = R.rank_k_vjp(st, Cd)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    fwd = e0.elapsed_time(e1) / args.steps
+    bwd = e1.elapsed_time(e2) / args.steps
+    res = {"workload": "rank-k map of randUTV and its reverse pass: FP64, m = n = 1024, sigma_j = exp(-j/40), "
+                       "b = 32, q = 1, k = 64, fixed G", "forward_ms": fwd, "vjp_ms": bwd,
+           "forward_plus_vjp_ms": fwd + bwd}
+    if not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        Ak_o, g_o = oracle.rank_k_vjp(A, b, q, lambda i, kk, w: synth.step_gaussian(998, i, kk, w), k, C)
+        dt = time.perf_counter() - t0
+        res["rel_diff_vs_oracle"] = {"A_k": float(np.max(np.abs(F.cpu().numpy() - Ak_o)) / np.max(np.abs(Ak_o))),
+                                     "vjp": float(np.max(np.abs(g.cpu().numpy() - g_o)) / np.max(np.abs(g_o)))}
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        res["cpu_baseline"] = {"value": dt * 1e3, "unit": "ms per forward + vjp", "cores": cores, "kind": "oracle",
+                               "sample": "one forward and one vector-Jacobian product of the same map "
+                                         "(torch.autograd on the host, FP64)"}
     return res
 
 
@@ -699,6 +750,8 @@ def run_own(args):
             "t_only": t_only, "mixed": mixed}
     if rank == 0 and not args.no_batched:
         line["batched"] = run_batched(args, native, stream)
+    if rank == 0 and not args.no_adjoint:
+        line["adjoint"] = run_adjoint(args, stream)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_sample(A.cpu().numpy(), b, q, args.cpu_seconds)
     if rank == 0:
@@ -715,6 +768,16 @@ def main():
         return run_reference(args)
     if args.probe_oz:
         return probe_oz()
+    if args.adjoint_only:
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        from paper_1703_00998_gb300 import native
+        torch.cuda.init()
+        stream = torch.cuda.current_stream()
+        native.lib().randutv_set_stream(ctypes.c_void_p(stream.cuda_stream))
+        print(json.dumps({"adjoint": run_adjoint(args, stream)}), flush=True)
+        return 0
     if args.batched_only:
         import torch
         import __graft_entry__

@@ -357,6 +357,29 @@ int randutv_batched_set_classes(randutv_batched_plan* plan, const int32_t* b_per
 int randutv_batched_gaussian(uint64_t seed, int64_t index, int64_t step, int64_t k, int64_t w,
                              float* G, int64_t ldg);
 
+/* ---- Rank-k approximation and its adjoint (FP64) ---------------------------
+ *
+ * A_k = U(:, 1:k) T(1:k, :) V^T (eq. Ak_randUTV) for k a multiple of b with
+ * k < min(m, n): the first k/b randomized steps of Fig. 4 fix U(:, 1:k) and
+ * A_k = U(:, 1:k) U(:, 1:k)^T A.  The Gaussian matrices are those of
+ * randutv_factor_ex with the same seed (or opts->g_inject, its first k/b
+ * steps), so A_k is a smooth function of A at fixed G.
+ *
+ * randutv_rank_k writes A_k (m x n, ld ldf, device) and, when state is
+ * non-NULL, keeps on the device what the reverse pass needs (the step
+ * inputs, reflectors, factors: about 3 (m n + m^2) doubles per step);
+ * randutv_rank_k_vjp then writes Abar = (dA_k/dA)^T Fbar (m x n, ld ldab)
+ * for any number of cotangents Fbar (m x n, ld ldfb); randutv_rank_k_free
+ * releases the state.  b <= 32 (EUNSUPPORTED above; also when k >=
+ * min(m, n)); opts->p must be 0. */
+typedef struct randutv_rank_k_state randutv_rank_k_state;
+
+int randutv_rank_k(int64_t m, int64_t n, const double* A, int64_t lda, int b, int q, int64_t k,
+                   double* F, int64_t ldf, const randutv_opts* opts, randutv_rank_k_state** state);
+int randutv_rank_k_vjp(randutv_rank_k_state* state, const double* Fbar, int64_t ldfb, double* Abar,
+                       int64_t ldab);
+int randutv_rank_k_free(randutv_rank_k_state* state);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,9 +13,11 @@ from collections import namedtuple
 from . import native
 from .native import RandutvError
 from .batched import BatchedPlan, BatchedUTV, batched_gaussian
+from .adjoint import rank_k, rank_k_forward, vjp as rank_k_vjp
 
 __all__ = ["factor", "factor_mixed", "factor_host", "gaussian", "philox_words", "dgemm", "sgemm", "panel_qr", "small_svd",
-           "RandutvError", "UTV", "BatchedPlan", "BatchedUTV", "batched_gaussian"]
+           "RandutvError", "UTV", "BatchedPlan", "BatchedUTV", "batched_gaussian",
+           "rank_k", "rank_k_forward", "rank_k_vjp"]
 
 UTV = namedtuple("UTV", ["U", "T", "V", "k_reached"])
 

@@ -121,3 +121,26 @@ def test_batched_argument_validation(lib):
     assert g(1, 0, 1, 4, -1, dummy, 4) == -5
     assert g(1, 0, 1, 4, 4, None, 4) == -6
     assert g(1, 0, 1, 4, 4, dummy, 3) == -7
+
+
+def test_rank_k_argument_validation(lib):
+    dummy = ctypes.c_void_p(16)
+    from paper_1703_00998_gb300 import native
+    f = lib.randutv_rank_k
+    h = ctypes.c_void_p()
+    assert f(0, 8, dummy, 8, 2, 1, 4, dummy, 8, None, ctypes.byref(h)) == -1
+    assert f(8, 0, dummy, 8, 2, 1, 4, dummy, 8, None, ctypes.byref(h)) == -2
+    assert f(8, 8, None, 8, 2, 1, 4, dummy, 8, None, ctypes.byref(h)) == -3
+    assert f(8, 8, dummy, 7, 2, 1, 4, dummy, 8, None, ctypes.byref(h)) == -4
+    assert f(8, 8, dummy, 8, 0, 1, 4, dummy, 8, None, ctypes.byref(h)) == -5
+    assert f(8, 8, dummy, 8, 2, -1, 4, dummy, 8, None, ctypes.byref(h)) == -6
+    assert f(8, 8, dummy, 8, 2, 1, 3, dummy, 8, None, ctypes.byref(h)) == -7      # k not a multiple of b
+    assert f(8, 8, dummy, 8, 2, 1, 4, None, 8, None, ctypes.byref(h)) == -8
+    assert f(8, 8, dummy, 8, 2, 1, 4, dummy, 7, None, ctypes.byref(h)) == -9
+    assert f(80, 80, dummy, 80, 40, 1, 40, dummy, 80, None, ctypes.byref(h)) == native.EUNSUPPORTED   # b > 32
+    assert f(8, 8, dummy, 8, 2, 1, 8, dummy, 8, None, ctypes.byref(h)) == native.EUNSUPPORTED        # k = min(m, n)
+    o = native.default_opts()
+    o.p = 3
+    assert f(8, 8, dummy, 8, 2, 1, 4, dummy, 8, ctypes.byref(o), ctypes.byref(h)) == -10
+    assert lib.randutv_rank_k_vjp(None, dummy, 8, dummy, 8) == -1
+    assert lib.randutv_rank_k_free(None) == -1
