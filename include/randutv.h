@@ -36,7 +36,7 @@ extern "C" {
 #define RANDUTV_ENOMEM        1  /* device allocation failed                    */
 #define RANDUTV_ENOCONV       2  /* small SVD hit max_sweeps (outputs written)  */
 #define RANDUTV_ENAN          3  /* non-finite input or trailing norm           */
-#define RANDUTV_EUNSUPPORTED  4  /* valid but not supported by this build       */
+#define RANDUTV_EUNSUPPORTED  4  /* valid but not supported by this library     */
 #define RANDUTV_ECUDA         5  /* a CUDA runtime call failed                  */
 #define RANDUTV_ETIMEOUT      6  /* a device grid barrier gave up waiting       */
 
@@ -366,8 +366,10 @@ int randutv_batched_gaussian(uint64_t seed, int64_t index, int64_t step, int64_t
  * steps), so A_k is a smooth function of A at fixed G.
  *
  * randutv_rank_k writes A_k (m x n, ld ldf, device) and, when state is
- * non-NULL, keeps on the device what the reverse pass needs (the step
- * inputs, reflectors, factors: about 3 (m n + m^2) doubles per step);
+ * non-NULL, keeps on the device what the reverse pass needs: T and U as
+ * they enter each step (m n + m^2 doubles per step) and a copy of the
+ * injected Gaussians; the reverse pass forms each step's sketch,
+ * reflectors and WY factors again from them;
  * randutv_rank_k_vjp then writes Abar = (dA_k/dA)^T Fbar (m x n, ld ldab)
  * for any number of cotangents Fbar (m x n, ld ldfb); randutv_rank_k_free
  * releases the state.  b <= 32 (EUNSUPPORTED above; also when k >=

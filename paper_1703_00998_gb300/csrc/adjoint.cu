@@ -14,7 +14,10 @@
 //   Abar = U_k U_k^T Fbar + Tbar_0,  Ubar_k = Fbar W^T + A Fbar^T U_k,
 // then step by step backwards through the two block-reflector applications
 // (Q = I - V S V^T: Cbar <- Cbar Q^T or Q Cbar, and the products Qbar V,
-// Qbar^T V formed from thin factors), the compact-WY factor (S^-1 =
+// Qbar^T V formed from thin factors; each step's Gaussian, sketches,
+// reflectors, WY factors and intermediate T are formed again from the
+// step's checkpointed T and U when the reverse pass reaches it, instead of
+// being stored), the compact-WY factor (S^-1 =
 // striu(V^T V) + diag(1/tau): Sbar = triu(-V^T Qbar V), Mbar = triu(-S^T
 // Sbar S^T), Vbar += V (N + N^T) with N = striu(Mbar), taubar = -diag(Mbar)
 // / tau^2), the Householder QR reflector by reflector (the intermediate
@@ -206,11 +209,20 @@ struct randutv_rank_k_state {
   int64_t m = 0, n = 0, k = 0;
   int b = 0, q = 0, s = 0;
   void* base = nullptr;                 // one device allocation for everything below
+  uint64_t seed = 0;
   double *A = nullptr, *U = nullptr, *W = nullptr;
+  double* gin = nullptr;                // copy of the injected Gaussian streams (or null: drawn from seed)
+  // checkpoints: T and U before each step
   struct Step {
-    double *Tprev, *Uprev, *T1, *G, *Ys, *Zs, *Vv, *tv, *Rv, *Sv, *Vu, *tu, *Ru, *Su;
+    double *Tprev, *Uprev;
   };
   std::vector<Step> st;
+  // one step's factors, formed in the forward and formed again from the
+  // checkpoint when the reverse pass reaches the step
+  struct Factors {
+    double *T1, *G, *Ys, *Zs, *Vv, *tv, *Rv, *Sv, *Vu, *tu, *Ru, *Su;
+  } f;
+  double *recT = nullptr, *recU = nullptr;   // the step's T and U while its factors are formed again
   // scratch
   double *work = nullptr, *gram = nullptr, *pq = nullptr, *c1 = nullptr, *c2 = nullptr, *c3 = nullptr,
          *c4 = nullptr, *big1 = nullptr, *big2 = nullptr, *Tbar = nullptr, *Ubar = nullptr, *vbar = nullptr,
@@ -289,40 +301,47 @@ cudaError_t add(cudaStream_t s, int64_t m, int64_t n, const double* X, int64_t l
   return cudaGetLastError();
 }
 
-cudaError_t forward(State& S, cudaStream_t s, const double* A, int64_t lda, uint64_t seed, const double* gin,
-                    double* F, int64_t ldf) {
+// Step i of the map on T (m x n) and U (m x m), both in place; the step's
+// Gaussian, sketches, reflectors, factors and T after the right application
+// go to S.f.
+cudaError_t step_forward(State& S, cudaStream_t s, int i, double* T, double* U) {
   const int64_t m = S.m, n = S.n;
   const int b = S.b, q = S.q;
+  auto& P = S.f;
+  const int64_t r0 = static_cast<int64_t>(b) * (i - 1), kr = m - r0, kc = n - r0;
+  if (S.gin) {
+    int64_t goff = 0;
+    for (int j = 1; j < i; ++j) goff += (m - static_cast<int64_t>(b) * (j - 1)) * b;
+    AD_CK(cudaMemcpyAsync(P.G, S.gin + goff, sizeof(double) * kr * b, cudaMemcpyDeviceToDevice, s));
+  } else {
+    AD_CK(launch_gaussian(s, S.seed, i, kr, b, P.G, kr));
+  }
+  const double* X = T + r0 + r0 * m;
+  // Ys holds Y_0 .. Y_q (kc x b each), Zs holds Z_1 .. Z_q (kr x b each)
+  AD_CK(g64(S, s, true, false, kc, b, kr, 1.0, X, m, P.G, kr, 0.0, P.Ys, kc));
+  for (int t = 1; t <= q; ++t) {
+    double* Z = P.Zs + (t - 1) * kr * b;
+    AD_CK(g64(S, s, false, false, kr, b, kc, 1.0, X, m, P.Ys + (t - 1) * kc * b, kc, 0.0, Z, kr));
+    AD_CK(g64(S, s, true, false, kc, b, kr, 1.0, X, m, Z, kr, 0.0, P.Ys + t * kc * b, kc));
+  }
+  AD_CK(qr_panel(S, s, kc, b, P.Ys + q * kc * b, kc, P.Vv, P.tv, P.Rv, P.Sv));
+  AD_CK(wy_apply(S, s, true, false, m, kc, b, P.Vv, P.Sv, T + r0 * m, m));
+  AD_CK(copy_matrix(s, m, n, T, m, P.T1, m));
+  AD_CK(qr_panel(S, s, kr, b, T + r0 + r0 * m, m, P.Vu, P.tu, P.Ru, P.Su));
+  AD_CK(wy_apply(S, s, true, false, m, kr, b, P.Vu, P.Su, U + r0 * m, m));
+  return wy_apply(S, s, false, false, kc, kr, b, P.Vu, P.Su, T + r0 + r0 * m, m);
+}
+
+cudaError_t forward(State& S, cudaStream_t s, const double* A, int64_t lda, double* F, int64_t ldf) {
+  const int64_t m = S.m, n = S.n;
   AD_CK(copy_matrix(s, m, n, A, lda, S.A, m));
   double* T = S.big1;                    // the running T (m x n)
   AD_CK(copy_matrix(s, m, n, A, lda, T, m));
   AD_CK(set_identity(s, m, S.U, m));
-  int64_t goff = 0;
   for (int i = 1; i <= S.s; ++i) {
-    auto& P = S.st[i - 1];
-    const int64_t r0 = static_cast<int64_t>(b) * (i - 1), kr = m - r0, kc = n - r0;
-    AD_CK(copy_matrix(s, m, n, T, m, P.Tprev, m));
-    AD_CK(copy_matrix(s, m, m, S.U, m, P.Uprev, m));
-    if (gin) {
-      AD_CK(cudaMemcpyAsync(P.G, gin + goff, sizeof(double) * kr * b, cudaMemcpyDeviceToDevice, s));
-      goff += kr * b;
-    } else {
-      AD_CK(launch_gaussian(s, seed, i, kr, b, P.G, kr));
-    }
-    const double* X = T + r0 + r0 * m;
-    // Ys holds Y_0 .. Y_q (kc x b each), Zs holds Z_1 .. Z_q (kr x b each)
-    AD_CK(g64(S, s, true, false, kc, b, kr, 1.0, X, m, P.G, kr, 0.0, P.Ys, kc));
-    for (int t = 1; t <= q; ++t) {
-      double* Z = P.Zs + (t - 1) * kr * b;
-      AD_CK(g64(S, s, false, false, kr, b, kc, 1.0, X, m, P.Ys + (t - 1) * kc * b, kc, 0.0, Z, kr));
-      AD_CK(g64(S, s, true, false, kc, b, kr, 1.0, X, m, Z, kr, 0.0, P.Ys + t * kc * b, kc));
-    }
-    AD_CK(qr_panel(S, s, kc, b, P.Ys + q * kc * b, kc, P.Vv, P.tv, P.Rv, P.Sv));
-    AD_CK(wy_apply(S, s, true, false, m, kc, b, P.Vv, P.Sv, T + r0 * m, m));
-    AD_CK(copy_matrix(s, m, n, T, m, P.T1, m));
-    AD_CK(qr_panel(S, s, kr, b, T + r0 + r0 * m, m, P.Vu, P.tu, P.Ru, P.Su));
-    AD_CK(wy_apply(S, s, true, false, m, kr, b, P.Vu, P.Su, S.U + r0 * m, m));
-    AD_CK(wy_apply(S, s, false, false, kc, kr, b, P.Vu, P.Su, T + r0 + r0 * m, m));
+    AD_CK(copy_matrix(s, m, n, T, m, S.st[i - 1].Tprev, m));
+    AD_CK(copy_matrix(s, m, m, S.U, m, S.st[i - 1].Uprev, m));
+    AD_CK(step_forward(S, s, i, T, S.U));
   }
   // W = U_k^T A, F = U_k W
   AD_CK(g64(S, s, true, false, S.k, n, m, 1.0, S.U, m, S.A, m, 0.0, S.W, S.k));
@@ -343,14 +362,20 @@ cudaError_t reverse(State& S, cudaStream_t s, const double* Fb, int64_t ldfb, do
   AD_CK(g64(S, s, false, false, m, k, n, 1.0, S.A, m, S.big2, n, 1.0, Ub, m));
   AD_CK(cudaMemsetAsync(Tb, 0, sizeof(double) * m * n, s));
   for (int i = S.s; i >= 1; --i) {
-    auto& P = S.st[i - 1];
+    // the step's factors again, from its checkpoint (per-block recomputation)
+    AD_CK(copy_matrix(s, m, n, S.st[i - 1].Tprev, m, S.recT, m));
+    AD_CK(copy_matrix(s, m, m, S.st[i - 1].Uprev, m, S.recU, m));
+    AD_CK(step_forward(S, s, i, S.recT, S.recU));
+    const auto& P = S.f;
+    const double* Tprev = S.st[i - 1].Tprev;
+    const double* Uprev = S.st[i - 1].Uprev;
     const int64_t r0 = static_cast<int64_t>(b) * (i - 1), kr = m - r0, kc = n - r0;
     double* T2b = S.big2;                                 // Tbar(r0:, r0:) after the step (kr x kc, ld kr)
     AD_CK(copy_matrix(s, kr, kc, Tb + r0 + r0 * m, m, T2b, kr));
     double* Ubb = S.big1;                                 // Ubar(:, r0:) after the step (m x kr, ld m)
     AD_CK(copy_matrix(s, m, kr, Ub + r0 * m, m, Ubb, m));
     const double* T1b = P.T1 + r0 + r0 * m;               // T(r0:, r0:) before the left application
-    const double* Uo = P.Uprev + r0 * m;                  // U(:, r0:) before the right application
+    const double* Uo = Uprev + r0 * m;                    // U(:, r0:) before the right application
     // (left application of Qu^T to T and right application of Qu to U)
     AD_CK(wy_apply(S, s, false, true, kc, kr, b, P.Vu, P.Su, Tb + r0 + r0 * m, m));   // Qu Tbar_blk
     AD_CK(wy_apply(S, s, true, true, m, kr, b, P.Vu, P.Su, Ub + r0 * m, m));          // Ubar_blk Qu^T
@@ -368,7 +393,7 @@ cudaError_t reverse(State& S, cudaStream_t s, const double* Fb, int64_t ldfb, do
     AD_CK(qr_reverse(S, s, kr, b, P.Vu, P.tu, P.Ru, S.pbar));
     AD_CK(add(s, kr, b, S.pbar, kr, Tb + r0 + r0 * m, m));
     // (right application of Qv to T(:, r0:)): C = Tprev(:, r0:), Cb = Tbar(:, r0:)
-    const double* C = P.Tprev + r0 * m;
+    const double* C = Tprev + r0 * m;
     double* Cb = Tb + r0 * m;
     AD_CK(g64(S, s, false, false, m, b, kc, 1.0, Cb, m, P.Vv, kc, 0.0, S.c2, m));     // Cb Vv
     AD_CK(g64(S, s, true, false, kc, b, m, 1.0, C, m, S.c2, m, 0.0, QV, kc));          // C^T (Cb Vv)
@@ -379,7 +404,7 @@ cudaError_t reverse(State& S, cudaStream_t s, const double* Fb, int64_t ldfb, do
     AD_CK(qr_reverse(S, s, kc, b, P.Vv, P.tv, P.Rv, Yb));
     AD_CK(wy_apply(S, s, true, true, m, kc, b, P.Vv, P.Sv, Cb, m));                   // Cb Qv^T
     // sketch: Y_t = X^T Z_t, Z_t = X Y_{t-1}, Y_0 = X^T G
-    const double* X = P.Tprev + r0 + r0 * m;
+    const double* X = Tprev + r0 + r0 * m;
     double* Xb = Tb + r0 + r0 * m;
     double* Ycur = Yb;                   // cotangent of Y_t
     for (int t = q; t >= 1; --t) {
@@ -453,23 +478,28 @@ int randutv_rank_k(int64_t m, int64_t n, const double* A, int64_t lda, int b, in
   items.push_back({&S->W, k * n});
   S->st.resize(S->s);
   for (int i = 0; i < S->s; ++i) {
-    const int64_t r0 = static_cast<int64_t>(b) * i, kr = m - r0, kc = n - r0;
-    auto& P = S->st[i];
-    items.push_back({&P.Tprev, m * n});
-    items.push_back({&P.Uprev, m * m});
-    items.push_back({&P.T1, m * n});
-    items.push_back({&P.G, kr * b});
-    items.push_back({&P.Ys, (q + 1) * kc * b});
-    items.push_back({&P.Zs, std::max<int64_t>(1, q * kr * b)});
-    items.push_back({&P.Vv, kc * b});
-    items.push_back({&P.tv, b});
-    items.push_back({&P.Rv, b * b});
-    items.push_back({&P.Sv, b * b});
-    items.push_back({&P.Vu, kr * b});
-    items.push_back({&P.tu, b});
-    items.push_back({&P.Ru, b * b});
-    items.push_back({&P.Su, b * b});
+    items.push_back({&S->st[i].Tprev, m * n});
+    items.push_back({&S->st[i].Uprev, m * m});
   }
+  // factors of one step, sized for the first (largest) one
+  auto& P = S->f;
+  items.push_back({&P.T1, m * n});
+  items.push_back({&P.G, m * b});
+  items.push_back({&P.Ys, (q + 1) * n * b});
+  items.push_back({&P.Zs, std::max<int64_t>(1, q * m * b)});
+  items.push_back({&P.Vv, n * b});
+  items.push_back({&P.tv, b});
+  items.push_back({&P.Rv, b * b});
+  items.push_back({&P.Sv, b * b});
+  items.push_back({&P.Vu, m * b});
+  items.push_back({&P.tu, b});
+  items.push_back({&P.Ru, b * b});
+  items.push_back({&P.Su, b * b});
+  items.push_back({&S->recT, m * n});
+  items.push_back({&S->recU, m * m});
+  int64_t gtot = 0;
+  for (int i = 0; i < S->s; ++i) gtot += (m - static_cast<int64_t>(b) * i) * b;
+  if (o.g_inject) items.push_back({&S->gin, gtot});
   items.push_back({&S->work, S->work_elems});
   items.push_back({&S->gram, b * b});
   items.push_back({&S->pq, panel_qr_part_elems(mx, b)});
@@ -496,7 +526,10 @@ int randutv_rank_k(int64_t m, int64_t n, const double* A, int64_t lda, int b, in
   }
   S->flags = reinterpret_cast<unsigned*>(p);
   e = cudaMemsetAsync(S->flags, 0, 256, s);
-  if (e == cudaSuccess) e = forward(*S, s, A, lda, o.seed, o.g_inject, F, ldf);
+  S->seed = o.seed;
+  if (e == cudaSuccess && o.g_inject)
+    e = cudaMemcpyAsync(S->gin, o.g_inject, sizeof(double) * gtot, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = forward(*S, s, A, lda, F, ldf);
   unsigned herr[4] = {0, 0, 0, 0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(herr, S->flags, sizeof(herr), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -316,7 +316,7 @@ const char* randutv_strerror(int st) {
     case RANDUTV_ENOMEM: return "device allocation failed";
     case RANDUTV_ENOCONV: return "small SVD did not converge within max_sweeps";
     case RANDUTV_ENAN: return "non-finite value in the input or the trailing block";
-    case RANDUTV_EUNSUPPORTED: return "valid arguments outside what this build supports";
+    case RANDUTV_EUNSUPPORTED: return "valid arguments outside what this library supports";
     case RANDUTV_ECUDA: return "a CUDA runtime call failed";
     case RANDUTV_ETIMEOUT: return "a device-side grid barrier gave up waiting";
     default: return "unknown status";

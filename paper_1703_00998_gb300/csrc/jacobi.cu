@@ -47,7 +47,7 @@ constexpr size_t kJcSmemLimit = 226 * 1024;   // dynamic; the static arrays need
 // one position down the cycle 1, 2, ..., P - 1 (so after P - 1 rounds every
 // block is home again).  Within a round a CTA rotates all bs^2 column pairs
 // across its two blocks in bs sub-rounds of bs disjoint pairs, separated by
-// __syncthreads only; in round 0 it first rotates the pairs inside each of
+// __syncthreads only; in the first pairing round it also rotates the pairs inside each of
 // its two blocks.  Every column pair meets exactly once per sweep, as in the
 // plain cyclic order, but the cluster synchronises only once per round.
 // Each seat holds bs columns of W and of Q (p entries each) and their
