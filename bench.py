@@ -41,6 +41,37 @@ def measured_peaks():
     except (OSError, KeyError, ValueError):
         return 1900.0, 1700.0, "fallback"
 
+def measured_hbm_gbs():
+    """STREAM-style copy bandwidth (GB/s) from MEASURED_PEAKS.json, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def algorithmic_elems(n, b, q, form_uv=True):
+    """Elements every pass of a square factorization must read and write
+    once (the HBM floor): per step with k = n - b(i-1), the sketch (2q+1) k^2,
+    the two-sided update 3 k^2 + 2 (n - k) k, and with U and V 2 n k each."""
+    tot, i = 0.0, 1
+    while b * (i - 1) < n:
+        k = n - b * (i - 1)
+        tot += (2 * q + 1) * k * k + 3.0 * k * k + 2.0 * (n - k) * k + (4.0 * n * k if form_uv else 0.0)
+        i += 1
+    return tot
+
+
+def hbm_view(n, b, q, elem_bytes, seconds):
+    """The same step against the HBM floor: algorithmic bytes / time and its
+    fraction of the measured copy bandwidth."""
+    peak, src = measured_hbm_gbs()
+    by = algorithmic_elems(n, b, q) * elem_bytes
+    gbs = by / seconds / 1e9
+    return {"algorithmic_bytes": by, "achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak,
+            "peak_source": src}
+
+
 # DRAM traffic of the FP64 GEMM kernel from one ncu capture (n=4096, launches
 # 7-9 of the factorization): measured dram read+write / algorithmic bytes.
 # Valid only for the kernel source it was taken on (sha256 prefix of
@@ -495,6 +526,7 @@ def run_mixed(args, lib, native, A, Tst64, n, b, q, stream, dist):
         out["diag_rel_vs_fp64"] = float(((d32 - d64).abs() / (d64 + floor)).max())
         out["diag_rel_vs_fp64_note"] = "max |d32-d64| / (|d64| + n 2^-24 ||A||_2 / 1e-4)"
         del eye, A64, U, T, V
+    out["hbm_view"] = hbm_view(n, b, q, 4, ms * 1e-3)
     out["speedup_vs_fp64"] = None
     return out
 
@@ -746,6 +778,7 @@ def run_own(args):
                        "parallelism": f"replicas x{world} (one independent factorization per GPU)",
                        "flops_per_step": total_flops(n, q)},
             "seconds_per_factorization": ms / 1e3, "verify": verify, "roofline": roofline,
+            "hbm_view": hbm_view(n, b, q, 8, ms * 1e-3),
             "breakdown": breakdown, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
             "t_only": t_only, "mixed": mixed}
     if rank == 0 and not args.no_batched:

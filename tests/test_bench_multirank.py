@@ -57,3 +57,18 @@ def test_single_process_identity():
     import bench
     assert bench.max_over_ranks(None, 3.5) == 3.5
     assert bench.whole_job_rate(1, 10.0, 2.0) == 5.0
+
+
+def test_algorithmic_bytes_floor():
+    """The HBM floor of a square factorization: 1.77e10 elements (141 GB in
+    FP64) at n = 8000, b = 128, q = 1, and the closed-form sums."""
+    sys.path.insert(0, ROOT)
+    import bench
+    e = bench.algorithmic_elems(8000, 128, 1)
+    assert abs(e - 1.77e10) / 1.77e10 < 0.01
+    n, b, q = 1000, 100, 2
+    ks = [n - b * i for i in range(n // b)]
+    ref = sum((2 * q + 1) * k * k + 3 * k * k + 2 * (n - k) * k + 4 * n * k for k in ks)
+    assert bench.algorithmic_elems(n, b, q) == ref
+    v = bench.hbm_view(8000, 128, 1, 8, 0.694)
+    assert 150 < v["achieved_gbs"] < 250 and 0 < v["frac"] < 0.05
