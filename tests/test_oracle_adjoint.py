@@ -44,7 +44,8 @@ def test_map_is_projection_on_sketched_range(m, n, b, k):
     np.testing.assert_allclose(oracle.rank_k_approx(A, b, 1, _g, k), Q @ (Q.T @ A), atol=1e-12)
 
 
-@pytest.mark.parametrize("m,n,b,k,q", [(48, 48, 8, 16, 1), (60, 40, 8, 16, 1), (40, 56, 8, 24, 1), (48, 48, 8, 16, 0)])
+@pytest.mark.parametrize("m,n,b,k,q", [(48, 48, 8, 16, 1), (60, 40, 8, 16, 1), (40, 56, 8, 24, 1), (48, 48, 8, 16, 0),
+                                     (50, 30, 6, 18, 2)])
 def test_vjp_against_central_differences(m, n, b, k, q):
     A = _mat(m, n, 10.0, 5)
     rng = np.random.default_rng(7)
