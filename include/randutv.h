@@ -348,6 +348,17 @@ int randutv_factor_batched(randutv_batched_plan* plan, const float* A, float* T,
 int randutv_batched_autotune(randutv_batched_plan* plan, const float* A, int q, double tol,
                              const randutv_batched_opts* opts, int32_t* choice);
 
+/* The layout a plan with these arguments would hold, computed on the host
+ * alone (no device, no plan): count, m, n, b as for
+ * randutv_batched_plan_create, b_per_class (8 entries, or NULL for 32
+ * everywhere) as for randutv_batched_set_classes; every output (HOST,
+ * count entries; totals 4) may be NULL.  order receives the queue order
+ * (largest m n min(m, n) first, ties by index). */
+int randutv_batched_layout_host(int64_t count, const int32_t* m, const int32_t* n, int b,
+                                const int32_t* b_per_class, int64_t* off_a, int64_t* off_u,
+                                int64_t* off_v, int64_t* off_g, int32_t* b_out, int32_t* order,
+                                int64_t* totals);
+
 /* Set the per-class block sizes (HOST, 8 entries in 1..32) directly. */
 int randutv_batched_set_classes(randutv_batched_plan* plan, const int32_t* b_per_class);
 

@@ -1047,14 +1047,17 @@ int bt_status(cudaError_t e) {
 
 // Block sizes, offsets and queue order (largest m n min(m, n) first) on the
 // host, then the table and order uploaded.
-int relayout(randutv_batched_plan* p) {
-  const int64_t c = p->count;
-  p->tab.assign(c, BMat{});
+// The host part of a plan: per matrix its block size (the fixed one, else
+// its size class's, capped at min(m, n)) and packed offsets, the totals, and
+// the queue order (largest m n min(m, n) first, ties by index).
+void batched_layout(int64_t c, const int* ms, const int* ns, int bfix, const int* tuned, BMat* tab, int* order,
+                    int64_t* totals) {
   int64_t a = 0, u = 0, v = 0, g = 0;
   for (int64_t i = 0; i < c; ++i) {
-    const int m = p->m[i], n = p->n[i];
-    const int bb = p->bfix ? p->bfix : p->tuned[size_class(m, n)];
-    BMat& t = p->tab[i];
+    const int m = ms[i], n = ns[i];
+    const int bb = bfix ? bfix : tuned[size_class(m, n)];
+    BMat& t = tab[i];
+    t = BMat{};
     t.m = m;
     t.n = n;
     t.b = std::min(bb, std::min(m, n));
@@ -1067,17 +1070,28 @@ int relayout(randutv_batched_plan* p) {
     v += static_cast<int64_t>(n) * n;
     g += gauss_elems(m, n, t.b);
   }
-  p->tot_a = a;
-  p->tot_u = u;
-  p->tot_v = v;
-  p->tot_g = g;
-  p->order.resize(c);
-  for (int64_t i = 0; i < c; ++i) p->order[i] = static_cast<int>(i);
-  std::stable_sort(p->order.begin(), p->order.end(), [p](int x, int y) {
-    const double cx = double(p->m[x]) * p->n[x] * std::min(p->m[x], p->n[x]);
-    const double cy = double(p->m[y]) * p->n[y] * std::min(p->m[y], p->n[y]);
+  totals[0] = a;
+  totals[1] = u;
+  totals[2] = v;
+  totals[3] = g;
+  for (int64_t i = 0; i < c; ++i) order[i] = static_cast<int>(i);
+  std::stable_sort(order, order + c, [ms, ns](int x, int y) {
+    const double cx = double(ms[x]) * ns[x] * std::min(ms[x], ns[x]);
+    const double cy = double(ms[y]) * ns[y] * std::min(ms[y], ns[y]);
     return cx > cy;
   });
+}
+
+int relayout(randutv_batched_plan* p) {
+  const int64_t c = p->count;
+  p->tab.assign(c, BMat{});
+  p->order.resize(c);
+  int64_t tot[4];
+  batched_layout(c, p->m.data(), p->n.data(), p->bfix, p->tuned, p->tab.data(), p->order.data(), tot);
+  p->tot_a = tot[0];
+  p->tot_u = tot[1];
+  p->tot_v = tot[2];
+  p->tot_g = tot[3];
   if (c == 0) return RANDUTV_OK;
   cudaError_t e = cudaMemcpy(p->d_tab, p->tab.data(), sizeof(BMat) * c, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->d_order, p->order.data(), sizeof(int) * c, cudaMemcpyHostToDevice);
@@ -1180,6 +1194,44 @@ int randutv_batched_plan_create(int64_t count, const int32_t* m, const int32_t* 
     return st;
   }
   *plan = p;
+  return RANDUTV_OK;
+}
+
+int randutv_batched_layout_host(int64_t count, const int32_t* m, const int32_t* n, int b, const int32_t* b_per_class,
+                                int64_t* off_a, int64_t* off_u, int64_t* off_v, int64_t* off_g, int32_t* b_out,
+                                int32_t* order, int64_t* totals) {
+  if (count < 0 || count > (int64_t(1) << 31) - 1) return -1;
+  if (count > 0 && !m) return -2;
+  if (count > 0 && !n) return -3;
+  if (b < 0 || b > 32) return -4;
+  int tuned[8] = {32, 32, 32, 32, 32, 32, 32, 32};
+  if (b_per_class)
+    for (int cl = 0; cl < 8; ++cl) {
+      if (b_per_class[cl] < 1 || b_per_class[cl] > 32) return -5;
+      tuned[cl] = b_per_class[cl];
+    }
+  for (int64_t i = 0; i < count; ++i) {
+    if (m[i] < 1) return -2;
+    if (n[i] < 1) return -3;
+    if (m[i] > rutv::BT_MAXD || n[i] > rutv::BT_MAXD) {
+      rutv::set_last_error("batched matrices are limited to m, n <= 512");
+      return RANDUTV_EUNSUPPORTED;
+    }
+  }
+  std::vector<rutv::BMat> tab(static_cast<size_t>(count));
+  std::vector<int> ord(static_cast<size_t>(count));
+  int64_t tot[4];
+  rutv::batched_layout(count, m, n, b, tuned, tab.data(), ord.data(), tot);
+  for (int64_t i = 0; i < count; ++i) {
+    if (off_a) off_a[i] = tab[i].a;
+    if (off_u) off_u[i] = tab[i].u;
+    if (off_v) off_v[i] = tab[i].v;
+    if (off_g) off_g[i] = tab[i].g;
+    if (b_out) b_out[i] = tab[i].b;
+    if (order) order[i] = ord[i];
+  }
+  if (totals)
+    for (int j = 0; j < 4; ++j) totals[j] = tot[j];
   return RANDUTV_OK;
 }
 

@@ -93,6 +93,7 @@ SIGNATURES = {
                                       ctypes.POINTER(BatchedOpts)]),
     "randutv_batched_autotune": (_i32, [_vp, _vp, _i32, _f64, ctypes.POINTER(BatchedOpts), _vp]),
     "randutv_batched_set_classes": (_i32, [_vp, _vp]),
+    "randutv_batched_layout_host": (_i32, [_i64, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "randutv_batched_gaussian": (_i32, [ctypes.c_uint64, _i64, _i64, _i64, _i64, _vp, _i64]),
     "randutv_rank_k": (_i32, [_i64, _i64, _vp, _i64, _i32, _i32, _i64, _vp, _i64, ctypes.POINTER(Opts),
                               ctypes.POINTER(_vp)]),
