@@ -114,3 +114,22 @@ def test_batch_dims_and_stream_layout():
         s0, k0, o0 = lay[0]
         np.testing.assert_array_equal(g[off[i]:off[i] + k0 * 32].reshape(32, k0).T,
                                       synth.step_gaussian_f32(SEED, 1, k0, 32, index=i))
+
+
+def test_device_generator_recipe_on_cpu():
+    """The large-batch generator (torch, grouped batched QR) builds the stated
+    workload: each matrix has singular values exp(-j / r_i) to FP32 accuracy,
+    its packed slot has the right size, and a seed fixes the batch."""
+    torch = pytest.importorskip("torch")
+    m, n, r = synth.batch.batch_dims(6, 5)
+    A = synth.batch.batch_matrices_torch(m, n, r, 11, "cpu")
+    A2 = synth.batch.batch_matrices_torch(m, n, r, 11, "cpu")
+    assert torch.equal(A, A2)
+    assert A.numel() == int(np.sum(m.astype(np.int64) * n))
+    pos = 0
+    for mi, ni, ri in zip(m, n, r):
+        Ai = A[pos:pos + mi * ni].view(int(ni), int(mi)).t().double().numpy()
+        pos += mi * ni
+        s = np.linalg.svd(Ai, compute_uv=False)
+        ref = np.exp(-np.arange(1, min(mi, ni) + 1) / ri)
+        assert np.max(np.abs(s - ref)) <= 1e-5
