@@ -43,8 +43,13 @@ def _bind_stream():
     native.lib().randutv_set_stream(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
-def _opts(seed, form_uv, max_sweeps, g_inject, overlap=True, fp64_emulation=True, p=0):
+def _opts(seed, form_uv, max_sweeps, g_inject, overlap=True, fp64_emulation=True, p=0, g_capture=None):
     o = native.default_opts()
+    if g_capture is not None:
+        torch = _torch()
+        if g_capture.dtype != torch.float64 or not g_capture.is_cuda or not g_capture.is_contiguous():
+            raise TypeError("g_capture must be a contiguous float64 CUDA tensor")
+        o.g_capture = ctypes.c_void_p(g_capture.data_ptr())
     o.p = int(p)
     o.overlap = 1 if overlap else 0
     o.fp64_emulation = 1 if fp64_emulation else 0
@@ -56,7 +61,7 @@ def _opts(seed, form_uv, max_sweeps, g_inject, overlap=True, fp64_emulation=True
 
 
 def factor(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sweeps=30, overlap=True,
-           fp64_emulation=True, p=0):
+           fp64_emulation=True, p=0, g_capture=None):
     """A = U T V^T by randUTV (Fig. 4) on A's CUDA device, FP64.
 
     A: (m, n) float64 CUDA tensor.  g_inject: optional 1-D float64 CUDA tensor
@@ -66,7 +71,9 @@ def factor(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sw
     (U, V are None when form_uv is False).  ENOCONV raises too.
     fp64_emulation: the large products through the Ozaki-scheme tensor-core
     GEMM (FP64-accurate) instead of the FP64 DFMA GEMM.  p: over-sampling
-    (each step sketches b + p columns; g_inject then holds (k, b + p) per step)."""
+    (each step sketches b + p columns; g_inject then holds (k, b + p) per step).
+    g_capture: optional 1-D float64 CUDA tensor of the g_inject layout that
+    receives every randomized step's G."""
     torch = _torch()
     _check_cuda64(A, "A")
     m, n = A.shape
@@ -77,7 +84,7 @@ def factor(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sw
         if g_inject is not None:
             if g_inject.dtype != torch.float64 or not g_inject.is_cuda or not g_inject.is_contiguous():
                 raise TypeError("g_inject must be a contiguous float64 CUDA tensor")
-        o = _opts(seed, form_uv, max_sweeps, g_inject, overlap, fp64_emulation, p)
+        o = _opts(seed, form_uv, max_sweeps, g_inject, overlap, fp64_emulation, p, g_capture)
         kr = ctypes.c_int64(0)
         _bind_stream()
         st = native.lib().randutv_factor_ex(
@@ -89,10 +96,11 @@ def factor(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sw
 
 
 def factor_mixed(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, max_sweeps=30, overlap=True,
-                 tensor_cores=1):
+                 tensor_cores=1, sketch_prec=0, g_capture=None):
     """Mixed-precision randUTV: A is an (m, n) float32 CUDA tensor; U, T, V
     come back float32.  Panel QRs and small SVDs run in FP64 inside.
-    tensor_cores: 1 runs the sketch products on the tcgen05 tensor cores."""
+    tensor_cores: 1 runs the sketch products on the tcgen05 tensor cores,
+    as 3xTF32 (sketch_prec 0) or one TF32 product (sketch_prec 1)."""
     torch = _torch()
     if not isinstance(A, torch.Tensor) or A.dim() != 2 or A.dtype != torch.float32 or not A.is_cuda:
         raise TypeError("A must be a 2-D float32 CUDA tensor")
@@ -104,8 +112,9 @@ def factor_mixed(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, 
         if g_inject is not None:
             if g_inject.dtype != torch.float64 or not g_inject.is_cuda or not g_inject.is_contiguous():
                 raise TypeError("g_inject must be a contiguous float64 CUDA tensor")
-        o = _opts(seed, form_uv, max_sweeps, g_inject, overlap)
+        o = _opts(seed, form_uv, max_sweeps, g_inject, overlap, g_capture=g_capture)
         o.tensor_cores = int(tensor_cores)
+        o.sketch_prec = int(sketch_prec)
         kr = ctypes.c_int64(0)
         _bind_stream()
         st = native.lib().randutv_factor_mixed(

@@ -302,6 +302,8 @@ void randutv_opts_default(randutv_opts* o) {
   o->overlap = 1;
   o->tensor_cores = 1;
   o->fp64_emulation = 1;
+  o->sketch_prec = RANDUTV_SKETCH_3XTF32;
+  o->g_capture = nullptr;
 }
 
 int randutv_set_stream(void* s) {
@@ -348,7 +350,9 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
   if (opts.form_uv && !V) return -12;
   if (opts.form_uv && ldv < n) return -13;
   if (!k_reached) return -14;
-  if (opts.precision != RANDUTV_FP64 || opts.p < 0 || opts.max_sweeps < 1) return -15;
+  if (opts.precision != RANDUTV_FP64 || opts.p < 0 || opts.max_sweeps < 1 ||
+      opts.sketch_prec != RANDUTV_SKETCH_3XTF32)
+    return -15;
 
   const int64_t mn = std::min(m, n);
   if (b > mn) b = static_cast<int>(mn);
@@ -377,12 +381,15 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
       e = cudaMallocAsync(&w.ozT, w.ozb, s);
       if (e == cudaSuccess && uv) e = cudaMallocAsync(&w.ozU, w.ozb, s);
       if (e == cudaSuccess) e = cudaMallocAsync(&w.ozS, w.ozbS, s);
+      for (void* oz : {w.ozT, w.ozU, w.ozS})
+        if (e == cudaSuccess && oz) e = cudaMemsetAsync(oz, 0, gemm_oz_head_bytes(), s);
     }
     if (e != cudaSuccess) {
       cudaGetLastError();
       snprintf(g_detail, sizeof(g_detail), "workspace: %s", cudaGetErrorString(e));
       if (w.ozT) cudaFreeAsync(w.ozT, s);
       if (w.ozU) cudaFreeAsync(w.ozU, s);
+      if (w.ozS) cudaFreeAsync(w.ozS, s);
       if (w.base) cudaFreeAsync(w.base, s);
       cudaStreamSynchronize(s);
       return e == cudaErrorMemoryAllocation ? RANDUTV_ENOMEM : RANDUTV_ECUDA;
@@ -444,6 +451,9 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
         } else {
           RUTV_CK(launch_gaussian(sT, opts.seed, i, kr, b + pov, w.G, kr));
         }
+        if (opts.g_capture)
+          RUTV_CK(cudaMemcpyAsync(opts.g_capture + g_off, G, kr * (b + pov) * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, sT));
         g_off += kr * (b + pov);
         RUTV_CK(gT.run(sT, true, false, kc, wv, kr, 1.0, X, ldt, G, kr, 0.0, w.Y, kc));
         for (int j = 0; j < q; ++j) {

@@ -214,6 +214,7 @@ enum GemmKind { kSketch = 0, kUpdate = 1 };
 
 struct Mg {
   bool tc;
+  bool split;   // sketch on the tensor cores as 3xTF32 (else one TF32 product)
   int* err;
   float* gws;
   int64_t ge;
@@ -221,7 +222,7 @@ struct Mg {
                   const float* A, int64_t lda, const float* B, int64_t ldb, float beta, float* C,
                   int64_t ldc) const {
     if (kind == kSketch && tc && gemm_tc_supported(A, lda, B, ldb, m, n, k))
-      return gemm_tc(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, gws, ge, err, true);
+      return gemm_tc(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, gws, ge, err, split);
     return gemm_f32(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, gws, ge);
   }
 };
@@ -313,7 +314,9 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
   if (opts.form_uv && !V) return -12;
   if (opts.form_uv && ldv < n) return -13;
   if (!k_reached) return -14;
-  if (opts.p != 0 || opts.max_sweeps < 1) return -15;
+  if (opts.p != 0 || opts.max_sweeps < 1 ||
+      (opts.sketch_prec != RANDUTV_SKETCH_3XTF32 && opts.sketch_prec != RANDUTV_SKETCH_TF32))
+    return -15;
 
   const int64_t mn = std::min(m, n);
   if (b > mn) b = static_cast<int>(mn);
@@ -338,14 +341,15 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
   }
   {
     const bool tcl = opts.tensor_cores != 0;
+    const bool split = opts.sketch_prec == RANDUTV_SKETCH_3XTF32;
     int* tc_err = reinterpret_cast<int*>(slot_of(w.flags, 3) + 2);
-    gT = Mg{tcl, tc_err, w.gws, w.gws_elems};
-    gU = Mg{tcl, tc_err, w.gwsu, w.gws_elems};
+    gT = Mg{tcl, split, tc_err, w.gws, w.gws_elems};
+    gU = Mg{tcl, split, tc_err, w.gwsu, w.gws_elems};
   }
   RUTV_MCK(L.open(s, opts.overlap != 0));
   {
     cudaStream_t sT = L.t, sU = L.uv, sS = L.sv;
-    const Mg gS{false, gT.err, w.gwss, w.gws_elems};   // SVD lane: the rotations (CUDA cores)
+    const Mg gS{false, false, gT.err, w.gwss, w.gws_elems};   // SVD lane: the rotations (CUDA cores)
     int prev_sl = -1;   // ring slot of the previous randomized step (its rotations of T run on the SVD lane)
     RUTV_MCK(copy32(sT, m, n, A, lda, T, ldt));
     if (uv) {
@@ -381,9 +385,15 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
         // sketch on the FP32 pipe; G from the same Philox stream (or the injected one) rounded to FP32
         if (opts.g_inject) {
           RUTV_MCK(down(sT, kr, b, opts.g_inject + g_off, kr, w.G, kr));
+          if (opts.g_capture)
+            RUTV_MCK(cudaMemcpyAsync(opts.g_capture + g_off, opts.g_inject + g_off, kr * b * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, sT));
         } else {
           RUTV_MCK(launch_gaussian(sT, opts.seed, i, kr, b, w.G64, kr));
           RUTV_MCK(down(sT, kr, b, w.G64, kr, w.G, kr));
+          if (opts.g_capture)
+            RUTV_MCK(cudaMemcpyAsync(opts.g_capture + g_off, w.G64, kr * b * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, sT));
         }
         g_off += kr * b;
         RUTV_MCK(gT.run(sT, kSketch, true, false, kc, b, kr, 1.f, X, ldt, w.G, kr, 0.f, w.Y, kc));

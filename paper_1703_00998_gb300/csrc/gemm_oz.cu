@@ -1,44 +1,65 @@
 // FP64 and FP32 GEMMs from BF16 tensor-core products (the Ozaki scheme):
 // D = alpha op(A) op(B) + beta D, column-major, for the FP64 form's sketch
-// products, block-reflector applications and rotations, and for the mixed
-// form's block-reflector applications and rotations (Fig. 4).
+// products, block-reflector applications and rotations (Fig. 4).
 //
-// FP64 issues at ~4 flop/clk/SM on this GPU (1.2 TFLOP/s), BF16 tensor-core
+// FP64 issues at ~2 DFMA/clk/SM on this GPU (1.2 TFLOP/s), BF16 tensor-core
 // products at ~1.9 PFLOP/s.  The scheme trades the FP64 multiply-adds for
 // exact integer products:
 //   * slicing: each row of op(A) and each column of op(B) is split, per K
 //     chunk of OZ_KC = 128, into a power-of-two scale 2^e (|x| < 2^e over the
-//     chunk) and OZ_S = 8 integer slices of 7 bits, x = 2^e sum_j s_j 2^-7(j+1)
+//     chunk) and S = 8 integer slices of 7 bits, x = 2^e sum_j s_j 2^-7(j+1)
 //     with |s_j| <= 127 (each an exact BF16), truncated after 56 bits;
 //   * products: for the 36 slice pairs (s, t) with s + t <= 7, the tensor
 //     cores form S_s T_t^T over the chunk and add it into the FP32
-//     accumulator of group g = s + t (8 accumulators of 128 x 64 in tensor
-//     memory).  Every product is an integer below 2^14 and a group holds at
-//     most 8 x 128 of them, below 2^24: the FP32 sums are exact whatever the
-//     accumulator's rounding;
-//   * epilogue: the 8 exact group sums are combined in 64-bit integers
-//     (H = g0 2^14 + g1 2^7 + g2, L = g3 2^28 + ... + g7) and rounded once to
-//     FP64: (H 2^35 + L) 2^(eA + eB - 63).
-// A chunk's result therefore has the accuracy of an FP64 dot product of
-// length 128 with 56-bit inputs (error <= 128 * 2^-55 * max|a| * max|b| over
-// the chunk, plus one rounding); longer K is split into chunks whose FP64
-// results are summed in FP64 by a reduction kernel.
-// The FP32 form (FP32 operands and result) takes 4 slices of 7 bits (28
-// bits, above FP32's 24), the 10 pairs with s + t <= 3 in 4 group
-// accumulators (128 x 64 tiles), W = g0 2^21 + g1 2^14 + g2 2^7 + g3 and one
-// rounding to FP32 per chunk: error <= 128 * 2^-27 * max|a| * max|b| over the
-// chunk plus FP32 rounding, the accuracy class of an FP32 GEMM with round-to-
-// nearest accumulation (the tensor-core FP32 accumulator's truncation never
-// acts: every partial sum is an exact integer below 2^24).
+//     accumulator of group g = s + t.  Every product is an integer below
+//     2^14 and group g holds g + 1 pairs x 128 of them, below 2^24: the FP32
+//     sums are exact whatever the accumulator's rounding;
+//   * combination: the chunk's value is 2^(eA + eB - 63) F with
+//     F = sum_g G_g 2^(49 - 7g), |F| < 2^70.  It is added, in 64-bit
+//     integers, into a fixed-point accumulator whose unit is
+//     2^(NA + NB - 62), where 2^NA bounds the 2-norm of the row over the
+//     whole K range (from the chunk scales and an integer bound of each
+//     chunk's norm the slicer records: |x| < (|s_0| + 1) 2^(e - 7)) and
+//     2^NB that of the column, so that |sum_k a_k b_k| <= |a| |b| < 2^62
+//     units (Cauchy-Schwarz) and the accumulator cannot overflow.  F 2^-7
+//     is split into its leading part (groups 0-3) and trailing part (groups
+//     4-7), each shifted to the accumulator's unit and rounded; all slices
+//     of one entry carry its sign, so each part is bounded like F itself;
+//   * one rounding to FP64 at the end (integer round-to-nearest-even of the
+//     accumulator), then the alpha/beta update.
+// The result is at least as accurate as an FP64 GEMM: the slices truncate
+// each operand after 56 bits of its chunk's scale (error <= 2 * 128 *
+// 2^-55 * max|a| * max|b| per chunk), the accumulator rounds each chunk
+// twice at 2^-62 |a| |b| (against the u sum |a_k| |b_k| <= 2^-53 |a| |b|
+// of an FP64 dot product), and the final value is rounded once.  Integer additions are associative, so a K range split over
+// several CTAs (their accumulators added with integer atomics) gives
+// bit-identical results in any order.
 //
-// MMA kernel, one CTA per 128 x 64 tile of D and K chunk (192 threads):
-//   warp 0 (one thread): TMA loads (128B swizzle, K-major) of the 8 B slices
-//     of both 64-wide K sub-blocks (128 KB, resident) and of the 16 A slice
-//     sub-blocks through a 4-stage ring (16 KB each);
-//   warp 1 (one thread): tcgen05.mma.kind::f16 (BF16 in, FP32 out,
-//     M = 128, N = 64, K = 16), A slice s against B slices t <= 7 - s;
-//   warps 2-5: tcgen05.ld of the 8 group accumulators, integer combination,
-//     FP64 scaling and the alpha/beta update (or FP64 chunk partials).
+// FP64 kernel (gemm_ozx_kernel): one CTA per SM (320 threads, 209 KB of
+// shared memory, all 512 tensor-memory columns), working through a
+// contiguous range of units (tile, K chunk) of 128 x 64 output tiles:
+//   warp 0 (one thread): TMA loads (128B swizzle, K-major): per 64-wide K
+//     sub-block, the 8 B slices of the tile's 64 columns side by side (a
+//     512-row operand, 64 KB, 2-stage ring) and the 8 A slices of its 128
+//     rows one by one (16 KB each, 5-stage ring);
+//   warp 1 (one thread): tcgen05.mma.kind::f16 (BF16 in, FP32 out, M = 128,
+//     K = 16): A slice s against the B slices t = 0 .. 7 - s in one or two
+//     instructions (N = 64 (8 - s), split at 256), whose output columns land
+//     in the accumulators of groups s .. 7 (tensor-memory columns 64 g ..);
+//     slices in the order 7, 6, .., 0, so that the next chunk's products
+//     start on group 7 while the epilogue is still reading groups 5 .. 0;
+//   warps 2-9: per chunk, read the group accumulators in pairs (7, 6),
+//     (5, 4), (3, 2), (1, 0) (tcgen05.ld), release each pair to the MMA
+//     thread, and fold it into the 64-bit accumulators in registers (one
+//     row and 32 columns per thread); at a tile's end, round to FP64 and
+//     update D, or (when the tile's chunks are split between CTAs) add into
+//     the tile's integer accumulator with atomics, the last CTA of the tile
+//     doing the update.
+// The FP32 form (FP32 operands and result: randutv_sgemm_oz) takes 4 slices
+// of 7 bits (28 bits, above FP32's 24), the 10 pairs with s + t <= 3 in 4
+// group accumulators, one CTA per 128 x 64 tile and K chunk, W = g0 2^21 +
+// g1 2^14 + g2 2^7 + g3 rounded once to FP32 per chunk and chunk results
+// summed in FP64 by a reduction kernel.
 // Every mbarrier wait is bounded (2 s); on expiry the CTA sets the error
 // word, waits (bounded) for its copies in flight, frees its tensor memory
 // and returns.
@@ -56,32 +77,8 @@ namespace {
 constexpr int OZ_KC = 128;         // K chunk: exact FP32 group sums
 constexpr int OZ_BM = 128;         // rows of a tile
 constexpr int OZ_KB = 64;          // K sub-block: 64 BF16 = 128 bytes = one swizzle row
-constexpr int OZ_ASTAGES = 2;
-constexpr int OZ_A_BYTES = OZ_BM * OZ_KB * 2;   // 16 KB: one A slice, one sub-block
-constexpr int OZ_NT = 192;
+constexpr int kOzZeroScale = -2000;  // scale reported for an all-zero chunk (below any FP64 exponent)
 static_assert(OZ_KC == 2 * OZ_KB, "two sub-blocks per chunk");
-
-// One form of the scheme: S slices of 7 bits per operand, tiles of 128 x BN,
-// operands and result of type T.  S groups x BN columns of tensor memory
-// (256 in both forms, so two CTAs share an SM and one's epilogue overlaps
-// the other's products).
-template <int S_, int BN_, typename T_>
-struct OzCfg {
-  static constexpr int S = S_, BN = BN_;
-  using T = T_;
-  static constexpr bool F32 = std::is_same<T_, float>::value;
-  static constexpr int W = 7 * S;                           // fixed-point bits of the slices
-  static constexpr int B_BYTES = BN * OZ_KB * 2;            // one B slice, one sub-block
-  static constexpr int B_ALL = 2 * S * B_BYTES;
-  static constexpr int SMEM = B_ALL + OZ_ASTAGES * OZ_A_BYTES + 1024 + 256;
-  static constexpr uint32_t TMEM_COLS = S * BN;
-  // instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, N = BN, M = 128
-  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((BN >> 3) << 17) | ((OZ_BM >> 4) << 24);
-  static_assert(S * OZ_KC * 127 * 127 < (1 << 24), "group sums exact in FP32");
-  static_assert(SMEM <= 113 * 1024 && TMEM_COLS <= 256, "two CTAs per SM");
-};
-using Oz64 = OzCfg<8, 32, double>;   // 56-bit slices: FP64 products
-using Oz32 = OzCfg<4, 64, float>;    // 28-bit slices: FP32 products
 
 __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
@@ -90,6 +87,12 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
       ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
+}
+
+// instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t oz_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
+         (static_cast<uint32_t>(OZ_BM >> 4) << 24);
 }
 
 // Bit layout of the element types: exponent field position and width, and
@@ -114,10 +117,13 @@ template <> struct FBits<float> {
 // largest biased exponent of the row's chunk minus the bias (so |x| < 2^e),
 // and the slices are the 7-bit groups of the W-bit fixed-point magnitude
 // trunc(|x| 2^(W - e)), each with the sign of x.
+// With NS non-null it also writes NS[c Rpad + r] = sum_k (|s_0| + 1)^2 over
+// the chunk's entries (0 for an all-zero chunk): the chunk's squared
+// 2-norm is below NS 2^(2e - 14), since |x| < (|s_0| + 1) 2^(e - 7).
 template <int S, typename T>
 __global__ void __launch_bounds__(128)
 oz_slice_kernel(int64_t R, int64_t K, const T* __restrict__ X, int64_t ldx, bool kcontig, int64_t Rpad,
-                int64_t Kpad, __nv_bfloat16* __restrict__ Sl, int* __restrict__ E) {
+                int64_t Kpad, __nv_bfloat16* __restrict__ Sl, int* __restrict__ E, int* __restrict__ NS) {
   using F = FBits<T>;
   constexpr int W = 7 * S;
   __shared__ long long tile[32][OZ_KC + 1];
@@ -140,15 +146,18 @@ oz_slice_kernel(int64_t R, int64_t K, const T* __restrict__ X, int64_t ldx, bool
     int be = 0;   // largest biased exponent of the row's chunk
     for (int kk = lane; kk < OZ_KC; kk += 32) be = max(be, static_cast<int>((tile[i][kk] >> F::MB) & EMASK));
     be = __reduce_max_sync(0xffffffffu, be);
-    if (lane == 0) s_e[i] = (be == 0) ? 0 : be - F::EBIAS;   // zero (or subnormal-only) row: e = 0
+    if (lane == 0) s_e[i] = (be == 0) ? kOzZeroScale : be - F::EBIAS;
   }
   __syncthreads();
+  // a zero (or subnormal-only) chunk reports the scale kOzZeroScale, so that it never sets a row's
+  // largest scale; its slices are zero
   if (tid < 32 && r0 + tid < Rpad) E[static_cast<int64_t>(blockIdx.y) * Rpad + r0 + tid] = s_e[tid];
   // each warp writes 8 rows; a lane owns 4 consecutive k of a row
   for (int i = warp; i < 32; i += 4) {
     const int64_t r = r0 + i;
     if (r >= Rpad) continue;
-    const int e = s_e[i];
+    const int e = s_e[i] == kOzZeroScale ? 0 : s_e[i];
+    int nsq = 0;
     unsigned long long mag[4];
     bool neg[4];
 #pragma unroll
@@ -169,6 +178,7 @@ oz_slice_kernel(int64_t R, int64_t K, const T* __restrict__ X, int64_t ldx, bool
       for (int q = 0; q < 4; ++q) {
         const int v = static_cast<int>((mag[q] >> (W - 7 * (j + 1))) & 127ull);
         out[q] = __float2bfloat16_rn(static_cast<float>(neg[q] ? -v : v));   // exact: 7 bits
+        if (j == 0) nsq += (v + 1) * (v + 1);
       }
       uint2 pk;
       pk.x = static_cast<uint32_t>(__bfloat16_as_ushort(out[0])) |
@@ -177,16 +187,455 @@ oz_slice_kernel(int64_t R, int64_t K, const T* __restrict__ X, int64_t ldx, bool
              (static_cast<uint32_t>(__bfloat16_as_ushort(out[3])) << 16);
       *reinterpret_cast<uint2*>(Sl + (static_cast<int64_t>(j) * Rpad + r) * Kpad + k0 + lane * 4) = pk;
     }
+    if (NS) {
+      nsq = __reduce_add_sync(0xffffffffu, nsq);
+      if (lane == 0) NS[static_cast<int64_t>(blockIdx.y) * Rpad + r] = (s_e[i] == kOzZeroScale) ? 0 : nsq;
+    }
   }
 }
 
-template <class C>
+// ============================================================ FP64 form
+constexpr int OX_S = 8;                                   // slices per operand
+constexpr int OX_BN = 64;                                 // B-role rows (output columns) of a tile
+constexpr int OX_A_BYTES = OZ_BM * OZ_KB * 2;             // 16 KB: one A slice, one K sub-block
+constexpr int OX_BSL = OX_BN * OZ_KB * 2;                 // 8 KB: one B slice, one K sub-block
+constexpr int OX_B_BYTES = OX_S * OX_BSL;                 // 64 KB: the 8 B slices side by side
+constexpr int OX_AST = 5, OX_BST = 2;                     // ring stages
+constexpr int OX_EPI = 8;                                 // epilogue warps
+constexpr int OX_NT = 64 + 32 * OX_EPI;                   // 320 threads
+constexpr int OX_TILE = OZ_BM * OX_BN;                    // 8192 outputs per tile
+constexpr int OX_NBAR = 2 * OX_BST + 2 * OX_AST + 2 + OX_S;
+constexpr int OX_SMEM = OX_BST * OX_B_BYTES + OX_AST * OX_A_BYTES + 1024 + 8 * OX_NBAR + 16;
+constexpr int OX_SPLIT_TILES = 2 * kNumSMs;               // tiles whose K range may be split between CTAs
+static_assert(OX_SMEM <= 227 * 1024, "shared memory per CTA");
+static_assert(OX_S * OX_BN == 512, "the group accumulators fill tensor memory");
+
+struct OxParams {
+  const int* eA;        // A-role chunk scales e[c RApad + r]
+  const int* eB;        // B-role chunk scales
+  const int* nA;        // A-role chunk norm bounds (|row chunk|_2^2 < n 2^(2e - 14))
+  const int* nB;        // B-role chunk norm bounds
+  int RApad, RBpad;     // padded rows of the A-role (x128) and B-role (x64) slice arrays
+  int nch;             // K chunks
+  int TM, ntiles;       // tiles along the A-role rows; tiles in all (tile = tn TM + tm)
+  int upc;              // units (tile, chunk) per CTA
+  int swap;             // 1: the tile's A-role rows are D's columns (D^T computed)
+  int64_t M, N;         // valid A-role rows, B-role rows
+  double alpha, beta;
+  double* D;
+  int64_t ldd;
+  unsigned long long* acc_ws;   // split tiles: OX_TILE integer accumulators per tile (zero between calls)
+  int* cnt;                     // split tiles: chunks done per tile (zero between calls)
+  int* err;
+};
+
+// Bounded mbarrier wait that also gives up once another role of the CTA
+// has failed (so a failure does not cascade into one 2 s wait per role).
+__device__ __forceinline__ bool ox_wait(uint64_t* bar, uint32_t parity, volatile int* fail) {
+  const uint32_t a = smem_u32(bar);
+  unsigned long long t0 = 0;
+  for (uint32_t spin = 0;; ++spin) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((spin & 255u) == 255u) {
+      if (*fail) return false;
+      const unsigned long long t = global_ns();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > 2000000000ull) { *fail = 1; return false; }
+    }
+  }
+}
+
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, uint32_t (&ra)[16], uint32_t (&rb)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(ra[0]), "=r"(ra[1]), "=r"(ra[2]), "=r"(ra[3]), "=r"(ra[4]), "=r"(ra[5]), "=r"(ra[6]), "=r"(ra[7]),
+        "=r"(ra[8]), "=r"(ra[9]), "=r"(ra[10]), "=r"(ra[11]), "=r"(ra[12]), "=r"(ra[13]), "=r"(ra[14]), "=r"(ra[15])
+      : "r"(ta));
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(rb[0]), "=r"(rb[1]), "=r"(rb[2]), "=r"(rb[3]), "=r"(rb[4]), "=r"(rb[5]), "=r"(rb[6]), "=r"(rb[7]),
+        "=r"(rb[8]), "=r"(rb[9]), "=r"(rb[10]), "=r"(rb[11]), "=r"(rb[12]), "=r"(rb[13]), "=r"(rb[14]), "=r"(rb[15])
+      : "r"(tb));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// An exact group sum (an integer below 2^24 held in FP32) as an integer.
+__device__ __forceinline__ int gsum(uint32_t r) { return __float2int_rz(__uint_as_float(r)); }
+
+// round(x 2^-sh) for -62 <= sh <= 62 (halves rounded up; sh <= 0 is an exact left shift of a value
+// known to fit), without overflow for |x| < 2^63 - 1.
+__device__ __forceinline__ long long shift_round(long long x, int sh) {
+  if (sh <= 0) return static_cast<long long>(static_cast<unsigned long long>(x) << (-sh));
+  return ((x >> (sh - 1)) + 1) >> 1;
+}
+
+constexpr int kOzZeroNorm = -4000;   // norm exponent of an all-zero row or column
+
+// Smallest N with ||x||_2 < 2^N for a row (or column) x of an operand over
+// the whole K range, from its chunks' scales e_c and norm bounds n_c
+// (||x_c||_2^2 < n_c 2^(2 e_c - 14)): with E the largest e_c and
+// s = sum_c n_c 2^(2 (e_c - E) - 14) = m 2^t (m in [1/2, 1)), ||x||^2 <
+// 2^(2E + t), so N = E + ceil(t / 2).  Also returns E.
+__device__ __forceinline__ int ox_norm_exp(const int* __restrict__ e, const int* __restrict__ ns, int64_t stride,
+                                           int64_t idx, int nch, int* emax) {
+  int E = kOzZeroScale;
+  for (int c = 0; c < nch; ++c) E = max(E, __ldg(e + c * stride + idx));
+  *emax = E;
+  double sum = 0.0;
+  for (int c = 0; c < nch; ++c) {
+    const int nc = __ldg(ns + c * stride + idx);
+    if (nc > 0) {
+      const int k = 2 * (__ldg(e + c * stride + idx) - E) - 14;   // <= -14
+      if (k >= -1022) sum += static_cast<double>(nc) * __longlong_as_double(static_cast<long long>(1023 + k) << 52);
+    }
+  }
+  if (sum == 0.0) return kOzZeroNorm;
+  const int t = static_cast<int>((__double_as_longlong(sum) >> 52) & 0x7FF) - 1022;   // sum in [2^(t-1), 2^t)
+  return E + ((t + 1) >> 1);
+}
+
+// a 2^e rounded once to FP64 (round to nearest even), by integer arithmetic
+// in the normal range (FP64 conversion only outside it).
+__device__ __forceinline__ double fixed_to_double(long long a, int e) {
+  if (a == 0) return 0.0;
+  const unsigned long long neg = static_cast<unsigned long long>(a) >> 63;
+  unsigned long long m = neg ? (0ull - static_cast<unsigned long long>(a)) : static_cast<unsigned long long>(a);
+  const int lz = __clzll(static_cast<long long>(m));
+  m <<= lz;                                  // bit 63 set
+  unsigned long long mant = m >> 11;         // 53 bits with the leading one
+  const unsigned long long rem = m & 0x7FFull;
+  mant += static_cast<unsigned long long>((rem > 0x400ull) | ((rem == 0x400ull) & (mant & 1ull)));
+  const int be = 1023 + 63 - lz + e;        // biased exponent of the leading bit
+  if (be < 1 || be > 2045) {   // subnormal or overflowing result: FP64 scaling by exact powers of two
+    double v = static_cast<double>(a);
+    for (; e > 1000; e -= 1000) v *= 0x1p1000;
+    for (; e < -1000; e += 1000) v *= 0x1p-1000;
+    return v * __longlong_as_double(static_cast<long long>(1023 + e) << 52);
+  }
+  return __longlong_as_double(static_cast<long long>((neg << 63) + (static_cast<unsigned long long>(be - 1) << 52) +
+                                                     mant));
+}
+
+// TMA loads of the 8 B slices of K sub-block x of a CTA's units into ring stage x % OX_BST.
+__device__ __forceinline__ bool ox_load_b(const CUtensorMap* mapB, unsigned char* sB, uint64_t* bfull, uint64_t* bempty,
+                                          int nch, int TM, int RBpad, int u0, int x, volatile int* fail) {
+  const int u = u0 + (x >> 1), kb = x & 1, tile = u / nch, c = u % nch, tn = tile / TM;
+  const int st = x % OX_BST;
+  if (!ox_wait(&bempty[st], ((x / OX_BST) & 1) ^ 1, fail)) return false;
+  mbar_expect_tx(&bfull[st], OX_B_BYTES);
+  for (int t = 0; t < OX_S; ++t)
+    tma_load_2d(sB + st * OX_B_BYTES + t * OX_BSL, mapB, c * OZ_KC + kb * OZ_KB, t * RBpad + tn * OX_BN,
+                &bfull[st]);
+  return true;
+}
+
+__global__ void __launch_bounds__(OX_NT, 1)
+gemm_ozx_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                const OxParams p) {
+  extern __shared__ __align__(1024) unsigned char ox_smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(ox_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  unsigned char* sB = base;                                   // [OX_BST][OX_B_BYTES]
+  unsigned char* sA = base + OX_BST * OX_B_BYTES;             // [OX_AST][OX_A_BYTES]
+  uint64_t* bfull = reinterpret_cast<uint64_t*>(sA + OX_AST * OX_A_BYTES);
+  uint64_t* bempty = bfull + OX_BST;
+  uint64_t* afull = bempty + OX_BST;
+  uint64_t* aempty = afull + OX_AST;
+  uint64_t* accfull = aempty + OX_AST;     // [1]: a chunk's products are complete
+  uint64_t* gempty = accfull + 1;          // [OX_S]: group g read by every epilogue warp
+  uint64_t* mdone = gempty + OX_S;         // [1]: every product this CTA issued is complete
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
+  __shared__ int s_fail;
+  __shared__ int s_last;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nch = p.nch;
+  const int W = p.ntiles * nch;
+  const int u0 = static_cast<int>(blockIdx.x) * p.upc;
+  const int u1 = min(W, u0 + p.upc);
+  const int nx = 2 * max(0, u1 - u0);   // K sub-blocks of this CTA
+  volatile int* fail = &s_fail;
+
+  if (tid == 0) {
+    s_fail = 0;
+    for (int i = 0; i < OX_BST; ++i) { mbar_init(&bfull[i], 1); mbar_init(&bempty[i], 1); }
+    for (int i = 0; i < OX_AST; ++i) { mbar_init(&afull[i], 1); mbar_init(&aempty[i], 1); }
+    mbar_init(accfull, 1);
+    mbar_init(mdone, 1);
+    for (int g = 0; g < OX_S; ++g) mbar_init(&gempty[g], OX_EPI);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  int issued_a = 0, issued_b = 0;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- producer: the B slices of sub-block x + 1 right after A slice 7 of sub-block x
+      bool ok = nx == 0 || ox_load_b(&mapB, sB, bfull, bempty, nch, p.TM, p.RBpad, u0, 0, fail);
+      issued_b = ok && nx > 0 ? 1 : 0;
+      for (int x = 0; x < nx && ok; ++x) {
+        const int u = u0 + (x >> 1), kb = x & 1, tile = u / nch, c = u % nch, tm = tile % p.TM;
+        for (int s = OX_S - 1; s >= 0 && ok; --s) {
+          const int st = issued_a % OX_AST;
+          if (!ox_wait(&aempty[st], ((issued_a / OX_AST) & 1) ^ 1, fail)) { ok = false; break; }
+          mbar_expect_tx(&afull[st], OX_A_BYTES);
+          tma_load_2d(sA + st * OX_A_BYTES, &mapA, c * OZ_KC + kb * OZ_KB, s * p.RApad + tm * OZ_BM, &afull[st]);
+          ++issued_a;
+          if (s == OX_S - 1 && x + 1 < nx) {
+            ok = ox_load_b(&mapB, sB, bfull, bempty, nch, p.TM, p.RBpad, u0, x + 1, fail);
+            if (ok) ++issued_b;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      int ia = 0, cc = 0;
+      bool ok = true;
+      for (int x = 0; x < nx && ok; ++x) {
+        const int kb = x & 1, sb = x % OX_BST;
+        if (!ox_wait(&bfull[sb], (x / OX_BST) & 1, fail)) break;
+        const uint64_t bdesc = kmajor_sw128_desc(smem_u32(sB + sb * OX_B_BYTES));
+        for (int s = OX_S - 1; s >= 0; --s) {
+          const int st = ia % OX_AST;
+          if (!ox_wait(&afull[st], (ia / OX_AST) & 1, fail)) { ok = false; break; }
+          // the previous chunk's group s (and, before it, s + 1 .. 7) must have been read
+          if (kb == 0 && cc > 0 && !ox_wait(&gempty[s], (cc - 1) & 1, fail)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t adesc = kmajor_sw128_desc(smem_u32(sA + st * OX_A_BYTES));
+          const int nt = OX_S - s;   // B slices t = 0 .. nt - 1 meet A slice s
+#pragma unroll
+          for (int kk = 0; kk < OZ_KB / 16; ++kk) {   // K = 16 per instruction: 32 bytes (+2 in 16 B units)
+            const uint64_t a = adesc + 2ull * kk, b = bdesc + 2ull * kk;
+            const uint64_t bstep = OX_BSL >> 4;        // one B slice further in the descriptor's address
+            if (kb == 0 && kk == 0) {
+              // first products of the chunk: group s starts from zero, groups s + 1 .. 7 already hold
+              // this chunk's products of the slices above s
+              mma_bf16(tmem + s * OX_BN, a, b, oz_idesc(OX_BN), 0u);
+              if (nt > 1) {
+                const int n1 = min(nt - 1, 4);
+                mma_bf16(tmem + (s + 1) * OX_BN, a, b + bstep, oz_idesc(n1 * OX_BN), 1u);
+                if (nt > 5) mma_bf16(tmem + (s + 5) * OX_BN, a, b + 5 * bstep, oz_idesc((nt - 5) * OX_BN), 1u);
+              }
+            } else {
+              const int n1 = min(nt, 4);
+              mma_bf16(tmem + s * OX_BN, a, b, oz_idesc(n1 * OX_BN), 1u);
+              if (nt > 4) mma_bf16(tmem + (s + 4) * OX_BN, a, b + 4 * bstep, oz_idesc((nt - 4) * OX_BN), 1u);
+            }
+          }
+          mma_commit(&aempty[st]);
+          ++ia;
+        }
+        if (!ok) break;
+        mma_commit(&bempty[sb]);
+        if (kb == 1) {
+          mma_commit(accfull);
+          ++cc;
+        }
+      }
+      // no product may still write tensor memory when it is freed (also after a failure)
+      mma_commit(mdone);
+      volatile int nofail = 0;
+      ox_wait(mdone, 0, &nofail);
+    }
+  } else {
+    // ---- epilogue warps: lanes 32 (warp % 4) .. +31 of tensor memory, columns 32 h .. +31
+    const int ew = warp - 2, q = warp & 3, h = ew >> 2;
+    const int rloc = q * 32 + lane;
+    const uint32_t tl = tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(h * 32);
+    // every epilogue warp runs the same sequence of named barriers whatever happens: after a
+    // failure (a wait that ran out) the remaining chunks are skipped, not the barriers
+    int cc = 0;
+    bool ok = true;
+    for (int u = u0; u < u1;) {
+      const int tile = u / nch, c0 = u % nch, c1 = min(nch, c0 + (u1 - u)), seg = c1 - c0;
+      const int tm = tile % p.TM, tn = tile / p.TM;
+      const int rowA = tm * OZ_BM + rloc;
+      const int colB0 = tn * OX_BN + h * 32;
+      // norm exponents of this row and of the lane's column over the whole K range: the
+      // accumulator's unit is 2^(NA + NB - 62) >= |row| |column| 2^-62, so it cannot overflow
+      int EA, EBl;   // (largest chunk scales: unused beyond the norm exponents)
+      const int NA = ox_norm_exp(p.eA, p.nA, p.RApad, rowA, nch, &EA);
+      const int NBl = ox_norm_exp(p.eB, p.nB, p.RBpad, colB0 + lane, nch, &EBl);
+      long long acc[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc[j] = 0;
+      for (int c = c0; c < c1 && ok; ++c) {
+        // chunk c's F 2^-7 has the unit 2^(eA + eB - 56): shift right by (NA - eA - 6) + (NB - eB)
+        const int dA = NA - __ldg(p.eA + static_cast<int64_t>(c) * p.RApad + rowA) - 6;
+        const int dBl = NBl - __ldg(p.eB + static_cast<int64_t>(c) * p.RBpad + colB0 + lane);
+        const bool waited = ox_wait(accfull, cc & 1, fail);
+        if (!__all_sync(0xffffffffu, waited)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // F 2^-7 = high + low with high = P0 2^35 + P1 2^21, low = P2 2^7 + (P3 >> 7) and
+        // P_i = G_2i 2^7 + G_2i+1 (each an int32); high and low are each rounded once to the
+        // accumulator's unit (P3 and P1 wait in `carry` for their partner pair)
+        int carry[32];
+#pragma unroll 1
+        for (int pr = 3; pr >= 0; --pr) {
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            uint32_t ra[16], rb[16];
+            tmem_ld16x2(tl + (2 * pr + 1) * OX_BN + hh * 16, tl + (2 * pr) * OX_BN + hh * 16, ra, rb);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int jj = hh * 16 + j;
+              const int P = (gsum(rb[j]) << 7) + gsum(ra[j]);
+              if (pr == 3) {
+                carry[jj] = P >> 7;
+              } else if (pr == 1) {
+                carry[jj] = P;
+              } else {
+                const int sh = min(62, max(-62, dA + __shfl_sync(0xffffffffu, dBl, jj)));
+                // integer wrap-around is harmless: high + low = F 2^-7 fits (|F| < 2^70 - 2^18)
+                const long long t = pr == 2
+                    ? (static_cast<long long>(P) << 7) + carry[jj]
+                    : static_cast<long long>((static_cast<unsigned long long>(static_cast<long long>(P)) << 35) +
+                                             (static_cast<unsigned long long>(static_cast<long long>(carry[jj])) << 21));
+                acc[jj] += shift_round(t, sh);
+              }
+            }
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) { mbar_arrive(&gempty[2 * pr + 1]); mbar_arrive(&gempty[2 * pr]); }
+        }
+        ++cc;
+      }
+      bool store = ok;
+      if (seg < nch) {
+        // K range split between CTAs: integer atomics into the tile's accumulator; the CTA that
+        // completes the tile's chunk count reads the sum back, clears it and updates D
+        unsigned long long* ws = p.acc_ws + static_cast<int64_t>(tile) * OX_TILE + static_cast<int64_t>(h * 32) * OZ_BM +
+                                 rloc;
+        if (ok) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) atomicAdd(ws + j * OZ_BM, static_cast<unsigned long long>(acc[j]));
+        }
+        __threadfence();
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * OX_EPI) : "memory");
+        if (ew == 0 && lane == 0) {
+          // a failed CTA does not count its chunks: the tile is then never stored (the call
+          // reports the failure)
+          const int old = *fail ? 0 : atomicAdd(p.cnt + tile, seg);
+          s_last = (!*fail && old + seg == nch) ? 1 : 0;
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * OX_EPI) : "memory");
+        store = s_last != 0;
+        if (store) {
+          __threadfence();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc[j] = static_cast<long long>(__ldcg(ws + j * OZ_BM));
+#pragma unroll
+          for (int j = 0; j < 32; ++j) __stcg(ws + j * OZ_BM, 0ull);
+          if (ew == 0 && lane == 0) p.cnt[tile] = 0;
+        }
+      }
+      if (store) {
+        // 16 columns at a time: the C reads are issued together, then rounded values stored
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          double cv[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int64_t colB = colB0 + h2 * 16 + j;
+            cv[j] = 0.0;
+            if (p.beta != 0.0 && rowA < p.M && colB < p.N)
+              cv[j] = p.swap ? p.D[colB + static_cast<int64_t>(rowA) * p.ldd] : p.D[rowA + colB * p.ldd];
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int jj = h2 * 16 + j;
+            const int e = NA + __shfl_sync(0xffffffffu, NBl, jj) - 62;
+            const int64_t colB = colB0 + jj;
+            if (rowA < p.M && colB < p.N) {
+              const double v = fixed_to_double(acc[jj], e);
+              double out;
+              if (p.beta == 0.0) out = (p.alpha == 1.0) ? v : (p.alpha == -1.0 ? -v : p.alpha * v);
+              else if (p.beta == 1.0 && p.alpha == -1.0) out = cv[j] - v;
+              else if (p.beta == 1.0 && p.alpha == 1.0) out = cv[j] + v;
+              else out = fma(p.alpha, v, p.beta * cv[j]);
+              if (p.swap) p.D[colB + static_cast<int64_t>(rowA) * p.ldd] = out;
+              else p.D[rowA + colB * p.ldd] = out;
+            }
+          }
+        }
+      }
+      u += seg;
+    }
+  }
+  if (warp == 0 && lane == 0 && *fail) {
+    // copies in flight must land before the CTA exits: the last load of every stage
+    for (int st = 0; st < OX_BST; ++st) {
+      int last = -1;
+      for (int x = 0; x < issued_b; ++x) if (x % OX_BST == st) last = x;
+      if (last >= 0) { volatile int nofail = 0; ox_wait(&bfull[st], (last / OX_BST) & 1, &nofail); }
+    }
+    for (int st = 0; st < OX_AST; ++st) {
+      int last = -1;
+      for (int i = 0; i < issued_a; ++i) if (i % OX_AST == st) last = i;
+      if (last >= 0) { volatile int nofail = 0; ox_wait(&afull[st], (last / OX_AST) & 1, &nofail); }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (tid == 0 && s_fail) atomicOr(p.err, kDevErrTimeout);
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
+// ============================================================ FP32 form
+constexpr int OZ_ASTAGES = 2;
+constexpr int OZ_A_BYTES = OZ_BM * OZ_KB * 2;   // 16 KB: one A slice, one sub-block
+constexpr int OZ_NT = 192;
+
+// S slices of 7 bits per operand, tiles of 128 x BN, operands and result of
+// type T; S groups x BN columns of tensor memory.
+template <int S_, int BN_, typename T_>
+struct OzCfg {
+  static constexpr int S = S_, BN = BN_;
+  using T = T_;
+  static constexpr int W = 7 * S;                           // fixed-point bits of the slices
+  static constexpr int B_BYTES = BN * OZ_KB * 2;            // one B slice, one sub-block
+  static constexpr int B_ALL = 2 * S * B_BYTES;
+  static constexpr int SMEM = B_ALL + OZ_ASTAGES * OZ_A_BYTES + 1024 + 256;
+  static constexpr uint32_t TMEM_COLS = S * BN;
+  static constexpr uint32_t IDESC = oz_idesc(BN);
+  static_assert(S * OZ_KC * 127 * 127 < (1 << 24), "group sums exact in FP32");
+  static_assert(SMEM <= 113 * 1024 && TMEM_COLS <= 256, "two CTAs per SM");
+};
+using Oz32 = OzCfg<4, 64, float>;    // 28-bit slices: FP32 products
+
+// FP32 form: one CTA per 128 x 64 tile of D and K chunk.  warp 0 (one
+// thread): TMA loads of the 4 B slices of both 64-wide K sub-blocks
+// (resident) and the 8 A slice sub-blocks through a 2-stage ring; warp 1
+// (one thread): A slice s against B slices t <= 3 - s into the accumulator
+// of group s + t; warps 2-5: the 4 group sums combined in 64-bit integers,
+// rounded once to FP32 and scaled (the alpha/beta update, or a chunk partial).
 __global__ void __launch_bounds__(OZ_NT, 2)
-gemm_oz_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-               const int* __restrict__ eA, const int* __restrict__ eB, int MApad, int NBpad, int64_t M, int64_t N,
-               typename C::T alpha, typename C::T beta, typename C::T* __restrict__ D, int64_t ldd,
-               typename C::T* __restrict__ part, int* __restrict__ err) {
-  using T = typename C::T;
+gemm_oz32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                 const int* __restrict__ eA, const int* __restrict__ eB, int MApad, int NBpad, int64_t M, int64_t N,
+                 float alpha, float beta, float* __restrict__ D, int64_t ldd, float* __restrict__ part,
+                 int* __restrict__ err) {
+  using C = Oz32;
   constexpr int S = C::S, BN = C::BN;
   extern __shared__ __align__(1024) unsigned char oz_smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -218,7 +667,7 @@ gemm_oz_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (tid < BN) s_eB[tid] = eB[static_cast<int64_t>(z) * NBpad + n0 + tid];
-  if (warp == 0) {   // the S group accumulators: half of tensor memory, so two CTAs share an SM
+  if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(C::TMEM_COLS)
                  : "memory");
@@ -233,7 +682,6 @@ gemm_oz_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   const int kx0 = z * OZ_KC;
 
   if (warp == 0 && lane == 0) {
-    // producer: B slices of a sub-block, then its S A slices through the ring
     for (int i = 0; i < NA; ++i) {
       const int kb = i / S, s = i % S, st = i % OZ_ASTAGES;
       if (s == 0) {
@@ -247,7 +695,6 @@ gemm_oz_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       ++issued_a;
     }
   } else if (warp == 1 && lane == 0) {
-    // MMA issuer
     uint32_t inited = 0;   // groups that have received their first product
     for (int i = 0; i < NA; ++i) {
       const int kb = i / S, s = i % S, st = i % OZ_ASTAGES;
@@ -260,13 +707,13 @@ gemm_oz_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         const uint64_t db = kmajor_sw128_desc(smem_u32(tileB(kb, t)));
         const uint32_t dacc = tmem + static_cast<uint32_t>(g * BN);
 #pragma unroll
-        for (int kk = 0; kk < OZ_KB / 16; ++kk)   // K = 16 per instruction: 32 bytes (+2 in 16 B units)
+        for (int kk = 0; kk < OZ_KB / 16; ++kk)
           mma_bf16(dacc, da + 2ull * kk, db + 2ull * kk, C::IDESC, (((inited >> g) & 1u) || kk > 0) ? 1u : 0u);
         inited |= 1u << g;
       }
       mma_commit(&aempty[st]);
     }
-    mma_commit(done);   // arrives once every issued MMA has completed
+    mma_commit(done);
   }
   __syncwarp();
   const bool epi = warp >= 2;
@@ -278,7 +725,7 @@ gemm_oz_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   const bool ok = (s_fail == 0);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (epi && ok) {
-    const int quarter = warp & 3;   // the 32 tensor-memory lanes this warp may read
+    const int quarter = warp & 3;
     const int64_t row = m0 + quarter * 32 + lane;
     const int ea = eA[static_cast<int64_t>(z) * MApad + m0 + quarter * 32 + lane];
     for (int c0 = 0; c0 < BN; c0 += 8) {
@@ -294,34 +741,22 @@ gemm_oz_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
           long long gi[S];
 #pragma unroll
           for (int g = 0; g < S; ++g) gi[g] = static_cast<long long>(__float2int_rn(__uint_as_float(r[g][j])));
-          const int sc0 = ea + s_eB[c0 + j];
-          T v;
-          if constexpr (C::F32) {
-            // W 2^-35 = g0 2^-14 + g1 2^-21 + g2 2^-28 + g3 2^-35, |W| < 2^45: one rounding to FP32
-            const long long Wv = (gi[0] << 21) + (gi[1] << 14) + (gi[2] << 7) + gi[3];
-            v = __ll2float_rn(Wv);
-            const int sc = sc0 - 35;
-            v = (sc > -126 && sc < 128) ? v * __int_as_float((127 + sc) << 23) : ldexpf(v, sc);
-          } else {
-            const long long H = (gi[0] << 14) + (gi[1] << 7) + gi[2];
-            const long long L = (gi[3] << 28) + (gi[4] << 21) + (gi[5] << 14) + (gi[6] << 7) + gi[7];
-            v = fma(static_cast<double>(H), 0x1p35, static_cast<double>(L));   // one rounding
-            const int sc = sc0 - 63;
-            v = (sc > -1022 && sc < 1023) ? v * __longlong_as_double(static_cast<long long>(1023 + sc) << 52)
-                                          : ldexp(v, sc);
-          }
+          // W 2^-35 = g0 2^-14 + g1 2^-21 + g2 2^-28 + g3 2^-35, |W| < 2^45: one rounding to FP32
+          const long long Wv = (gi[0] << 21) + (gi[1] << 14) + (gi[2] << 7) + gi[3];
+          float v = __ll2float_rn(Wv);
+          const int sc = ea + s_eB[c0 + j] - 35;
+          v = (sc > -126 && sc < 128) ? v * __int_as_float((127 + sc) << 23) : ldexpf(v, sc);
           if (part) {
             part[static_cast<int64_t>(z) * M * N + row + col * M] = v;
           } else {
-            T* dp = D + row + col * ldd;
-            *dp = (beta == T(0)) ? alpha * v : fma(alpha, v, beta * *dp);
+            float* dp = D + row + col * ldd;
+            *dp = (beta == 0.0f) ? alpha * v : fmaf(alpha, v, beta * *dp);
           }
         }
       }
     }
   }
   if (!ok && tid == 0) atomicOr(err, kDevErrTimeout);
-  // drain: the producer's copies in flight must land before the CTA exits
   if (!ok && warp == 0 && lane == 0) {
     for (int b = 0; b < issued_b; ++b) mbar_wait(&bfull[b], 0, global_ns());
     for (int i = 0; i < issued_a; ++i) mbar_wait(&afull[i % OZ_ASTAGES], (i / OZ_ASTAGES) & 1, global_ns());
@@ -335,15 +770,15 @@ gemm_oz_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 }
 
 // D = alpha sum_z part[z] + beta D (chunks in order, summed in FP64).
-template <typename T>
-__global__ void oz_reduce_kernel(int64_t M, int64_t N, int nch, T alpha, const T* __restrict__ part, T beta,
-                                 T* __restrict__ D, int64_t ldd) {
+__global__ void oz32_reduce_kernel(int64_t M, int64_t N, int nch, float alpha, const float* __restrict__ part,
+                                   float beta, float* __restrict__ D, int64_t ldd) {
   const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (t >= M * N) return;
   double s = 0.0;
   for (int z = 0; z < nch; ++z) s += static_cast<double>(part[static_cast<int64_t>(z) * M * N + t]);
-  T* dp = D + (t % M) + (t / M) * ldd;
-  *dp = (beta == T(0)) ? static_cast<T>(alpha * s) : static_cast<T>(fma(static_cast<double>(alpha), s, static_cast<double>(beta) * static_cast<double>(*dp)));
+  float* dp = D + (t % M) + (t / M) * ldd;
+  *dp = (beta == 0.0f) ? static_cast<float>(alpha * s)
+                       : static_cast<float>(fma(static_cast<double>(alpha), s, static_cast<double>(beta) * *dp));
 }
 
 template <typename T>
@@ -371,14 +806,140 @@ bool make_slice_map(CUtensorMap* map, const __nv_bfloat16* ptr, int64_t Kpad, in
 inline int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 inline size_t al256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
+// ---------------------------------------------------------------- FP64 host
+// Workspace: the split-tile accumulators and counters first (fixed offset;
+// zero between calls: each split tile's last CTA clears them), then the
+// slices and scales of the call.
+constexpr size_t OX_HEAD = static_cast<size_t>(OX_SPLIT_TILES) * OX_TILE * 8 + OX_SPLIT_TILES * 4;
+
+struct OxLayout {
+  bool swap;
+  int64_t RA, RB;            // A-role and B-role rows (valid)
+  int64_t RApad, RBpad, Kpad;
+  int nch;
+  size_t head, sa, ea, sb, eb, total;
+};
+
+OxLayout ox_layout(int64_t m, int64_t n, int64_t k) {
+  OxLayout L;
+  L.swap = (n <= 256 && m > n);          // the thin operand takes the 128-row side; the large one is read once
+  L.RA = L.swap ? n : m;
+  L.RB = L.swap ? m : n;
+  L.nch = static_cast<int>((k + OZ_KC - 1) / OZ_KC);
+  L.RApad = rup(L.RA, OZ_BM);
+  L.RBpad = rup(L.RB, OX_BN);
+  L.Kpad = static_cast<int64_t>(L.nch) * OZ_KC;
+  L.head = al256(OX_HEAD);
+  L.sa = al256(static_cast<size_t>(OX_S) * L.RApad * L.Kpad * 2);
+  L.ea = al256(2 * static_cast<size_t>(L.nch) * L.RApad * 4);   // scales, then norm bounds
+  L.sb = al256(static_cast<size_t>(OX_S) * L.RBpad * L.Kpad * 2);
+  L.eb = al256(2 * static_cast<size_t>(L.nch) * L.RBpad * 4);
+  L.total = L.head + L.sa + L.ea + L.sb + L.eb;
+  return L;
+}
+
+PerDeviceOnce g_ozx_attr;
+
+cudaError_t ozx_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
+                    int64_t lda, const double* B, int64_t ldb, double beta, double* D, int64_t ldd, void* work,
+                    size_t work_bytes, int* err) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  const ProfToken tok = prof_begin(s, kProfGemmOz);
+  cudaError_t e = cudaSuccess;
+  if (k <= 0) {
+    oz_scale_kernel<double><<<static_cast<unsigned>((m * n + 255) / 256), 256, 0, s>>>(m, n, beta, D, ldd);
+    note_launch();
+    e = cudaGetLastError();
+    prof_end(s, tok, 0.0, 16.0 * m * n);
+    return e;
+  }
+  const OxLayout L = ox_layout(m, n, k);
+  if (work_bytes < L.total || !work) return cudaErrorInvalidValue;
+  if (L.RApad * OX_S >= (1ll << 31) || L.RBpad * OX_S >= (1ll << 31) || L.Kpad >= (1ll << 31)) return cudaErrorInvalidValue;
+  char* w = static_cast<char*>(work);
+  auto* acc_ws = reinterpret_cast<unsigned long long*>(w);
+  int* cnt = reinterpret_cast<int*>(w + static_cast<size_t>(OX_SPLIT_TILES) * OX_TILE * 8);
+  auto* SA = reinterpret_cast<__nv_bfloat16*>(w + L.head);
+  int* EA = reinterpret_cast<int*>(w + L.head + L.sa);
+  auto* SB = reinterpret_cast<__nv_bfloat16*>(w + L.head + L.sa + L.ea);
+  int* EB = reinterpret_cast<int*>(w + L.head + L.sa + L.ea + L.sb);
+  // op(A): rows = the m dimension, K contiguous when ta; op(B): columns = the n dimension, K contiguous when !tb
+  int* NA = EA + static_cast<int64_t>(L.nch) * L.RApad;
+  int* NB = EB + static_cast<int64_t>(L.nch) * L.RBpad;
+  __nv_bfloat16* Sm = L.swap ? SB : SA;
+  int* Em = L.swap ? EB : EA;
+  int* Nm = L.swap ? NB : NA;
+  __nv_bfloat16* Sn = L.swap ? SA : SB;
+  int* En = L.swap ? EA : EB;
+  int* Nn = L.swap ? NA : NB;
+  const int64_t mpad = L.swap ? L.RBpad : L.RApad, npad = L.swap ? L.RApad : L.RBpad;
+  oz_slice_kernel<OX_S, double><<<dim3(static_cast<unsigned>(mpad / 32), static_cast<unsigned>(L.nch)), 128, 0, s>>>(
+      m, k, A, lda, ta, mpad, L.Kpad, Sm, Em, Nm);
+  oz_slice_kernel<OX_S, double><<<dim3(static_cast<unsigned>(npad / 32), static_cast<unsigned>(L.nch)), 128, 0, s>>>(
+      n, k, B, ldb, !tb, npad, L.Kpad, Sn, En, Nn);
+  note_launch(2);
+  e = cudaGetLastError();
+  CUtensorMap ma, mb;
+  if (e == cudaSuccess && (!make_slice_map(&ma, SA, L.Kpad, OX_S * L.RApad, OZ_BM) ||
+                           !make_slice_map(&mb, SB, L.Kpad, OX_S * L.RBpad, OX_BN)))
+    e = cudaErrorInvalidValue;
+  if (e == cudaSuccess)
+    e = per_device_once(g_ozx_attr, [] {
+      return cudaFuncSetAttribute(gemm_ozx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OX_SMEM);
+    });
+  if (e == cudaSuccess) {
+    OxParams p;
+    p.eA = EA;
+    p.eB = EB;
+    p.nA = NA;
+    p.nB = NB;
+    p.RApad = static_cast<int>(L.RApad);
+    p.RBpad = static_cast<int>(L.RBpad);
+    p.nch = L.nch;
+    p.TM = static_cast<int>(L.RApad / OZ_BM);
+    p.ntiles = p.TM * static_cast<int>(L.RBpad / OX_BN);
+    p.swap = L.swap ? 1 : 0;
+    p.M = L.RA;
+    p.N = L.RB;
+    p.alpha = alpha;
+    p.beta = beta;
+    p.D = D;
+    p.ldd = ldd;
+    p.acc_ws = acc_ws;
+    p.cnt = cnt;
+    p.err = err;
+    const int64_t W = static_cast<int64_t>(p.ntiles) * L.nch;
+    int64_t grid;
+    if (L.nch >= 2 && p.ntiles <= OX_SPLIT_TILES && p.ntiles < 2 * kNumSMs) {
+      // few tiles, long K: the (tile, chunk) units spread evenly over one wave, tiles split between CTAs
+      grid = std::min<int64_t>(W, kNumSMs);
+      p.upc = static_cast<int>((W + grid - 1) / grid);
+    } else {
+      // whole tiles per CTA, up to 8, in as few waves as that allows
+      const int64_t waves = (p.ntiles + 8ll * kNumSMs - 1) / (8ll * kNumSMs);
+      const int64_t tpc = (p.ntiles + waves * kNumSMs - 1) / (waves * kNumSMs);
+      p.upc = static_cast<int>(tpc * L.nch);
+    }
+    grid = (W + p.upc - 1) / p.upc;
+    gemm_ozx_kernel<<<static_cast<unsigned>(grid), OX_NT, OX_SMEM, s>>>(ma, mb, p);
+    note_launch();
+    e = cudaGetLastError();
+  }
+  // flops of the product it stands for; bytes: operands once, slices written and read
+  prof_end(s, tok, 2.0 * m * n * k,
+           8.0 * (m * k + k * n + m * n * (beta != 0.0 ? 2.0 : 1.0)) + 2.0 * static_cast<double>(L.sa + L.sb));
+  return e;
+}
+
+// ---------------------------------------------------------------- FP32 host
 struct OzLayout {
   int64_t MApad, NBpad, Kpad;
   int nch;
   size_t sa, ea, sb, eb, pt, total;   // byte sizes
 };
 
-template <class C>
-OzLayout oz_layout(int64_t m, int64_t n, int64_t k) {
+OzLayout oz32_layout(int64_t m, int64_t n, int64_t k) {
+  using C = Oz32;
   OzLayout L;
   L.nch = static_cast<int>((k + OZ_KC - 1) / OZ_KC);
   L.MApad = rup(m, OZ_BM);
@@ -388,30 +949,28 @@ OzLayout oz_layout(int64_t m, int64_t n, int64_t k) {
   L.ea = al256(static_cast<size_t>(L.nch) * L.MApad * 4);
   L.sb = al256(static_cast<size_t>(C::S) * L.NBpad * L.Kpad * 2);
   L.eb = al256(static_cast<size_t>(L.nch) * L.NBpad * 4);
-  L.pt = L.nch > 1 ? al256(static_cast<size_t>(L.nch) * m * n * sizeof(typename C::T)) : 0;
+  L.pt = L.nch > 1 ? al256(static_cast<size_t>(L.nch) * m * n * sizeof(float)) : 0;
   L.total = L.sa + L.ea + L.sb + L.eb + L.pt;
   return L;
 }
 
-// D (m x n) = alpha op(A) op(B) + beta D, column-major: op(A) = A^T with A
-// k x m (ta) or A (m x k); op(B) = B (k x n, !tb) or B^T with B n x k.
-// work: oz_layout<C>(m, n, k).total bytes of device memory.
-template <class C>
-cudaError_t oz_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, typename C::T alpha,
-                   const typename C::T* A, int64_t lda, const typename C::T* B, int64_t ldb, typename C::T beta,
-                   typename C::T* D, int64_t ldd, void* work, size_t work_bytes, int* err, int prof_class) {
-  using T = typename C::T;
+PerDeviceOnce g_oz32_attr;
+
+cudaError_t oz32_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, float alpha, const float* A,
+                     int64_t lda, const float* B, int64_t ldb, float beta, float* D, int64_t ldd, void* work,
+                     size_t work_bytes, int* err) {
+  using C = Oz32;
   if (m <= 0 || n <= 0) return cudaSuccess;
-  const ProfToken tok = prof_begin(s, prof_class);
+  const ProfToken tok = prof_begin(s, kProfGemmOz32);
   cudaError_t e = cudaSuccess;
   if (k <= 0) {
-    oz_scale_kernel<T><<<static_cast<unsigned>((m * n + 255) / 256), 256, 0, s>>>(m, n, beta, D, ldd);
+    oz_scale_kernel<float><<<static_cast<unsigned>((m * n + 255) / 256), 256, 0, s>>>(m, n, beta, D, ldd);
     note_launch();
     e = cudaGetLastError();
-    prof_end(s, tok, 0.0, 2.0 * sizeof(T) * m * n);
+    prof_end(s, tok, 0.0, 8.0 * m * n);
     return e;
   }
-  const OzLayout L = oz_layout<C>(m, n, k);
+  const OzLayout L = oz32_layout(m, n, k);
   if (work_bytes < L.total || !work) return cudaErrorInvalidValue;
   if (L.MApad * C::S >= (1ll << 31) || L.NBpad * C::S >= (1ll << 31) || L.nch > 65535) return cudaErrorInvalidValue;
   char* w = static_cast<char*>(work);
@@ -419,41 +978,37 @@ cudaError_t oz_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64
   int* EA = reinterpret_cast<int*>(w + L.sa);
   auto* SB = reinterpret_cast<__nv_bfloat16*>(w + L.sa + L.ea);
   int* EB = reinterpret_cast<int*>(w + L.sa + L.ea + L.sb);
-  T* part = L.nch > 1 ? reinterpret_cast<T*>(w + L.sa + L.ea + L.sb + L.eb) : nullptr;
-  // op(A) rows = the m dimension, K contiguous when ta; op(B) columns = the n
-  // dimension, K contiguous when !tb
-  oz_slice_kernel<C::S, T><<<dim3(static_cast<unsigned>(L.MApad / 32), static_cast<unsigned>(L.nch)), 128, 0, s>>>(
-      m, k, A, lda, ta, L.MApad, L.Kpad, SA, EA);
-  oz_slice_kernel<C::S, T><<<dim3(static_cast<unsigned>(L.NBpad / 32), static_cast<unsigned>(L.nch)), 128, 0, s>>>(
-      n, k, B, ldb, !tb, L.NBpad, L.Kpad, SB, EB);
+  float* part = L.nch > 1 ? reinterpret_cast<float*>(w + L.sa + L.ea + L.sb + L.eb) : nullptr;
+  oz_slice_kernel<C::S, float><<<dim3(static_cast<unsigned>(L.MApad / 32), static_cast<unsigned>(L.nch)), 128, 0, s>>>(
+      m, k, A, lda, ta, L.MApad, L.Kpad, SA, EA, nullptr);
+  oz_slice_kernel<C::S, float><<<dim3(static_cast<unsigned>(L.NBpad / 32), static_cast<unsigned>(L.nch)), 128, 0, s>>>(
+      n, k, B, ldb, !tb, L.NBpad, L.Kpad, SB, EB, nullptr);
   note_launch(2);
   e = cudaGetLastError();
   CUtensorMap ma, mb;
   if (e == cudaSuccess && (!make_slice_map(&ma, SA, L.Kpad, C::S * L.MApad, OZ_BM) ||
                            !make_slice_map(&mb, SB, L.Kpad, C::S * L.NBpad, C::BN)))
     e = cudaErrorInvalidValue;
-  static bool attr = false;
-  if (e == cudaSuccess && !attr) {
-    e = cudaFuncSetAttribute(gemm_oz_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-    if (e == cudaSuccess) attr = true;
-  }
+  if (e == cudaSuccess)
+    e = per_device_once(g_oz32_attr, [] {
+      return cudaFuncSetAttribute(gemm_oz32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    });
   if (e == cudaSuccess) {
     dim3 grid(static_cast<unsigned>(L.MApad / OZ_BM), static_cast<unsigned>(L.NBpad / C::BN),
               static_cast<unsigned>(L.nch));
-    gemm_oz_kernel<C><<<grid, OZ_NT, C::SMEM, s>>>(ma, mb, EA, EB, static_cast<int>(L.MApad),
-                                                   static_cast<int>(L.NBpad), m, n, alpha, beta, D, ldd, part, err);
+    gemm_oz32_kernel<<<grid, OZ_NT, C::SMEM, s>>>(ma, mb, EA, EB, static_cast<int>(L.MApad), static_cast<int>(L.NBpad),
+                                                  m, n, alpha, beta, D, ldd, part, err);
     note_launch();
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && part) {
-    oz_reduce_kernel<T><<<static_cast<unsigned>((m * n + 255) / 256), 256, 0, s>>>(m, n, L.nch, alpha, part, beta,
-                                                                                  D, ldd);
+    oz32_reduce_kernel<<<static_cast<unsigned>((m * n + 255) / 256), 256, 0, s>>>(m, n, L.nch, alpha, part, beta, D,
+                                                                                 ldd);
     note_launch();
     e = cudaGetLastError();
   }
-  // flops of the product it stands for; bytes: operands once, slices written and read
   prof_end(s, tok, 2.0 * m * n * k,
-           sizeof(T) * (m * k + k * n + m * n * (beta != T(0) ? 2.0 : 1.0)) + 2.0 * static_cast<double>(L.sa + L.sb));
+           4.0 * (m * k + k * n + m * n * (beta != 0.0f ? 2.0 : 1.0)) + 2.0 * static_cast<double>(L.sa + L.sb));
   return e;
 }
 
@@ -461,12 +1016,14 @@ cudaError_t oz_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64
 
 size_t gemm_oz_work_bytes(int64_t m, int64_t n, int64_t k) {
   if (m <= 0 || n <= 0 || k <= 0) return 0;
-  return oz_layout<Oz64>(m, n, k).total;
+  return ox_layout(m, n, k).total;
 }
+
+size_t gemm_oz_head_bytes() { return al256(OX_HEAD); }
 
 size_t gemm_oz32_work_bytes(int64_t m, int64_t n, int64_t k) {
   if (m <= 0 || n <= 0 || k <= 0) return 0;
-  return oz_layout<Oz32>(m, n, k).total;
+  return oz32_layout(m, n, k).total;
 }
 
 bool gemm_oz_supported() { return encode_fn() != nullptr; }
@@ -474,13 +1031,13 @@ bool gemm_oz_supported() { return encode_fn() != nullptr; }
 cudaError_t gemm_oz(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* D, int64_t ldd,
                     void* work, size_t work_bytes, int* err) {
-  return oz_run<Oz64>(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, D, ldd, work, work_bytes, err, kProfGemmOz);
+  return ozx_run(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, D, ldd, work, work_bytes, err);
 }
 
 cudaError_t gemm_oz32(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, float alpha,
                       const float* A, int64_t lda, const float* B, int64_t ldb, float beta, float* D, int64_t ldd,
                       void* work, size_t work_bytes, int* err) {
-  return oz_run<Oz32>(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, D, ldd, work, work_bytes, err, kProfGemmOz32);
+  return oz32_run(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, D, ldd, work, work_bytes, err);
 }
 
 }  // namespace rutv
@@ -488,7 +1045,7 @@ cudaError_t gemm_oz32(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, in
 namespace {
 
 // The ABI entry points: argument checks, scratch from cudaMallocAsync on the
-// bound stream, synchronised.
+// bound stream (the FP64 form's split-tile head cleared), synchronised.
 template <typename T>
 int oz_abi(const char* name, char transa, char transb, int64_t m, int64_t n, int64_t k, T alpha, const T* A,
            int64_t lda, const T* B, int64_t ldb, T beta, T* C, int64_t ldc) {
@@ -511,16 +1068,18 @@ int oz_abi(const char* name, char transa, char transb, int64_t m, int64_t n, int
     set_last_error(msg);
     return RANDUTV_EUNSUPPORTED;
   }
+  constexpr bool F64 = std::is_same<T, double>::value;
   cudaStream_t s = current_stream();
-  const size_t wb = std::is_same<T, double>::value ? gemm_oz_work_bytes(m, n, k) : gemm_oz32_work_bytes(m, n, k);
+  const size_t wb = F64 ? gemm_oz_work_bytes(m, n, k) : gemm_oz32_work_bytes(m, n, k);
   void* ws = nullptr;
   int herr = 0;
   cudaError_t e = cudaMallocAsync(&ws, wb + 256, s);
   if (e != cudaSuccess) { cudaGetLastError(); return RANDUTV_ENOMEM; }
   int* err = reinterpret_cast<int*>(static_cast<char*>(ws) + wb);
   e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess && F64 && wb > 0) e = cudaMemsetAsync(ws, 0, gemm_oz_head_bytes(), s);
   if (e == cudaSuccess) {
-    if constexpr (std::is_same<T, double>::value)
+    if constexpr (F64)
       e = gemm_oz(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, wb, err);
     else
       e = gemm_oz32(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, wb, err);
@@ -531,7 +1090,9 @@ int oz_abi(const char* name, char transa, char transb, int64_t m, int64_t n, int
   cudaFreeAsync(ws, s);
   cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
-    set_last_error(cudaGetErrorString(e));
+    char msg[192];
+    snprintf(msg, sizeof(msg), "%s: %s", name, cudaGetErrorString(e));
+    set_last_error(msg);
     return RANDUTV_ECUDA;
   }
   return (herr & kDevErrTimeout) ? RANDUTV_ETIMEOUT : RANDUTV_OK;

@@ -1,9 +1,31 @@
 // Host-side interfaces between the engine and its kernels (not exported).
 #pragma once
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 
 namespace rutv {
+
+// One-time setup per device (kernel attributes such as the dynamic shared
+// memory limit are per device): per_device_once(o, init) runs init() the
+// first time it is called with a given current device and records success;
+// thread-safe.  Devices 64 and above run init() on every call.
+struct PerDeviceOnce {
+  std::mutex mu;
+  uint64_t done = 0;   // bit d: device d set up
+};
+template <class F>
+cudaError_t per_device_once(PerDeviceOnce& o, F init) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return init();
+  std::lock_guard<std::mutex> lk(o.mu);
+  if ((o.done >> dev) & 1ull) return cudaSuccess;
+  e = init();
+  if (e == cudaSuccess) o.done |= 1ull << dev;
+  return e;
+}
 
 // Process-wide stream used by every entry point.
 cudaStream_t current_stream();
@@ -66,6 +88,9 @@ cudaError_t gemm_oz(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int6
                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* D, int64_t ldd,
                     void* work, size_t work_bytes, int* err);
 size_t gemm_oz_work_bytes(int64_t m, int64_t n, int64_t k);
+// Leading bytes of a gemm_oz workspace that must be zero before its first
+// use (the split-tile accumulators; every call leaves them zero again).
+size_t gemm_oz_head_bytes();
 // The FP32 form (4 slices, FP32-accurate): the mixed form's updates.
 cudaError_t gemm_oz32(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, float alpha,
                       const float* A, int64_t lda, const float* B, int64_t ldb, float beta, float* D, int64_t ldd,

@@ -34,6 +34,8 @@ class Opts(ctypes.Structure):
         ("overlap", ctypes.c_int),
         ("tensor_cores", ctypes.c_int),
         ("fp64_emulation", ctypes.c_int),
+        ("sketch_prec", ctypes.c_int),
+        ("g_capture", ctypes.c_void_p),
     ]
 
 

@@ -46,6 +46,21 @@ def test_strerror_and_defaults(lib):
     assert (o.precision, o.form_uv, o.max_sweeps, o.p, o.seed, o.overlap, o.tensor_cores, o.fp64_emulation) == (
         0, 1, 30, 0, 998, 1, 1, 1)
     assert o.g_inject is None
+    assert o.sketch_prec == 0 and o.g_capture is None
+
+
+def test_sketch_prec_validation(lib):
+    # the FP64 form has one sketch precision; the mixed form takes the two tensor-core forms
+    from paper_1703_00998_gb300 import native
+    k = ctypes.c_int64(0)
+    dummy = ctypes.c_void_p(16)
+    o = native.default_opts()
+    o.sketch_prec = 1
+    assert lib.randutv_factor_ex(4, 4, dummy, 4, 2, 1, 0.0, dummy, 4, dummy, 4, dummy, 4, ctypes.byref(k),
+                                 ctypes.byref(o)) == -15
+    o.sketch_prec = 2
+    assert lib.randutv_factor_mixed(4, 4, dummy, 4, 2, 1, 0.0, dummy, 4, dummy, 4, dummy, 4, ctypes.byref(k),
+                                    ctypes.byref(o)) == -15
 
 
 def test_argument_validation(lib):

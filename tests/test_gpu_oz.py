@@ -1,7 +1,8 @@
 """Ozaki-scheme FP64 GEMM (BF16 tensor-core slice products, exact group
-sums, one FP64 rounding per K chunk of 128) against FP64 numpy: exact on
-small-integer inputs for all four transpose forms and K spanning several
-chunks, within the FP64 dot-product bound on Gaussian inputs, and within the
+sums, 64-bit fixed-point accumulation over the K chunks of 128, one FP64
+rounding at the end) against FP64 numpy: exact on small-integer inputs for
+all four transpose forms and K spanning several chunks (and several CTAs),
+within the FP64 dot-product bound on Gaussian inputs, and within the
 scheme's max-based bound on rows graded over 16 orders of magnitude."""
 import ctypes
 import numpy as np
