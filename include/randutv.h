@@ -78,13 +78,20 @@ typedef struct randutv_opts {
                            factors and products too small for its tiles
                            always use DFMA.  Needs about 24 n^2 bytes of
                            scratch per lane (n = max(m, n)).                 */
-  int sketch_prec;      /* mixed form with tensor_cores = 1: precision of the
-                           sketch products (Section 4.3, step 2; they decide
-                           which subspace a step captures, not the backward
-                           error): RANDUTV_SKETCH_3XTF32 (hi/lo TF32 split,
-                           three products, FP32 accumulation) or
-                           RANDUTV_SKETCH_TF32 (one TF32 product).  The FP64
-                           form requires RANDUTV_SKETCH_3XTF32 (ignored).     */
+  int sketch_prec;      /* mixed form: how the sketch products (Section 4.3,
+                           step 2) are formed; they decide which subspace a
+                           step captures, not the backward error, but on
+                           slowly decaying spectra FP32-level rounding of the
+                           sketch moves |diag T| far more than the FP32
+                           backward error does.  RANDUTV_SKETCH_OZAKI
+                           (default): tensor-core products of the FP32 trailing
+                           block, split exactly into 4 BF16 slices, with the
+                           FP64 G / Y / Z split into 5 (35 bits), FP64 results;
+                           RANDUTV_SKETCH_3XTF32: hi/lo TF32 split, three
+                           products, FP32 accumulation; RANDUTV_SKETCH_TF32:
+                           one TF32 product (both with tensor_cores = 1; FP32
+                           CUDA cores otherwise).  The FP64 form requires
+                           RANDUTV_SKETCH_OZAKI (its sketch is FP64).         */
   double* g_capture;    /* NULL, or a device buffer receiving every randomized
                            step's G (FP64) in the g_inject layout: a run with
                            the Philox stream records the matrices it used, so
@@ -93,12 +100,13 @@ typedef struct randutv_opts {
                            randomized steps i of (m - b(i-1)) (b + p).       */
 } randutv_opts;
 
-#define RANDUTV_SKETCH_3XTF32 0
-#define RANDUTV_SKETCH_TF32   1
+#define RANDUTV_SKETCH_OZAKI  0
+#define RANDUTV_SKETCH_3XTF32 1
+#define RANDUTV_SKETCH_TF32   2
 
 /* Defaults: FP64, form_uv = 1, max_sweeps = 30, p = 0, seed = 998, no g_inject,
    overlap = 1, tensor_cores = 1, fp64_emulation = 1, sketch_prec =
-   RANDUTV_SKETCH_3XTF32, no g_capture. */
+   RANDUTV_SKETCH_OZAKI, no g_capture. */
 void randutv_opts_default(randutv_opts* opts);
 
 /* Stream used by all later calls in this process (a cudaStream_t; NULL =

@@ -99,8 +99,10 @@ def factor_mixed(A, b=128, q=1, tol=0.0, seed=998, g_inject=None, form_uv=True, 
                  tensor_cores=1, sketch_prec=0, g_capture=None):
     """Mixed-precision randUTV: A is an (m, n) float32 CUDA tensor; U, T, V
     come back float32.  Panel QRs and small SVDs run in FP64 inside.
-    tensor_cores: 1 runs the sketch products on the tcgen05 tensor cores,
-    as 3xTF32 (sketch_prec 0) or one TF32 product (sketch_prec 1)."""
+    sketch_prec: 0 forms the sketch products from BF16 slices on the tensor
+    cores (the FP32 block exactly, G / Y / Z to 35 bits); 1 as 3xTF32 and 2
+    as one TF32 product on the tcgen05 tensor cores (tensor_cores = 1) or
+    the FP32 CUDA cores (tensor_cores = 0)."""
     torch = _torch()
     if not isinstance(A, torch.Tensor) or A.dim() != 2 or A.dtype != torch.float32 or not A.is_cuda:
         raise TypeError("A must be a 2-D float32 CUDA tensor")

@@ -302,7 +302,7 @@ void randutv_opts_default(randutv_opts* o) {
   o->overlap = 1;
   o->tensor_cores = 1;
   o->fp64_emulation = 1;
-  o->sketch_prec = RANDUTV_SKETCH_3XTF32;
+  o->sketch_prec = RANDUTV_SKETCH_OZAKI;
   o->g_capture = nullptr;
 }
 
@@ -351,7 +351,7 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
   if (opts.form_uv && ldv < n) return -13;
   if (!k_reached) return -14;
   if (opts.precision != RANDUTV_FP64 || opts.p < 0 || opts.max_sweeps < 1 ||
-      opts.sketch_prec != RANDUTV_SKETCH_3XTF32)
+      opts.sketch_prec != RANDUTV_SKETCH_OZAKI)
     return -15;
 
   const int64_t mn = std::min(m, n);

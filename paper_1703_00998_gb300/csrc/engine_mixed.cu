@@ -144,8 +144,10 @@ struct MWork {
   float *W1u, *W2u, *tmpu, *gwsu;
   float *tmps, *gwss;   // the SVD lane's rotation buffer and GEMM partials
   // FP64
-  double *G64, *Y64, *P64, *Vv64, *Vu64, *tau, *R, *Rt, *gram, *S64, *Us64, *Vs64, *d, *part, *jws, *gws64,
+  double *G64, *Y64, *Z64, *P64, *Vv64, *Vu64, *tau, *R, *Rt, *gram, *S64, *Us64, *Vs64, *d, *part, *jws, *gws64,
       *red, *scal;
+  void* oz = nullptr;   // workspace of the sliced sketch products (gemm_oz_sketch), or null
+  size_t ozb = 0;
   int64_t gws_elems, gws64_elems;
   unsigned* flags;
   void* base;
@@ -186,7 +188,7 @@ cudaError_t mwork_alloc(cudaStream_t s, int64_t m, int64_t n, int b, MWork* w) {
              {&w->W1u, mx * b}, {&w->W2u, mx * b}, {&w->tmpu, mx * b}, {&w->gwsu, w->gws_elems},
              {&w->tmps, mx * b}, {&w->gwss, w->gws_elems}};
   static_assert(kRing == 3, "ring buffers listed above");
-  I64 d[] = {{&w->G64, m * b}, {&w->Y64, mx * b}, {&w->P64, mx * b}, {&w->Vv64, mx * b}, {&w->Vu64, mx * b},
+  I64 d[] = {{&w->G64, m * b}, {&w->Y64, mx * b}, {&w->Z64, mx * b}, {&w->P64, mx * b}, {&w->Vv64, mx * b}, {&w->Vu64, mx * b},
              {&w->tau, b}, {&w->R, bb}, {&w->Rt, bb}, {&w->gram, bb}, {&w->S64, bb}, {&w->Us64, bb},
              {&w->Vs64, bb}, {&w->d, b}, {&w->part, panel_qr_part_elems(mx, b)}, {&w->jws, jacobi_work_elems(b)},
              {&w->gws64, w->gws64_elems}, {&w->red, kSumBlocks}, {&w->scal, 8}};
@@ -315,7 +317,8 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
   if (opts.form_uv && ldv < n) return -13;
   if (!k_reached) return -14;
   if (opts.p != 0 || opts.max_sweeps < 1 ||
-      (opts.sketch_prec != RANDUTV_SKETCH_3XTF32 && opts.sketch_prec != RANDUTV_SKETCH_TF32))
+      (opts.sketch_prec != RANDUTV_SKETCH_OZAKI && opts.sketch_prec != RANDUTV_SKETCH_3XTF32 &&
+       opts.sketch_prec != RANDUTV_SKETCH_TF32))
     return -15;
 
   const int64_t mn = std::min(m, n);
@@ -333,7 +336,22 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
   const int64_t nsteps = std::min((m + b - 1) / b, (n + b - 1) / b);
   {
     cudaError_t e = mwork_alloc(s, m, n, b, &w);
+    if (e == cudaSuccess && opts.sketch_prec == RANDUTV_SKETCH_OZAKI) {
+      if (!gemm_oz_supported()) {
+        set_last_error("sliced sketch: cuTensorMapEncodeTiled is not available");
+        if (w.base) cudaFreeAsync(w.base, s);
+        cudaStreamSynchronize(s);
+        return RANDUTV_EUNSUPPORTED;
+      }
+      const int64_t mx = std::max(m, n);
+      w.ozb = gemm_oz_sketch_work_bytes(mx, b, mx);   // bounds every sketch product of the factorization
+      e = cudaMallocAsync(&w.oz, w.ozb, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(w.oz, 0, gemm_oz_head_bytes(), s);
+    }
     if (e != cudaSuccess) {
+      if (w.oz) cudaFreeAsync(w.oz, s);
+      if (w.base) cudaFreeAsync(w.base, s);
+      cudaStreamSynchronize(s);
       cudaGetLastError();
       set_last_error("workspace allocation failed");
       return e == cudaErrorMemoryAllocation ? RANDUTV_ENOMEM : RANDUTV_ECUDA;
@@ -341,7 +359,7 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
   }
   {
     const bool tcl = opts.tensor_cores != 0;
-    const bool split = opts.sketch_prec == RANDUTV_SKETCH_3XTF32;
+    const bool split = opts.sketch_prec != RANDUTV_SKETCH_TF32;
     int* tc_err = reinterpret_cast<int*>(slot_of(w.flags, 3) + 2);
     gT = Mg{tcl, split, tc_err, w.gws, w.gws_elems};
     gU = Mg{tcl, split, tc_err, w.gwsu, w.gws_elems};
@@ -395,14 +413,25 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
             RUTV_MCK(cudaMemcpyAsync(opts.g_capture + g_off, w.G64, kr * b * sizeof(double),
                                      cudaMemcpyDeviceToDevice, sT));
         }
-        g_off += kr * b;
-        RUTV_MCK(gT.run(sT, kSketch, true, false, kc, b, kr, 1.f, X, ldt, w.G, kr, 0.f, w.Y, kc));
-        for (int j = 0; j < q; ++j) {
-          RUTV_MCK(gT.run(sT, kSketch, false, false, kr, b, kc, 1.f, X, ldt, w.Y, kc, 0.f, w.Z, kr));
-          RUTV_MCK(gT.run(sT, kSketch, true, false, kc, b, kr, 1.f, X, ldt, w.Z, kr, 0.f, w.Y, kc));
+        if (w.oz) {
+          // sliced sketch: the FP32 trailing block exactly, G / Y / Z to 35 bits, FP64 results
+          const double* G64 = opts.g_inject ? opts.g_inject + g_off : w.G64;
+          int* oz_err = reinterpret_cast<int*>(slot_of(w.flags, 3) + 2);
+          RUTV_MCK(gemm_oz_sketch(sT, true, false, kc, b, kr, X, ldt, G64, kr, w.Y64, kc, w.oz, w.ozb, oz_err));
+          for (int j = 0; j < q; ++j) {
+            RUTV_MCK(gemm_oz_sketch(sT, false, false, kr, b, kc, X, ldt, w.Y64, kc, w.Z64, kr, w.oz, w.ozb, oz_err));
+            RUTV_MCK(gemm_oz_sketch(sT, true, false, kc, b, kr, X, ldt, w.Z64, kr, w.Y64, kc, w.oz, w.ozb, oz_err));
+          }
+        } else {
+          RUTV_MCK(gT.run(sT, kSketch, true, false, kc, b, kr, 1.f, X, ldt, w.G, kr, 0.f, w.Y, kc));
+          for (int j = 0; j < q; ++j) {
+            RUTV_MCK(gT.run(sT, kSketch, false, false, kr, b, kc, 1.f, X, ldt, w.Y, kc, 0.f, w.Z, kr));
+            RUTV_MCK(gT.run(sT, kSketch, true, false, kc, b, kr, 1.f, X, ldt, w.Z, kr, 0.f, w.Y, kc));
+          }
+          RUTV_MCK(up(sT, kc, b, w.Y, kc, w.Y64, kc));
         }
+        g_off += kr * b;
         // QR(Y) in FP64
-        RUTV_MCK(up(sT, kc, b, w.Y, kc, w.Y64, kc));
         RUTV_MCK(panel_wy(sT, kc, b, w.Y64, w.tau, w.Vv64, w.Rt, w.gram, w.S64, Vv, Sv, w, slot_of(w.flags, 0)));
         RUTV_MCK(cudaEventRecord(L.v[sl], sT));
         // rows I2 of the previous step are rotated on the SVD lane: wait for it
@@ -500,6 +529,7 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
   if (prof_enabled()) prof_flush();
 done:
   L.join(s);
+  if (w.oz) cudaFreeAsync(w.oz, s);
   if (w.base) {
     cudaFreeAsync(w.base, s);
     cudaStreamSynchronize(s);

@@ -195,11 +195,11 @@ oz_slice_kernel(int64_t R, int64_t K, const T* __restrict__ X, int64_t ldx, bool
 }
 
 // ============================================================ FP64 form
-constexpr int OX_S = 8;                                   // slices per operand
+constexpr int OX_S = 8;                                   // largest slice count of an operand (and groups)
 constexpr int OX_BN = 64;                                 // B-role rows (output columns) of a tile
 constexpr int OX_A_BYTES = OZ_BM * OZ_KB * 2;             // 16 KB: one A slice, one K sub-block
 constexpr int OX_BSL = OX_BN * OZ_KB * 2;                 // 8 KB: one B slice, one K sub-block
-constexpr int OX_B_BYTES = OX_S * OX_BSL;                 // 64 KB: the 8 B slices side by side
+constexpr int OX_B_BYTES = OX_S * OX_BSL;                 // 64 KB stage: up to 8 B slices side by side
 constexpr int OX_AST = 5, OX_BST = 2;                     // ring stages
 constexpr int OX_EPI = 8;                                 // epilogue warps
 constexpr int OX_NT = 64 + 32 * OX_EPI;                   // 320 threads
@@ -323,21 +323,25 @@ __device__ __forceinline__ double fixed_to_double(long long a, int e) {
 }
 
 // TMA loads of the 8 B slices of K sub-block x of a CTA's units into ring stage x % OX_BST.
+template <int SB>
 __device__ __forceinline__ bool ox_load_b(const CUtensorMap* mapB, unsigned char* sB, uint64_t* bfull, uint64_t* bempty,
                                           int nch, int TM, int RBpad, int u0, int x, volatile int* fail) {
   const int u = u0 + (x >> 1), kb = x & 1, tile = u / nch, c = u % nch, tn = tile / TM;
   const int st = x % OX_BST;
   if (!ox_wait(&bempty[st], ((x / OX_BST) & 1) ^ 1, fail)) return false;
-  mbar_expect_tx(&bfull[st], OX_B_BYTES);
-  for (int t = 0; t < OX_S; ++t)
+  mbar_expect_tx(&bfull[st], SB * OX_BSL);
+  for (int t = 0; t < SB; ++t)
     tma_load_2d(sB + st * OX_B_BYTES + t * OX_BSL, mapB, c * OZ_KC + kb * OZ_KB, t * RBpad + tn * OX_BN,
                 &bfull[st]);
   return true;
 }
 
+// SA (SB): slices of the A-role (B-role) operand; GM: the last group formed (pairs s + t <= GM).
+template <int SA, int SB, int GM>
 __global__ void __launch_bounds__(OX_NT, 1)
 gemm_ozx_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 const OxParams p) {
+  static_assert(SA >= 1 && SA <= OX_S && SB >= 1 && SB <= OX_S && GM < OX_S && GM <= SA + SB - 2, "slices");
   extern __shared__ __align__(1024) unsigned char ox_smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(ox_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -386,18 +390,18 @@ gemm_ozx_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   if (warp == 0) {
     if (lane == 0) {
       // ---- producer: the B slices of sub-block x + 1 right after A slice 7 of sub-block x
-      bool ok = nx == 0 || ox_load_b(&mapB, sB, bfull, bempty, nch, p.TM, p.RBpad, u0, 0, fail);
+      bool ok = nx == 0 || ox_load_b<SB>(&mapB, sB, bfull, bempty, nch, p.TM, p.RBpad, u0, 0, fail);
       issued_b = ok && nx > 0 ? 1 : 0;
       for (int x = 0; x < nx && ok; ++x) {
         const int u = u0 + (x >> 1), kb = x & 1, tile = u / nch, c = u % nch, tm = tile % p.TM;
-        for (int s = OX_S - 1; s >= 0 && ok; --s) {
+        for (int s = SA - 1; s >= 0 && ok; --s) {
           const int st = issued_a % OX_AST;
           if (!ox_wait(&aempty[st], ((issued_a / OX_AST) & 1) ^ 1, fail)) { ok = false; break; }
           mbar_expect_tx(&afull[st], OX_A_BYTES);
           tma_load_2d(sA + st * OX_A_BYTES, &mapA, c * OZ_KC + kb * OZ_KB, s * p.RApad + tm * OZ_BM, &afull[st]);
           ++issued_a;
-          if (s == OX_S - 1 && x + 1 < nx) {
-            ok = ox_load_b(&mapB, sB, bfull, bempty, nch, p.TM, p.RBpad, u0, x + 1, fail);
+          if (s == SA - 1 && x + 1 < nx) {
+            ok = ox_load_b<SB>(&mapB, sB, bfull, bempty, nch, p.TM, p.RBpad, u0, x + 1, fail);
             if (ok) ++issued_b;
           }
         }
@@ -412,21 +416,32 @@ gemm_ozx_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         const int kb = x & 1, sb = x % OX_BST;
         if (!ox_wait(&bfull[sb], (x / OX_BST) & 1, fail)) break;
         const uint64_t bdesc = kmajor_sw128_desc(smem_u32(sB + sb * OX_B_BYTES));
-        for (int s = OX_S - 1; s >= 0; --s) {
+        for (int s = SA - 1; s >= 0; --s) {
           const int st = ia % OX_AST;
           if (!ox_wait(&afull[st], (ia / OX_AST) & 1, fail)) { ok = false; break; }
-          // the previous chunk's group s (and, before it, s + 1 .. 7) must have been read
-          if (kb == 0 && cc > 0 && !ox_wait(&gempty[s], (cc - 1) & 1, fail)) { ok = false; break; }
+          const int nt = min(SB, GM + 1 - s);   // B slices t = 0 .. nt - 1 meet A slice s (s + t <= GM)
+          // the previous chunk's groups must have been read before this slice writes them first:
+          // every group of the top slice, then group s
+          if (kb == 0 && cc > 0) {
+            const int gtop = (s == SA - 1) ? s + nt - 1 : s;
+            bool w = true;
+            for (int g = gtop; g >= s && w; --g) w = ox_wait(&gempty[g], (cc - 1) & 1, fail);
+            if (!w) { ok = false; break; }
+          }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint64_t adesc = kmajor_sw128_desc(smem_u32(sA + st * OX_A_BYTES));
-          const int nt = OX_S - s;   // B slices t = 0 .. nt - 1 meet A slice s
 #pragma unroll
           for (int kk = 0; kk < OZ_KB / 16; ++kk) {   // K = 16 per instruction: 32 bytes (+2 in 16 B units)
             const uint64_t a = adesc + 2ull * kk, b = bdesc + 2ull * kk;
             const uint64_t bstep = OX_BSL >> 4;        // one B slice further in the descriptor's address
-            if (kb == 0 && kk == 0) {
-              // first products of the chunk: group s starts from zero, groups s + 1 .. 7 already hold
-              // this chunk's products of the slices above s
+            if (kb == 0 && kk == 0 && s == SA - 1) {
+              // first products of the chunk: every group of the top slice starts from zero
+              const int n1 = min(nt, 4);
+              mma_bf16(tmem + s * OX_BN, a, b, oz_idesc(n1 * OX_BN), 0u);
+              if (nt > 4) mma_bf16(tmem + (s + 4) * OX_BN, a, b + 4 * bstep, oz_idesc((nt - 4) * OX_BN), 0u);
+            } else if (kb == 0 && kk == 0) {
+              // group s starts from zero; groups s + 1 .. already hold this chunk's products of the
+              // slices above s
               mma_bf16(tmem + s * OX_BN, a, b, oz_idesc(OX_BN), 0u);
               if (nt > 1) {
                 const int n1 = min(nt - 1, 4);
@@ -492,7 +507,18 @@ gemm_ozx_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
 #pragma unroll
           for (int hh = 0; hh < 2; ++hh) {
             uint32_t ra[16], rb[16];
-            tmem_ld16x2(tl + (2 * pr + 1) * OX_BN + hh * 16, tl + (2 * pr) * OX_BN + hh * 16, ra, rb);
+            if (2 * pr + 1 <= GM) {
+              tmem_ld16x2(tl + (2 * pr + 1) * OX_BN + hh * 16, tl + (2 * pr) * OX_BN + hh * 16, ra, rb);
+            } else {
+              // group 2 pr + 1 is not formed (its accumulator is never written): zero
+#pragma unroll
+              for (int j = 0; j < 16; ++j) ra[j] = 0u;
+              if (2 * pr <= GM) tmem_ld16(tl + (2 * pr) * OX_BN + hh * 16, rb);
+              else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) rb[j] = 0u;
+              }
+            }
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               const int jj = hh * 16 + j;
@@ -814,35 +840,68 @@ constexpr size_t OX_HEAD = static_cast<size_t>(OX_SPLIT_TILES) * OX_TILE * 8 + O
 
 struct OxLayout {
   bool swap;
+  int SAs, SBs;              // slices of the A-role and B-role operands
   int64_t RA, RB;            // A-role and B-role rows (valid)
   int64_t RApad, RBpad, Kpad;
   int nch;
   size_t head, sa, ea, sb, eb, total;
 };
 
-OxLayout ox_layout(int64_t m, int64_t n, int64_t k) {
+// sm (sn): slices of op(A) (op(B)).
+OxLayout ox_layout(int64_t m, int64_t n, int64_t k, int sm, int sn) {
   OxLayout L;
   L.swap = (n <= 256 && m > n);          // the thin operand takes the 128-row side; the large one is read once
   L.RA = L.swap ? n : m;
   L.RB = L.swap ? m : n;
+  L.SAs = L.swap ? sn : sm;
+  L.SBs = L.swap ? sm : sn;
   L.nch = static_cast<int>((k + OZ_KC - 1) / OZ_KC);
   L.RApad = rup(L.RA, OZ_BM);
   L.RBpad = rup(L.RB, OX_BN);
   L.Kpad = static_cast<int64_t>(L.nch) * OZ_KC;
   L.head = al256(OX_HEAD);
-  L.sa = al256(static_cast<size_t>(OX_S) * L.RApad * L.Kpad * 2);
+  L.sa = al256(static_cast<size_t>(L.SAs) * L.RApad * L.Kpad * 2);
   L.ea = al256(2 * static_cast<size_t>(L.nch) * L.RApad * 4);   // scales, then norm bounds
-  L.sb = al256(static_cast<size_t>(OX_S) * L.RBpad * L.Kpad * 2);
+  L.sb = al256(static_cast<size_t>(L.SBs) * L.RBpad * L.Kpad * 2);
   L.eb = al256(2 * static_cast<size_t>(L.nch) * L.RBpad * 4);
   L.total = L.head + L.sa + L.ea + L.sb + L.eb;
   return L;
 }
 
-PerDeviceOnce g_ozx_attr;
+// Slices of an operand: FP64 (f32 = false) or FP32 data, `slices` of them.
+void launch_slices(cudaStream_t s, bool f32, int slices, int64_t R, int64_t K, const void* X, int64_t ldx,
+                   bool kcontig, int64_t Rpad, int64_t Kpad, int nch, __nv_bfloat16* Sl, int* E, int* NS) {
+  const dim3 g(static_cast<unsigned>(Rpad / 32), static_cast<unsigned>(nch));
+  if (!f32 && slices == 8)
+    oz_slice_kernel<8, double><<<g, 128, 0, s>>>(R, K, static_cast<const double*>(X), ldx, kcontig, Rpad, Kpad, Sl, E, NS);
+  else if (!f32 && slices == 5)
+    oz_slice_kernel<5, double><<<g, 128, 0, s>>>(R, K, static_cast<const double*>(X), ldx, kcontig, Rpad, Kpad, Sl, E, NS);
+  else
+    oz_slice_kernel<4, float><<<g, 128, 0, s>>>(R, K, static_cast<const float*>(X), ldx, kcontig, Rpad, Kpad, Sl, E, NS);
+  note_launch();
+}
 
-cudaError_t ozx_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
-                    int64_t lda, const double* B, int64_t ldb, double beta, double* D, int64_t ldd, void* work,
-                    size_t work_bytes, int* err) {
+PerDeviceOnce g_ozx_attr_88, g_ozx_attr_54;
+
+template <int SA, int SB, int GM>
+cudaError_t launch_ozx(PerDeviceOnce& attr, unsigned grid, cudaStream_t s, const CUtensorMap& ma, const CUtensorMap& mb,
+                       const OxParams& p) {
+  cudaError_t e = per_device_once(attr, [] {
+    return cudaFuncSetAttribute(gemm_ozx_kernel<SA, SB, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize, OX_SMEM);
+  });
+  if (e != cudaSuccess) return e;
+  gemm_ozx_kernel<SA, SB, GM><<<grid, OX_NT, OX_SMEM, s>>>(ma, mb, p);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// D (m x n, FP64) = alpha op(A) op(B) + beta D, column-major.  op(A) (op(B))
+// holds FP32 data when a32 (b32), split into sm (sn) slices; the pairs
+// (slices, last group) supported are (8, 8 -> group 7), the FP64 products,
+// and (4 FP32, 5 FP64 -> group 5), the sketch of the mixed form.
+cudaError_t ozx_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const void* A,
+                    int64_t lda, bool a32, int sm, const void* B, int64_t ldb, bool b32, int sn, double beta, double* D,
+                    int64_t ldd, void* work, size_t work_bytes, int* err) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   const ProfToken tok = prof_begin(s, kProfGemmOz);
   cudaError_t e = cudaSuccess;
@@ -853,7 +912,9 @@ cudaError_t ozx_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int6
     prof_end(s, tok, 0.0, 16.0 * m * n);
     return e;
   }
-  const OxLayout L = ox_layout(m, n, k);
+  const OxLayout L = ox_layout(m, n, k, sm, sn);
+  const bool cfg88 = (L.SAs == 8 && L.SBs == 8), cfg54 = (L.SAs == 5 && L.SBs == 4);
+  if (!cfg88 && !cfg54) return cudaErrorInvalidValue;
   if (work_bytes < L.total || !work) return cudaErrorInvalidValue;
   if (L.RApad * OX_S >= (1ll << 31) || L.RBpad * OX_S >= (1ll << 31) || L.Kpad >= (1ll << 31)) return cudaErrorInvalidValue;
   char* w = static_cast<char*>(work);
@@ -863,30 +924,19 @@ cudaError_t ozx_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int6
   int* EA = reinterpret_cast<int*>(w + L.head + L.sa);
   auto* SB = reinterpret_cast<__nv_bfloat16*>(w + L.head + L.sa + L.ea);
   int* EB = reinterpret_cast<int*>(w + L.head + L.sa + L.ea + L.sb);
-  // op(A): rows = the m dimension, K contiguous when ta; op(B): columns = the n dimension, K contiguous when !tb
   int* NA = EA + static_cast<int64_t>(L.nch) * L.RApad;
   int* NB = EB + static_cast<int64_t>(L.nch) * L.RBpad;
-  __nv_bfloat16* Sm = L.swap ? SB : SA;
-  int* Em = L.swap ? EB : EA;
-  int* Nm = L.swap ? NB : NA;
-  __nv_bfloat16* Sn = L.swap ? SA : SB;
-  int* En = L.swap ? EA : EB;
-  int* Nn = L.swap ? NA : NB;
+  // op(A): rows = the m dimension, K contiguous when ta; op(B): columns = the n dimension, K contiguous when !tb
   const int64_t mpad = L.swap ? L.RBpad : L.RApad, npad = L.swap ? L.RApad : L.RBpad;
-  oz_slice_kernel<OX_S, double><<<dim3(static_cast<unsigned>(mpad / 32), static_cast<unsigned>(L.nch)), 128, 0, s>>>(
-      m, k, A, lda, ta, mpad, L.Kpad, Sm, Em, Nm);
-  oz_slice_kernel<OX_S, double><<<dim3(static_cast<unsigned>(npad / 32), static_cast<unsigned>(L.nch)), 128, 0, s>>>(
-      n, k, B, ldb, !tb, npad, L.Kpad, Sn, En, Nn);
-  note_launch(2);
+  launch_slices(s, a32, sm, m, k, A, lda, ta, mpad, L.Kpad, L.nch, L.swap ? SB : SA, L.swap ? EB : EA,
+                L.swap ? NB : NA);
+  launch_slices(s, b32, sn, n, k, B, ldb, !tb, npad, L.Kpad, L.nch, L.swap ? SA : SB, L.swap ? EA : EB,
+                L.swap ? NA : NB);
   e = cudaGetLastError();
   CUtensorMap ma, mb;
-  if (e == cudaSuccess && (!make_slice_map(&ma, SA, L.Kpad, OX_S * L.RApad, OZ_BM) ||
-                           !make_slice_map(&mb, SB, L.Kpad, OX_S * L.RBpad, OX_BN)))
+  if (e == cudaSuccess && (!make_slice_map(&ma, SA, L.Kpad, L.SAs * L.RApad, OZ_BM) ||
+                           !make_slice_map(&mb, SB, L.Kpad, L.SBs * L.RBpad, OX_BN)))
     e = cudaErrorInvalidValue;
-  if (e == cudaSuccess)
-    e = per_device_once(g_ozx_attr, [] {
-      return cudaFuncSetAttribute(gemm_ozx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OX_SMEM);
-    });
   if (e == cudaSuccess) {
     OxParams p;
     p.eA = EA;
@@ -921,13 +971,13 @@ cudaError_t ozx_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int6
       p.upc = static_cast<int>(tpc * L.nch);
     }
     grid = (W + p.upc - 1) / p.upc;
-    gemm_ozx_kernel<<<static_cast<unsigned>(grid), OX_NT, OX_SMEM, s>>>(ma, mb, p);
-    note_launch();
-    e = cudaGetLastError();
+    e = cfg88 ? launch_ozx<8, 8, 7>(g_ozx_attr_88, static_cast<unsigned>(grid), s, ma, mb, p)
+              : launch_ozx<5, 4, 5>(g_ozx_attr_54, static_cast<unsigned>(grid), s, ma, mb, p);
   }
   // flops of the product it stands for; bytes: operands once, slices written and read
   prof_end(s, tok, 2.0 * m * n * k,
-           8.0 * (m * k + k * n + m * n * (beta != 0.0 ? 2.0 : 1.0)) + 2.0 * static_cast<double>(L.sa + L.sb));
+           (a32 ? 4.0 : 8.0) * m * k + (b32 ? 4.0 : 8.0) * k * n + 8.0 * m * n * (beta != 0.0 ? 2.0 : 1.0) +
+               2.0 * static_cast<double>(L.sa + L.sb));
   return e;
 }
 
@@ -1016,7 +1066,12 @@ cudaError_t oz32_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int
 
 size_t gemm_oz_work_bytes(int64_t m, int64_t n, int64_t k) {
   if (m <= 0 || n <= 0 || k <= 0) return 0;
-  return ox_layout(m, n, k).total;
+  return ox_layout(m, n, k, 8, 8).total;
+}
+
+size_t gemm_oz_sketch_work_bytes(int64_t m, int64_t n, int64_t k) {
+  if (m <= 0 || n <= 0 || k <= 0) return 0;
+  return ox_layout(m, n, k, 4, 5).total;
 }
 
 size_t gemm_oz_head_bytes() { return al256(OX_HEAD); }
@@ -1031,7 +1086,13 @@ bool gemm_oz_supported() { return encode_fn() != nullptr; }
 cudaError_t gemm_oz(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* D, int64_t ldd,
                     void* work, size_t work_bytes, int* err) {
-  return ozx_run(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, D, ldd, work, work_bytes, err);
+  return ozx_run(s, ta, tb, m, n, k, alpha, A, lda, false, 8, B, ldb, false, 8, beta, D, ldd, work, work_bytes, err);
+}
+
+cudaError_t gemm_oz_sketch(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, const float* A,
+                           int64_t lda, const double* B, int64_t ldb, double* D, int64_t ldd, void* work,
+                           size_t work_bytes, int* err) {
+  return ozx_run(s, ta, tb, m, n, k, 1.0, A, lda, true, 4, B, ldb, false, 5, 0.0, D, ldd, work, work_bytes, err);
 }
 
 cudaError_t gemm_oz32(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, float alpha,

@@ -88,6 +88,13 @@ cudaError_t gemm_oz(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int6
                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* D, int64_t ldd,
                     void* work, size_t work_bytes, int* err);
 size_t gemm_oz_work_bytes(int64_t m, int64_t n, int64_t k);
+// D (m x n, FP64) = op(A) op(B) with op(A) FP32 data (split exactly into 4
+// slices) and op(B) FP64 data split into 5 slices (35 bits): the sketch
+// products of the mixed form, n <= 256 < m.  work: gemm_oz_sketch_work_bytes.
+cudaError_t gemm_oz_sketch(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, const float* A,
+                           int64_t lda, const double* B, int64_t ldb, double* D, int64_t ldd, void* work,
+                           size_t work_bytes, int* err);
+size_t gemm_oz_sketch_work_bytes(int64_t m, int64_t n, int64_t k);
 // Leading bytes of a gemm_oz workspace that must be zero before its first
 // use (the split-tile accumulators; every call leaves them zero again).
 size_t gemm_oz_head_bytes();

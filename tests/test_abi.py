@@ -58,7 +58,7 @@ def test_sketch_prec_validation(lib):
     o.sketch_prec = 1
     assert lib.randutv_factor_ex(4, 4, dummy, 4, 2, 1, 0.0, dummy, 4, dummy, 4, dummy, 4, ctypes.byref(k),
                                  ctypes.byref(o)) == -15
-    o.sketch_prec = 2
+    o.sketch_prec = 3
     assert lib.randutv_factor_mixed(4, 4, dummy, 4, 2, 1, 0.0, dummy, 4, dummy, 4, dummy, 4, ctypes.byref(k),
                                     ctypes.byref(o)) == -15
 

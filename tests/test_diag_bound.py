@@ -33,5 +33,5 @@ def test_sensitivity_takes_the_window_max():
 def test_perturbation_norm():
     E = perturbations((40, 30), 3.0, 1e-6, [1, 2])
     for e in E:
-        assert abs(np.linalg.norm(e, 2) - 3e-6) <= 1e-12
+        assert abs(np.linalg.norm(e, 2) - 3e-6) <= 1e-3 * 3e-6
     assert not np.allclose(E[0], E[1])
