@@ -35,26 +35,30 @@
 // several CTAs (their accumulators added with integer atomics) gives
 // bit-identical results in any order.
 //
-// FP64 kernel (gemm_ozx_kernel): one CTA per SM (320 threads, 209 KB of
-// shared memory, all 512 tensor-memory columns), working through a
-// contiguous range of units (tile, K chunk) of 128 x 64 output tiles:
+// FP64 kernel (gemm_ozx_kernel): one CTA per SM (208 KB of shared memory,
+// 512 tensor-memory columns), working through a contiguous range of units
+// (tile, K chunk) of 128 x BN output tiles (BN = 64 for long K, 48 for short
+// K; see OxT):
 //   warp 0 (one thread): TMA loads (128B swizzle, K-major): per 64-wide K
-//     sub-block, the 8 B slices of the tile's 64 columns side by side (a
-//     512-row operand, 64 KB, 2-stage ring) and the 8 A slices of its 128
-//     rows one by one (16 KB each, 5-stage ring);
+//     sub-block, the B slices of the tile's BN columns side by side (one
+//     operand of up to 8 BN rows, 2-stage ring) and the A slices of its 128
+//     rows one by one (16 KB each, 5- or 7-stage ring);
 //   warp 1 (one thread): tcgen05.mma.kind::f16 (BF16 in, FP32 out, M = 128,
-//     K = 16): A slice s against the B slices t = 0 .. 7 - s in one or two
-//     instructions (N = 64 (8 - s), split at 256), whose output columns land
-//     in the accumulators of groups s .. 7 (tensor-memory columns 64 g ..);
-//     slices in the order 7, 6, .., 0, so that the next chunk's products
-//     start on group 7 while the epilogue is still reading groups 5 .. 0;
-//   warps 2-9: per chunk, read the group accumulators in pairs (7, 6),
-//     (5, 4), (3, 2), (1, 0) (tcgen05.ld), release each pair to the MMA
-//     thread, and fold it into the 64-bit accumulators in registers (one
-//     row and 32 columns per thread); at a tile's end, round to FP64 and
-//     update D, or (when the tile's chunks are split between CTAs) add into
-//     the tile's integer accumulator with atomics, the last CTA of the tile
-//     doing the update.
+//     K = 16): A slice s against the B slices t it pairs with, in one or two
+//     instructions (N = BN x slices, split at 256), whose output columns land
+//     in the accumulators of groups s, s + 1, .. (tensor-memory columns
+//     BN g ..); slices in descending order, so that the next chunk's products
+//     start on the top groups while the epilogue is still reading the others;
+//   8 or 12 epilogue warps: per chunk, read the group accumulators in pairs
+//     (7, 6), (5, 4), (3, 2), (1, 0) (tcgen05.ld), release each pair to the
+//     MMA thread, and fold it into the 64-bit accumulators in registers (one
+//     row and 32 or 16 columns per thread); at a tile's end, round to FP64
+//     and update D, or (when the tile's chunks are split between CTAs) add
+//     into the tile's integer accumulator with atomics, the last CTA of the
+//     tile doing the update.
+// The slice counts are template parameters: 8 and 8 (group 7) for FP64 data,
+// 5 (FP64 data, 35 bits) and 4 (FP32 data, exact) up to group 5 for the
+// mixed form's sketch.
 // The FP32 form (FP32 operands and result: randutv_sgemm_oz) takes 4 slices
 // of 7 bits (28 bits, above FP32's 24), the 10 pairs with s + t <= 3 in 4
 // group accumulators, one CTA per 128 x 64 tile and K chunk, W = g0 2^21 +
@@ -196,19 +200,34 @@ oz_slice_kernel(int64_t R, int64_t K, const T* __restrict__ X, int64_t ldx, bool
 
 // ============================================================ FP64 form
 constexpr int OX_S = 8;                                   // largest slice count of an operand (and groups)
-constexpr int OX_BN = 64;                                 // B-role rows (output columns) of a tile
 constexpr int OX_A_BYTES = OZ_BM * OZ_KB * 2;             // 16 KB: one A slice, one K sub-block
-constexpr int OX_BSL = OX_BN * OZ_KB * 2;                 // 8 KB: one B slice, one K sub-block
-constexpr int OX_B_BYTES = OX_S * OX_BSL;                 // 64 KB stage: up to 8 B slices side by side
-constexpr int OX_AST = 5, OX_BST = 2;                     // ring stages
-constexpr int OX_EPI = 8;                                 // epilogue warps
-constexpr int OX_NT = 64 + 32 * OX_EPI;                   // 320 threads
-constexpr int OX_TILE = OZ_BM * OX_BN;                    // 8192 outputs per tile
-constexpr int OX_NBAR = 2 * OX_BST + 2 * OX_AST + 2 + OX_S;
-constexpr int OX_SMEM = OX_BST * OX_B_BYTES + OX_AST * OX_A_BYTES + 1024 + 8 * OX_NBAR + 16;
+constexpr int OX_BST = 2;                                 // B ring stages
+constexpr int OX_TILE = OZ_BM * 64;                       // outputs of the largest tile (128 x 64)
 constexpr int OX_SPLIT_TILES = 2 * kNumSMs;               // tiles whose K range may be split between CTAs
-static_assert(OX_SMEM <= 227 * 1024, "shared memory per CTA");
-static_assert(OX_S * OX_BN == 512, "the group accumulators fill tensor memory");
+
+// Tile shapes of the FP64 kernel: 128 x BN outputs.  BN = 64 with 8 epilogue
+// warps (32 columns each) for long K, where the products dominate and the
+// wider tile re-reads the 128-row operand's slices less; BN = 48 with 12
+// epilogue warps (16 columns each) for short K (rank-b updates), where the
+// per-tile epilogue dominates and more warps hide its latencies.  Both use
+// 208 KB of shared memory and one CTA per SM.
+template <int BN_>
+struct OxT {
+  static constexpr int BN = BN_;
+  static constexpr int MT = 256 / BN;                     // B slices one MMA covers (N <= 256)
+  static constexpr int BSL = BN * OZ_KB * 2;              // one B slice, one K sub-block
+  static constexpr int B_BYTES = OX_S * BSL;              // a B stage: up to 8 slices side by side
+  static constexpr int AST = BN == 64 ? 5 : 7;            // A ring stages
+  static constexpr int EPI = BN == 64 ? 8 : 12;           // epilogue warps (EPI / 4 per TMEM lane quarter)
+  static constexpr int EC = 4 * BN / EPI;                 // columns per epilogue warp: 32 or 16
+  static constexpr int NT = 64 + 32 * EPI;                // 320 or 448 threads
+  static constexpr int NBAR = 2 * OX_BST + 2 * AST + 2 + OX_S;
+  static constexpr int SMEM = OX_BST * B_BYTES + AST * OX_A_BYTES + 1024 + 8 * NBAR + 16;
+  static_assert(BN == 64 || BN == 48, "tile widths");
+  static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
+  static_assert(OX_S * BN <= 512, "the group accumulators fit tensor memory");
+  static_assert(BSL % 1024 == 0, "B slices start on swizzle atoms");
+};
 
 struct OxParams {
   const int* eA;        // A-role chunk scales e[c RApad + r]
@@ -323,35 +342,37 @@ __device__ __forceinline__ double fixed_to_double(long long a, int e) {
 }
 
 // TMA loads of the 8 B slices of K sub-block x of a CTA's units into ring stage x % OX_BST.
-template <int SB>
+template <int SB, class C>
 __device__ __forceinline__ bool ox_load_b(const CUtensorMap* mapB, unsigned char* sB, uint64_t* bfull, uint64_t* bempty,
                                           int nch, int TM, int RBpad, int u0, int x, volatile int* fail) {
   const int u = u0 + (x >> 1), kb = x & 1, tile = u / nch, c = u % nch, tn = tile / TM;
   const int st = x % OX_BST;
   if (!ox_wait(&bempty[st], ((x / OX_BST) & 1) ^ 1, fail)) return false;
-  mbar_expect_tx(&bfull[st], SB * OX_BSL);
+  mbar_expect_tx(&bfull[st], SB * C::BSL);
   for (int t = 0; t < SB; ++t)
-    tma_load_2d(sB + st * OX_B_BYTES + t * OX_BSL, mapB, c * OZ_KC + kb * OZ_KB, t * RBpad + tn * OX_BN,
+    tma_load_2d(sB + st * C::B_BYTES + t * C::BSL, mapB, c * OZ_KC + kb * OZ_KB, t * RBpad + tn * C::BN,
                 &bfull[st]);
   return true;
 }
 
-// SA (SB): slices of the A-role (B-role) operand; GM: the last group formed (pairs s + t <= GM).
-template <int SA, int SB, int GM>
-__global__ void __launch_bounds__(OX_NT, 1)
+// SA (SB): slices of the A-role (B-role) operand; GM: the last group formed (pairs s + t <= GM);
+// BN: the tile width (OxT).
+template <int SA, int SB, int GM, int BN>
+__global__ void __launch_bounds__(OxT<BN>::NT, 1)
 gemm_ozx_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 const OxParams p) {
   static_assert(SA >= 1 && SA <= OX_S && SB >= 1 && SB <= OX_S && GM < OX_S && GM <= SA + SB - 2, "slices");
+  using C = OxT<BN>;
   extern __shared__ __align__(1024) unsigned char ox_smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(ox_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  unsigned char* sB = base;                                   // [OX_BST][OX_B_BYTES]
-  unsigned char* sA = base + OX_BST * OX_B_BYTES;             // [OX_AST][OX_A_BYTES]
-  uint64_t* bfull = reinterpret_cast<uint64_t*>(sA + OX_AST * OX_A_BYTES);
+  unsigned char* sB = base;                                   // [OX_BST][C::B_BYTES]
+  unsigned char* sA = base + OX_BST * C::B_BYTES;             // [C::AST][OX_A_BYTES]
+  uint64_t* bfull = reinterpret_cast<uint64_t*>(sA + C::AST * OX_A_BYTES);
   uint64_t* bempty = bfull + OX_BST;
   uint64_t* afull = bempty + OX_BST;
-  uint64_t* aempty = afull + OX_AST;
-  uint64_t* accfull = aempty + OX_AST;     // [1]: a chunk's products are complete
+  uint64_t* aempty = afull + C::AST;
+  uint64_t* accfull = aempty + C::AST;     // [1]: a chunk's products are complete
   uint64_t* gempty = accfull + 1;          // [OX_S]: group g read by every epilogue warp
   uint64_t* mdone = gempty + OX_S;         // [1]: every product this CTA issued is complete
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
@@ -369,10 +390,10 @@ gemm_ozx_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   if (tid == 0) {
     s_fail = 0;
     for (int i = 0; i < OX_BST; ++i) { mbar_init(&bfull[i], 1); mbar_init(&bempty[i], 1); }
-    for (int i = 0; i < OX_AST; ++i) { mbar_init(&afull[i], 1); mbar_init(&aempty[i], 1); }
+    for (int i = 0; i < C::AST; ++i) { mbar_init(&afull[i], 1); mbar_init(&aempty[i], 1); }
     mbar_init(accfull, 1);
     mbar_init(mdone, 1);
-    for (int g = 0; g < OX_S; ++g) mbar_init(&gempty[g], OX_EPI);
+    for (int g = 0; g < OX_S; ++g) mbar_init(&gempty[g], C::EPI);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -390,18 +411,18 @@ gemm_ozx_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   if (warp == 0) {
     if (lane == 0) {
       // ---- producer: the B slices of sub-block x + 1 right after A slice 7 of sub-block x
-      bool ok = nx == 0 || ox_load_b<SB>(&mapB, sB, bfull, bempty, nch, p.TM, p.RBpad, u0, 0, fail);
+      bool ok = nx == 0 || ox_load_b<SB, C>(&mapB, sB, bfull, bempty, nch, p.TM, p.RBpad, u0, 0, fail);
       issued_b = ok && nx > 0 ? 1 : 0;
       for (int x = 0; x < nx && ok; ++x) {
         const int u = u0 + (x >> 1), kb = x & 1, tile = u / nch, c = u % nch, tm = tile % p.TM;
         for (int s = SA - 1; s >= 0 && ok; --s) {
-          const int st = issued_a % OX_AST;
-          if (!ox_wait(&aempty[st], ((issued_a / OX_AST) & 1) ^ 1, fail)) { ok = false; break; }
+          const int st = issued_a % C::AST;
+          if (!ox_wait(&aempty[st], ((issued_a / C::AST) & 1) ^ 1, fail)) { ok = false; break; }
           mbar_expect_tx(&afull[st], OX_A_BYTES);
           tma_load_2d(sA + st * OX_A_BYTES, &mapA, c * OZ_KC + kb * OZ_KB, s * p.RApad + tm * OZ_BM, &afull[st]);
           ++issued_a;
           if (s == SA - 1 && x + 1 < nx) {
-            ok = ox_load_b<SB>(&mapB, sB, bfull, bempty, nch, p.TM, p.RBpad, u0, x + 1, fail);
+            ok = ox_load_b<SB, C>(&mapB, sB, bfull, bempty, nch, p.TM, p.RBpad, u0, x + 1, fail);
             if (ok) ++issued_b;
           }
         }
@@ -415,10 +436,10 @@ gemm_ozx_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       for (int x = 0; x < nx && ok; ++x) {
         const int kb = x & 1, sb = x % OX_BST;
         if (!ox_wait(&bfull[sb], (x / OX_BST) & 1, fail)) break;
-        const uint64_t bdesc = kmajor_sw128_desc(smem_u32(sB + sb * OX_B_BYTES));
+        const uint64_t bdesc = kmajor_sw128_desc(smem_u32(sB + sb * C::B_BYTES));
         for (int s = SA - 1; s >= 0; --s) {
-          const int st = ia % OX_AST;
-          if (!ox_wait(&afull[st], (ia / OX_AST) & 1, fail)) { ok = false; break; }
+          const int st = ia % C::AST;
+          if (!ox_wait(&afull[st], (ia / C::AST) & 1, fail)) { ok = false; break; }
           const int nt = min(SB, GM + 1 - s);   // B slices t = 0 .. nt - 1 meet A slice s (s + t <= GM)
           // the previous chunk's groups must have been read before this slice writes them first:
           // every group of the top slice, then group s
@@ -433,25 +454,29 @@ gemm_ozx_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
 #pragma unroll
           for (int kk = 0; kk < OZ_KB / 16; ++kk) {   // K = 16 per instruction: 32 bytes (+2 in 16 B units)
             const uint64_t a = adesc + 2ull * kk, b = bdesc + 2ull * kk;
-            const uint64_t bstep = OX_BSL >> 4;        // one B slice further in the descriptor's address
+            const uint64_t bstep = C::BSL >> 4;        // one B slice further in the descriptor's address
             if (kb == 0 && kk == 0 && s == SA - 1) {
               // first products of the chunk: every group of the top slice starts from zero
-              const int n1 = min(nt, 4);
-              mma_bf16(tmem + s * OX_BN, a, b, oz_idesc(n1 * OX_BN), 0u);
-              if (nt > 4) mma_bf16(tmem + (s + 4) * OX_BN, a, b + 4 * bstep, oz_idesc((nt - 4) * OX_BN), 0u);
+              const int n1 = min(nt, C::MT);
+              mma_bf16(tmem + s * BN, a, b, oz_idesc(n1 * BN), 0u);
+              if (nt > C::MT)
+                mma_bf16(tmem + (s + C::MT) * BN, a, b + C::MT * bstep, oz_idesc((nt - C::MT) * BN), 0u);
             } else if (kb == 0 && kk == 0) {
               // group s starts from zero; groups s + 1 .. already hold this chunk's products of the
               // slices above s
-              mma_bf16(tmem + s * OX_BN, a, b, oz_idesc(OX_BN), 0u);
+              mma_bf16(tmem + s * BN, a, b, oz_idesc(BN), 0u);
               if (nt > 1) {
-                const int n1 = min(nt - 1, 4);
-                mma_bf16(tmem + (s + 1) * OX_BN, a, b + bstep, oz_idesc(n1 * OX_BN), 1u);
-                if (nt > 5) mma_bf16(tmem + (s + 5) * OX_BN, a, b + 5 * bstep, oz_idesc((nt - 5) * OX_BN), 1u);
+                const int n1 = min(nt - 1, C::MT);
+                mma_bf16(tmem + (s + 1) * BN, a, b + bstep, oz_idesc(n1 * BN), 1u);
+                if (nt > 1 + C::MT)
+                  mma_bf16(tmem + (s + 1 + C::MT) * BN, a, b + (1 + C::MT) * bstep,
+                           oz_idesc((nt - 1 - C::MT) * BN), 1u);
               }
             } else {
-              const int n1 = min(nt, 4);
-              mma_bf16(tmem + s * OX_BN, a, b, oz_idesc(n1 * OX_BN), 1u);
-              if (nt > 4) mma_bf16(tmem + (s + 4) * OX_BN, a, b + 4 * bstep, oz_idesc((nt - 4) * OX_BN), 1u);
+              const int n1 = min(nt, C::MT);
+              mma_bf16(tmem + s * BN, a, b, oz_idesc(n1 * BN), 1u);
+              if (nt > C::MT)
+                mma_bf16(tmem + (s + C::MT) * BN, a, b + C::MT * bstep, oz_idesc((nt - C::MT) * BN), 1u);
             }
           }
           mma_commit(&aempty[st]);
@@ -470,10 +495,10 @@ gemm_ozx_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       ox_wait(mdone, 0, &nofail);
     }
   } else {
-    // ---- epilogue warps: lanes 32 (warp % 4) .. +31 of tensor memory, columns 32 h .. +31
+    // ---- epilogue warps: lanes 32 (warp % 4) .. +31 of tensor memory, columns C::EC h .. + C::EC - 1
     const int ew = warp - 2, q = warp & 3, h = ew >> 2;
     const int rloc = q * 32 + lane;
-    const uint32_t tl = tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(h * 32);
+    const uint32_t tl = tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(h * C::EC);
     // every epilogue warp runs the same sequence of named barriers whatever happens: after a
     // failure (a wait that ran out) the remaining chunks are skipped, not the barriers
     int cc = 0;
@@ -482,53 +507,80 @@ gemm_ozx_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       const int tile = u / nch, c0 = u % nch, c1 = min(nch, c0 + (u1 - u)), seg = c1 - c0;
       const int tm = tile % p.TM, tn = tile / p.TM;
       const int rowA = tm * OZ_BM + rloc;
-      const int colB0 = tn * OX_BN + h * 32;
+      const int colB0 = tn * BN + h * C::EC;
+      const int lc = lane & (C::EC - 1);   // the column of this warp's range that the lane describes
       // norm exponents of this row and of the lane's column over the whole K range: the
       // accumulator's unit is 2^(NA + NB - 62) >= |row| |column| 2^-62, so it cannot overflow
       int EA, EBl;   // (largest chunk scales: unused beyond the norm exponents)
       const int NA = ox_norm_exp(p.eA, p.nA, p.RApad, rowA, nch, &EA);
-      const int NBl = ox_norm_exp(p.eB, p.nB, p.RBpad, colB0 + lane, nch, &EBl);
-      long long acc[32];
+      const int NBl = ox_norm_exp(p.eB, p.nB, p.RBpad, colB0 + lc, nch, &EBl);
+      long long acc[C::EC];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) acc[j] = 0;
+      for (int j = 0; j < C::EC; ++j) acc[j] = 0;
       for (int c = c0; c < c1 && ok; ++c) {
         // chunk c's F 2^-7 has the unit 2^(eA + eB - 56): shift right by (NA - eA - 6) + (NB - eB)
         const int dA = NA - __ldg(p.eA + static_cast<int64_t>(c) * p.RApad + rowA) - 6;
-        const int dBl = NBl - __ldg(p.eB + static_cast<int64_t>(c) * p.RBpad + colB0 + lane);
+        const int dBl = NBl - __ldg(p.eB + static_cast<int64_t>(c) * p.RBpad + colB0 + lc);
+        // the chunk's shift of each of the columns, one byte each (-62 .. 62, offset by 64)
+        // (32-column warps shuffle it when needed instead: registers)
+        constexpr bool kPacked = C::EC == 16;
+        uint32_t shp[kPacked ? C::EC / 4 : 1];
+        if constexpr (kPacked) {
+#pragma unroll
+          for (int j4 = 0; j4 < C::EC / 4; ++j4) {
+            uint32_t wv = 0;
+#pragma unroll
+            for (int bb = 0; bb < 4; ++bb) {
+              const int sh = min(62, max(-62, dA + __shfl_sync(0xffffffffu, dBl, 4 * j4 + bb)));
+              wv |= static_cast<uint32_t>(sh + 64) << (8 * bb);
+            }
+            shp[j4] = wv;
+          }
+        }
         const bool waited = ox_wait(accfull, cc & 1, fail);
         if (!__all_sync(0xffffffffu, waited)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // F 2^-7 = high + low with high = P0 2^35 + P1 2^21, low = P2 2^7 + (P3 >> 7) and
         // P_i = G_2i 2^7 + G_2i+1 (each an int32); high and low are each rounded once to the
         // accumulator's unit (P3 and P1 wait in `carry` for their partner pair)
-        int carry[32];
+        int carry[C::EC];
 #pragma unroll 1
         for (int pr = 3; pr >= 0; --pr) {
 #pragma unroll
-          for (int hh = 0; hh < 2; ++hh) {
+          for (int hh = 0; hh < C::EC / 16; ++hh) {
             uint32_t ra[16], rb[16];
             if (2 * pr + 1 <= GM) {
-              tmem_ld16x2(tl + (2 * pr + 1) * OX_BN + hh * 16, tl + (2 * pr) * OX_BN + hh * 16, ra, rb);
+              tmem_ld16x2(tl + (2 * pr + 1) * BN + hh * 16, tl + (2 * pr) * BN + hh * 16, ra, rb);
             } else {
               // group 2 pr + 1 is not formed (its accumulator is never written): zero
 #pragma unroll
               for (int j = 0; j < 16; ++j) ra[j] = 0u;
-              if (2 * pr <= GM) tmem_ld16(tl + (2 * pr) * OX_BN + hh * 16, rb);
+              if (2 * pr <= GM) tmem_ld16(tl + (2 * pr) * BN + hh * 16, rb);
               else {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) rb[j] = 0u;
               }
             }
+            if (hh == C::EC / 16 - 1) {
+              // the pair's accumulators are in registers: release them to the next chunk's products
+              asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+              __syncwarp();
+              if (lane == 0) { mbar_arrive(&gempty[2 * pr + 1]); mbar_arrive(&gempty[2 * pr]); }
+            }
+            if (pr == 3) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int jj = hh * 16 + j;
-              const int P = (gsum(rb[j]) << 7) + gsum(ra[j]);
-              if (pr == 3) {
-                carry[jj] = P >> 7;
-              } else if (pr == 1) {
-                carry[jj] = P;
-              } else {
-                const int sh = min(62, max(-62, dA + __shfl_sync(0xffffffffu, dBl, jj)));
+              for (int j = 0; j < 16; ++j) carry[hh * 16 + j] = ((gsum(rb[j]) << 7) + gsum(ra[j])) >> 7;
+            } else if (pr == 1) {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) carry[hh * 16 + j] = (gsum(rb[j]) << 7) + gsum(ra[j]);
+            } else {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                const int jj = hh * 16 + j;
+                const int P = (gsum(rb[j]) << 7) + gsum(ra[j]);
+                int sh;
+                if constexpr (kPacked) sh = static_cast<int>((shp[jj >> 2] >> (8 * (jj & 3))) & 0xFFu) - 64;
+                else sh = min(62, max(-62, dA + __shfl_sync(0xffffffffu, dBl, jj)));
                 // integer wrap-around is harmless: high + low = F 2^-7 fits (|F| < 2^70 - 2^18)
                 const long long t = pr == 2
                     ? (static_cast<long long>(P) << 7) + carry[jj]
@@ -538,9 +590,6 @@ gemm_ozx_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
               }
             }
           }
-          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-          __syncwarp();
-          if (lane == 0) { mbar_arrive(&gempty[2 * pr + 1]); mbar_arrive(&gempty[2 * pr]); }
         }
         ++cc;
       }
@@ -548,41 +597,44 @@ gemm_ozx_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       if (seg < nch) {
         // K range split between CTAs: integer atomics into the tile's accumulator; the CTA that
         // completes the tile's chunk count reads the sum back, clears it and updates D
-        unsigned long long* ws = p.acc_ws + static_cast<int64_t>(tile) * OX_TILE + static_cast<int64_t>(h * 32) * OZ_BM +
-                                 rloc;
+        unsigned long long* ws = p.acc_ws + static_cast<int64_t>(tile) * OX_TILE +
+                                 static_cast<int64_t>(h * C::EC) * OZ_BM + rloc;
         if (ok) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) atomicAdd(ws + j * OZ_BM, static_cast<unsigned long long>(acc[j]));
+          for (int j = 0; j < C::EC; ++j) atomicAdd(ws + j * OZ_BM, static_cast<unsigned long long>(acc[j]));
         }
         __threadfence();
-        asm volatile("bar.sync 1, %0;" ::"r"(32 * OX_EPI) : "memory");
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * C::EPI) : "memory");
         if (ew == 0 && lane == 0) {
           // a failed CTA does not count its chunks: the tile is then never stored (the call
           // reports the failure)
           const int old = *fail ? 0 : atomicAdd(p.cnt + tile, seg);
           s_last = (!*fail && old + seg == nch) ? 1 : 0;
         }
-        asm volatile("bar.sync 1, %0;" ::"r"(32 * OX_EPI) : "memory");
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * C::EPI) : "memory");
         store = s_last != 0;
         if (store) {
           __threadfence();
 #pragma unroll
-          for (int j = 0; j < 32; ++j) acc[j] = static_cast<long long>(__ldcg(ws + j * OZ_BM));
+          for (int j = 0; j < C::EC; ++j) acc[j] = static_cast<long long>(__ldcg(ws + j * OZ_BM));
 #pragma unroll
-          for (int j = 0; j < 32; ++j) __stcg(ws + j * OZ_BM, 0ull);
+          for (int j = 0; j < C::EC; ++j) __stcg(ws + j * OZ_BM, 0ull);
           if (ew == 0 && lane == 0) p.cnt[tile] = 0;
         }
       }
       if (store) {
-        // 16 columns at a time: the C reads are issued together, then rounded values stored
+        // the C reads are issued together, then the rounded values stored; mode: 0 D = v,
+        // 1 D = -v, 2 D = C - v, 3 D = C + v, 4 D = alpha v + beta C
+        const int mode = p.beta == 0.0 ? (p.alpha == 1.0 ? 0 : (p.alpha == -1.0 ? 1 : 4))
+                                       : (p.beta == 1.0 && p.alpha == -1.0 ? 2 : (p.beta == 1.0 && p.alpha == 1.0 ? 3 : 4));
 #pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
+        for (int h2 = 0; h2 < C::EC / 16; ++h2) {
           double cv[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int64_t colB = colB0 + h2 * 16 + j;
             cv[j] = 0.0;
-            if (p.beta != 0.0 && rowA < p.M && colB < p.N)
+            if (mode >= 2 && rowA < p.M && colB < p.N)
               cv[j] = p.swap ? p.D[colB + static_cast<int64_t>(rowA) * p.ldd] : p.D[rowA + colB * p.ldd];
           }
 #pragma unroll
@@ -593,9 +645,10 @@ gemm_ozx_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             if (rowA < p.M && colB < p.N) {
               const double v = fixed_to_double(acc[jj], e);
               double out;
-              if (p.beta == 0.0) out = (p.alpha == 1.0) ? v : (p.alpha == -1.0 ? -v : p.alpha * v);
-              else if (p.beta == 1.0 && p.alpha == -1.0) out = cv[j] - v;
-              else if (p.beta == 1.0 && p.alpha == 1.0) out = cv[j] + v;
+              if (mode == 0) out = v;
+              else if (mode == 1) out = -v;
+              else if (mode == 2) out = cv[j] - v;
+              else if (mode == 3) out = cv[j] + v;
               else out = fma(p.alpha, v, p.beta * cv[j]);
               if (p.swap) p.D[colB + static_cast<int64_t>(rowA) * p.ldd] = out;
               else p.D[rowA + colB * p.ldd] = out;
@@ -613,10 +666,10 @@ gemm_ozx_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       for (int x = 0; x < issued_b; ++x) if (x % OX_BST == st) last = x;
       if (last >= 0) { volatile int nofail = 0; ox_wait(&bfull[st], (last / OX_BST) & 1, &nofail); }
     }
-    for (int st = 0; st < OX_AST; ++st) {
+    for (int st = 0; st < C::AST; ++st) {
       int last = -1;
-      for (int i = 0; i < issued_a; ++i) if (i % OX_AST == st) last = i;
-      if (last >= 0) { volatile int nofail = 0; ox_wait(&afull[st], (last / OX_AST) & 1, &nofail); }
+      for (int i = 0; i < issued_a; ++i) if (i % C::AST == st) last = i;
+      if (last >= 0) { volatile int nofail = 0; ox_wait(&afull[st], (last / C::AST) & 1, &nofail); }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -843,13 +896,14 @@ struct OxLayout {
   int SAs, SBs;              // slices of the A-role and B-role operands
   int64_t RA, RB;            // A-role and B-role rows (valid)
   int64_t RApad, RBpad, Kpad;
-  int nch;
+  int nch, TN, BN;
   size_t head, sa, ea, sb, eb, total;
 };
 
 // sm (sn): slices of op(A) (op(B)).
 OxLayout ox_layout(int64_t m, int64_t n, int64_t k, int sm, int sn) {
   OxLayout L;
+  L.BN = ((k + OZ_KC - 1) / OZ_KC >= 4) ? 64 : 48;   // see OxT
   L.swap = (n <= 256 && m > n);          // the thin operand takes the 128-row side; the large one is read once
   L.RA = L.swap ? n : m;
   L.RB = L.swap ? m : n;
@@ -857,7 +911,8 @@ OxLayout ox_layout(int64_t m, int64_t n, int64_t k, int sm, int sn) {
   L.SBs = L.swap ? sm : sn;
   L.nch = static_cast<int>((k + OZ_KC - 1) / OZ_KC);
   L.RApad = rup(L.RA, OZ_BM);
-  L.RBpad = rup(L.RB, OX_BN);
+  L.TN = static_cast<int>((L.RB + L.BN - 1) / L.BN);
+  L.RBpad = rup(static_cast<int64_t>(L.TN) * L.BN, 32);   // the slicer works on 32-row blocks
   L.Kpad = static_cast<int64_t>(L.nch) * OZ_KC;
   L.head = al256(OX_HEAD);
   L.sa = al256(static_cast<size_t>(L.SAs) * L.RApad * L.Kpad * 2);
@@ -881,16 +936,17 @@ void launch_slices(cudaStream_t s, bool f32, int slices, int64_t R, int64_t K, c
   note_launch();
 }
 
-PerDeviceOnce g_ozx_attr_88, g_ozx_attr_54;
+PerDeviceOnce g_ozx_attr[4];
 
-template <int SA, int SB, int GM>
+template <int SA, int SB, int GM, int BN>
 cudaError_t launch_ozx(PerDeviceOnce& attr, unsigned grid, cudaStream_t s, const CUtensorMap& ma, const CUtensorMap& mb,
                        const OxParams& p) {
+  using C = OxT<BN>;
   cudaError_t e = per_device_once(attr, [] {
-    return cudaFuncSetAttribute(gemm_ozx_kernel<SA, SB, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize, OX_SMEM);
+    return cudaFuncSetAttribute(gemm_ozx_kernel<SA, SB, GM, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
   });
   if (e != cudaSuccess) return e;
-  gemm_ozx_kernel<SA, SB, GM><<<grid, OX_NT, OX_SMEM, s>>>(ma, mb, p);
+  gemm_ozx_kernel<SA, SB, GM, BN><<<grid, C::NT, C::SMEM, s>>>(ma, mb, p);
   note_launch();
   return cudaGetLastError();
 }
@@ -935,7 +991,7 @@ cudaError_t ozx_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int6
   e = cudaGetLastError();
   CUtensorMap ma, mb;
   if (e == cudaSuccess && (!make_slice_map(&ma, SA, L.Kpad, L.SAs * L.RApad, OZ_BM) ||
-                           !make_slice_map(&mb, SB, L.Kpad, L.SBs * L.RBpad, OX_BN)))
+                           !make_slice_map(&mb, SB, L.Kpad, L.SBs * L.RBpad, static_cast<uint32_t>(L.BN))))
     e = cudaErrorInvalidValue;
   if (e == cudaSuccess) {
     OxParams p;
@@ -947,7 +1003,7 @@ cudaError_t ozx_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int6
     p.RBpad = static_cast<int>(L.RBpad);
     p.nch = L.nch;
     p.TM = static_cast<int>(L.RApad / OZ_BM);
-    p.ntiles = p.TM * static_cast<int>(L.RBpad / OX_BN);
+    p.ntiles = p.TM * L.TN;
     p.swap = L.swap ? 1 : 0;
     p.M = L.RA;
     p.N = L.RB;
@@ -971,8 +1027,11 @@ cudaError_t ozx_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int6
       p.upc = static_cast<int>(tpc * L.nch);
     }
     grid = (W + p.upc - 1) / p.upc;
-    e = cfg88 ? launch_ozx<8, 8, 7>(g_ozx_attr_88, static_cast<unsigned>(grid), s, ma, mb, p)
-              : launch_ozx<5, 4, 5>(g_ozx_attr_54, static_cast<unsigned>(grid), s, ma, mb, p);
+    const unsigned gu = static_cast<unsigned>(grid);
+    if (cfg88) e = L.BN == 64 ? launch_ozx<8, 8, 7, 64>(g_ozx_attr[0], gu, s, ma, mb, p)
+                              : launch_ozx<8, 8, 7, 48>(g_ozx_attr[1], gu, s, ma, mb, p);
+    else e = L.BN == 64 ? launch_ozx<5, 4, 5, 64>(g_ozx_attr[2], gu, s, ma, mb, p)
+                        : launch_ozx<5, 4, 5, 48>(g_ozx_attr[3], gu, s, ma, mb, p);
   }
   // flops of the product it stands for; bytes: operands once, slices written and read
   prof_end(s, tok, 2.0 * m * n * k,
