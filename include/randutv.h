@@ -177,6 +177,9 @@ const char* randutv_last_error(void);
 #define RANDUTV_PROF_OTHER    5  /* copies, fills, norms                              */
 #define RANDUTV_PROF_GEMM32   6  /* FP32 GEMM of the mixed-precision form             */
 #define RANDUTV_PROF_GEMMTC   7  /* tensor-core (tcgen05, TF32) GEMM of the sketch    */
+#define RANDUTV_PROF_GEMMOZ   8  /* Ozaki-scheme product kernel (tcgen05, BF16 slices) */
+#define RANDUTV_PROF_GEMMOZ32 9  /* the FP32 Ozaki form (randutv_sgemm_oz)            */
+#define RANDUTV_PROF_OZSLICE 10  /* slicing of the Ozaki products' operands           */
 
 /* Turn per-kernel-class timing on (1) or off (0).  While on, each launch of a
  * class is bracketed by CUDA events on its stream and its algorithmic flops

@@ -1093,7 +1093,12 @@ int relayout(randutv_batched_plan* p) {
   p->tot_v = tot[2];
   p->tot_g = tot[3];
   if (c == 0) return RANDUTV_OK;
-  cudaError_t e = cudaMemcpy(p->d_tab, p->tab.data(), sizeof(BMat) * c, cudaMemcpyHostToDevice);
+  // a launch still running (asynchronous calls, on the graph stream or the caller's stream) reads
+  // the table: let it finish before the table changes
+  cudaError_t e = cudaSuccess;
+  if (p->ps) e = cudaStreamSynchronize(p->ps);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(current_stream());
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_tab, p->tab.data(), sizeof(BMat) * c, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->d_order, p->order.data(), sizeof(int) * c, cudaMemcpyHostToDevice);
   if (p->exec) {
     cudaGraphExecDestroy(p->exec);
@@ -1327,7 +1332,9 @@ int randutv_factor_batched(randutv_batched_plan* plan, const float* A, float* T,
     if (e == cudaSuccess) e = cudaEventRecord(plan->ev1, plan->ps);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->ev1, 0);
   } else {
-    e = rutv::bt_launch(plan, a, s);
+    // the direct launch shares the queue counters with the graph launches: after the last of them
+    e = cudaStreamWaitEvent(s, plan->ev1, 0);
+    if (e == cudaSuccess) e = rutv::bt_launch(plan, a, s);
   }
   if (e != cudaSuccess) return rutv::bt_status(e);
   if (o.async) return RANDUTV_OK;

@@ -959,9 +959,9 @@ cudaError_t ozx_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int6
                     int64_t lda, bool a32, int sm, const void* B, int64_t ldb, bool b32, int sn, double beta, double* D,
                     int64_t ldd, void* work, size_t work_bytes, int* err) {
   if (m <= 0 || n <= 0) return cudaSuccess;
-  const ProfToken tok = prof_begin(s, kProfGemmOz);
   cudaError_t e = cudaSuccess;
   if (k <= 0) {
+    const ProfToken tok = prof_begin(s, kProfOther);
     oz_scale_kernel<double><<<static_cast<unsigned>((m * n + 255) / 256), 256, 0, s>>>(m, n, beta, D, ldd);
     note_launch();
     e = cudaGetLastError();
@@ -984,11 +984,18 @@ cudaError_t ozx_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int6
   int* NB = EB + static_cast<int64_t>(L.nch) * L.RBpad;
   // op(A): rows = the m dimension, K contiguous when ta; op(B): columns = the n dimension, K contiguous when !tb
   const int64_t mpad = L.swap ? L.RBpad : L.RApad, npad = L.swap ? L.RApad : L.RBpad;
-  launch_slices(s, a32, sm, m, k, A, lda, ta, mpad, L.Kpad, L.nch, L.swap ? SB : SA, L.swap ? EB : EA,
-                L.swap ? NB : NA);
-  launch_slices(s, b32, sn, n, k, B, ldb, !tb, npad, L.Kpad, L.nch, L.swap ? SA : SB, L.swap ? EA : EB,
-                L.swap ? NA : NB);
+  {
+    // slicing: operands read once, slices, scales and norm bounds written (bytes of the launch)
+    const ProfToken ts = prof_begin(s, kProfOzSlice);
+    launch_slices(s, a32, sm, m, k, A, lda, ta, mpad, L.Kpad, L.nch, L.swap ? SB : SA, L.swap ? EB : EA,
+                  L.swap ? NB : NA);
+    launch_slices(s, b32, sn, n, k, B, ldb, !tb, npad, L.Kpad, L.nch, L.swap ? SA : SB, L.swap ? EA : EB,
+                  L.swap ? NA : NB);
+    prof_end(s, ts, 0.0, (a32 ? 4.0 : 8.0) * m * k + (b32 ? 4.0 : 8.0) * k * n + static_cast<double>(L.sa + L.sb) +
+                             static_cast<double>(L.ea + L.eb));
+  }
   e = cudaGetLastError();
+  const ProfToken tok = prof_begin(s, kProfGemmOz);
   CUtensorMap ma, mb;
   if (e == cudaSuccess && (!make_slice_map(&ma, SA, L.Kpad, L.SAs * L.RApad, OZ_BM) ||
                            !make_slice_map(&mb, SB, L.Kpad, L.SBs * L.RBpad, static_cast<uint32_t>(L.BN))))
@@ -1033,10 +1040,10 @@ cudaError_t ozx_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int6
     else e = L.BN == 64 ? launch_ozx<5, 4, 5, 64>(g_ozx_attr[2], gu, s, ma, mb, p)
                         : launch_ozx<5, 4, 5, 48>(g_ozx_attr[3], gu, s, ma, mb, p);
   }
-  // flops of the product it stands for; bytes: operands once, slices written and read
-  prof_end(s, tok, 2.0 * m * n * k,
-           (a32 ? 4.0 : 8.0) * m * k + (b32 ? 4.0 : 8.0) * k * n + 8.0 * m * n * (beta != 0.0 ? 2.0 : 1.0) +
-               2.0 * static_cast<double>(L.sa + L.sb));
+  // flops: the BF16 slice-pair products (2 m n k each); bytes: the slices read once, D written (and read)
+  const double pairs = cfg88 ? 36.0 : 17.0;
+  prof_end(s, tok, pairs * 2.0 * m * n * k,
+           static_cast<double>(L.sa + L.sb) + 8.0 * m * n * (beta != 0.0 ? 2.0 : 1.0));
   return e;
 }
 

@@ -349,13 +349,12 @@ bool gemm_tc_supported(const float* A, int64_t lda, const float* B, int64_t ldb,
 template <bool SPLIT, bool AMN, bool BMN>
 cudaError_t launch_tc(dim3 grid, cudaStream_t s, const CUtensorMap& ma, const CUtensorMap& mb, int64_t m, int64_t n,
                       int64_t k, float alpha, float beta, float* D, int64_t ldd, float* part, int64_t kc, int* err) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<SPLIT, AMN, BMN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         TcCfg<SPLIT>::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static PerDeviceOnce once;
+  cudaError_t e = per_device_once(once, [] {
+    return cudaFuncSetAttribute(gemm_tc_kernel<SPLIT, AMN, BMN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TcCfg<SPLIT>::SMEM);
+  });
+  if (e != cudaSuccess) return e;
   gemm_tc_kernel<SPLIT, AMN, BMN><<<grid, TcCfg<SPLIT>::NT, TcCfg<SPLIT>::SMEM, s>>>(ma, mb, m, n, k, alpha, beta, D,
                                                                                     ldd, part, kc, err);
   return cudaGetLastError();

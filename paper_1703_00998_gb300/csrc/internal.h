@@ -41,7 +41,7 @@ constexpr int kFlagSlots = 8;
 // ---- prof.cu ----
 enum ProfClass { kProfGemm = 0, kProfPanel = 1, kProfTfactor = 2, kProfJacobi = 3, kProfGauss = 4,
                  kProfOther = 5, kProfGemm32 = 6, kProfGemmTc = 7, kProfGemmOz = 8, kProfGemmOz32 = 9,
-                 kProfClasses = 10 };
+                 kProfOzSlice = 10, kProfClasses = 11 };
 struct ProfTotals { double ms = 0.0; int64_t launches = 0; double flops = 0.0; double bytes = 0.0; };
 struct ProfToken { int idx; };
 void note_launch(int n = 1);

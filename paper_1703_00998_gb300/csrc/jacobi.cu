@@ -576,12 +576,9 @@ template <int NU>
 cudaError_t launch64(cudaStream_t s, int csize, int p, const double* M, int64_t ldm, const double* W0,
                      const double* Q0, double* Us, double* d, double* Vs, int max_sweeps, double tol, int* err,
                      int* zflag) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = prepare(jacobi_block64_kernel<NU>, csize, kJcSmemLimit);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static PerDeviceOnce once;
+  cudaError_t e = per_device_once(once, [&] { return prepare(jacobi_block64_kernel<NU>, csize, kJcSmemLimit); });
+  if (e != cudaSuccess) return e;
   const size_t smem = jb_smem(p, csize, sizeof(double));
   if (smem > kJcSmemLimit) return cudaErrorInvalidConfiguration;   // p > 240 needs the 16-CTA cluster
   cudaLaunchAttribute at[1];
@@ -592,12 +589,9 @@ cudaError_t launch64(cudaStream_t s, int csize, int p, const double* M, int64_t 
 
 template <int NU>
 cudaError_t launch32(cudaStream_t s, int csize, int p, const double* M, int64_t ldm, double* Qg, int sweeps) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = prepare(jacobi_block32_kernel<NU>, csize, kJcSmemLimit);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static PerDeviceOnce once;
+  cudaError_t e = per_device_once(once, [&] { return prepare(jacobi_block32_kernel<NU>, csize, kJcSmemLimit); });
+  if (e != cudaSuccess) return e;
   const size_t smem = jb_smem(p, csize, sizeof(float));
   if (smem > kJcSmemLimit) return cudaErrorInvalidConfiguration;
   cudaLaunchAttribute at[1];
@@ -621,10 +615,18 @@ cudaError_t run32(cudaStream_t s, int csize, int p, const double* M, int64_t ldm
 }
 
 // Largest cluster size (16 with the non-portable opt-in, else 8) that can be scheduled.
+// Cached per device (the query depends on the device's limits).
 int cluster_size() {
-  static int csize = 0;
-  if (csize) return csize;
-  csize = 8;
+  static std::mutex mu;
+  static int cached[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    dev = -1;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev >= 0 && cached[dev]) return cached[dev];
+  int csize = 8;
   if (prepare(jacobi_block64_kernel<8>, JC_CLUSTER, kJcSmemLimit) == cudaSuccess) {
     cudaLaunchAttribute qa[1];
     cudaLaunchConfig_t q = cluster_cfg(nullptr, JC_CLUSTER, jb_smem(JC_MAXP, JC_CLUSTER, sizeof(double)), qa);
@@ -633,6 +635,7 @@ int cluster_size() {
       csize = JC_CLUSTER;
   }
   cudaGetLastError();
+  if (dev >= 0) cached[dev] = csize;
   return csize;
 }
 

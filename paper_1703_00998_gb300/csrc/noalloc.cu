@@ -18,6 +18,7 @@
 // race on it; serialise them.  The first call on each device looks up the
 // device address of the array (cudaGetSymbolAddress, with that device
 // current) and caches it; make that first call before any stream capture.
+#include <cstdio>
 #include <mutex>
 #include "common.cuh"
 #include "internal.h"
@@ -71,9 +72,12 @@ extern "C" int randutv_small_svd_noalloc(int64_t p, const double* M, int64_t ldm
   }
   const int pi = static_cast<int>(p);
   double* base = nullptr;
+  char msg[192];
   cudaError_t e = scratch_address(&base);
   if (e != cudaSuccess) {
-    set_last_error("randutv_small_svd_noalloc: cudaGetSymbolAddress of the scratch array failed");
+    snprintf(msg, sizeof(msg), "randutv_small_svd_noalloc: cudaGetSymbolAddress of the scratch array: %s",
+             cudaGetErrorString(e));
+    set_last_error(msg);
     return RANDUTV_ECUDA;
   }
   cudaStream_t s = current_stream();
@@ -86,7 +90,10 @@ extern "C" int randutv_small_svd_noalloc(int64_t p, const double* M, int64_t ldm
   if (e == cudaSuccess) e = cudaMemcpyAsync(herr, flags, sizeof(herr), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
-    set_last_error("randutv_small_svd_noalloc: a CUDA call failed");
+    // no work this call queued may still be writing the shared scratch once it returns
+    cudaStreamSynchronize(s);
+    snprintf(msg, sizeof(msg), "randutv_small_svd_noalloc: %s", cudaGetErrorString(e));
+    set_last_error(msg);
     return RANDUTV_ECUDA;
   }
   if (herr[2] & kDevErrTimeout) return RANDUTV_ETIMEOUT;

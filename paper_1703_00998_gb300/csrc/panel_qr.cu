@@ -172,14 +172,13 @@ cudaError_t panel_qr(cudaStream_t s, int64_t k, int w, double* P, int64_t ldp, d
   if (k < w || w < 1) return cudaErrorInvalidValue;
   PqGeom g = pq_geometry(k, w);
   if (g.nb > kMaxCoopBlocks) return cudaErrorInvalidConfiguration;  // panel too tall for this layout
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(kPqSmemBudget));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+  static PerDeviceOnce once;
+  cudaError_t e = per_device_once(once, [] {
+    return cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kPqSmemBudget));
+  });
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(part, 0, static_cast<size_t>(w) * w * sizeof(double), s);
   if (e != cudaSuccess) return e;
   GridBarrier gb{bar, bar + 1, reinterpret_cast<int*>(bar + 2)};
@@ -222,14 +221,17 @@ tfactor_kernel(int w, const double* __restrict__ gram, const double* __restrict_
 }
 
 cudaError_t tfactor_from_gram(cudaStream_t s, int w, const double* gram, const double* tau, double* S) {
+  if (w < 1 || w > 256) return cudaErrorInvalidValue;
   const int blocks = (w + TF_WARPS - 1) / TF_WARPS;
   const size_t smem = static_cast<size_t>(TF_WARPS) * w * sizeof(double);
-  static int attr_w = 0;
-  if (smem > 48 * 1024 && w > attr_w) {
-    cudaError_t e = cudaFuncSetAttribute(tfactor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+  // the largest block (w = 256) bounds every launch: one attribute per device
+  static PerDeviceOnce once;
+  if (smem > 48 * 1024) {
+    cudaError_t e = per_device_once(once, [] {
+      return cudaFuncSetAttribute(tfactor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(static_cast<size_t>(TF_WARPS) * 256 * sizeof(double)));
+    });
     if (e != cudaSuccess) return e;
-    attr_w = w;
   }
   const ProfToken tok = prof_begin(s, kProfTfactor);
   tfactor_kernel<<<blocks, TF_WARPS * 32, smem, s>>>(w, gram, tau, S);

@@ -105,7 +105,7 @@ SIGNATURES = {
 
 PROF_GEMM, PROF_PANEL, PROF_TFACTOR, PROF_JACOBI, PROF_GAUSS, PROF_OTHER, PROF_GEMM32, PROF_GEMMTC = range(8)
 PROF_NAMES = ["gemm", "panel_qr", "tfactor", "jacobi", "gauss", "other", "gemm32", "gemm_tc", "gemm_oz",
-              "gemm_oz32"]
+              "gemm_oz32", "oz_slice"]
 
 
 def profile_read(cls):
