@@ -100,6 +100,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="also time the oracle to completion at n=4000 (median of 3, all cores) and on one core")
     ap.add_argument("--no-verify", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
@@ -425,6 +427,31 @@ def cpu_sample(A, b, q, seconds):
             "sample": f"first {s} of {-(-n // b)} steps of the same n={n} factorization (U, V formed), "
                       f"{dt:.1f} s; numpy/OpenBLAS with its default thread count",
             "seconds": dt, "steps": s}
+
+
+def cpu_full(n=4000, b=128, q=1, reps=3):
+    """The oracle as it stands, timed to completion at n (U and V formed): median of `reps` runs
+    with numpy/OpenBLAS's default threads, and one run on a single core (a child process with
+    the BLAS thread count set to 1 before numpy loads)."""
+    import statistics
+    import subprocess
+    import sys
+    code = ("import sys, time; sys.path.insert(0, %r); import numpy, oracle, synth; "
+            "A = synth.make_matrix('exp200', %d, %d, 1703002); "
+            "g = lambda i, k, bb: synth.step_gaussian(998, i, k, bb); "
+            "ts = []\nfor _ in range(%%d):\n    t0 = time.perf_counter(); oracle.randutv(A, %d, %d, g); "
+            "ts.append(time.perf_counter() - t0)\nprint(' '.join(map(str, ts)))") % (ROOT, n, n, b, q)
+    env1 = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    multi = [float(x) for x in subprocess.run([sys.executable, "-c", code % reps], capture_output=True, text=True,
+                                               check=True).stdout.split()]
+    single = [float(x) for x in subprocess.run([sys.executable, "-c", code % 1], capture_output=True, text=True,
+                                                check=True, env=env1).stdout.split()]
+    fl = total_flops(n, q)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    med = statistics.median(multi)
+    return {"workload": f"oracle randUTV n={n} b={b} q={q} sigma_j=exp(-j/200), U and V formed, to completion",
+            "all_cores": {"seconds_median": med, "runs": multi, "tflops": fl / med / 1e12, "cores": cores},
+            "single_core": {"seconds": single[0], "tflops": fl / single[0] / 1e12, "cores": 1}}
 
 
 def run_reference(args):
@@ -841,6 +868,8 @@ def run_own(args):
         line["adjoint"] = run_adjoint(args, stream)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_sample(A.cpu().numpy(), b, q, args.cpu_seconds)
+    if rank == 0 and args.cpu_full:
+        line["cpu_full"] = cpu_full()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
