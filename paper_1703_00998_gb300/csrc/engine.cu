@@ -144,9 +144,13 @@ struct G64 {
   double* gws;
   int64_t ge;
   cudaError_t run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
-                  int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc) const {
-    if (oz && m >= 64 && n >= 32 && k >= 32 && gemm_oz_work_bytes(m, n, k) <= owb)
+                  int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                  OzKeep* keep = nullptr) const {
+    if (oz && m >= 64 && n >= 32 && k >= 32 && gemm_oz_work_bytes(m, n, k) <= owb) {
+      if (keep && keep->base && gemm_oz_keep_bytes(m, n, k, false) <= keep->bytes)
+        return gemm_oz_keep(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ow, owb, err, keep);
       return gemm_oz(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ow, owb, err);
+    }
     return gemm_f64(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, gws, ge);
   }
 };
@@ -210,6 +214,8 @@ struct Work {
   size_t bytes;
   void *ozT, *ozU, *ozS;   // Ozaki GEMM workspaces of the T, U/V and SVD lanes (or null)
   size_t ozb, ozbS;
+  void* ozX;               // the slices of X^T, shared by a step's products X^T G and X^T Z (or null)
+  size_t ozXb;
 };
 
 // Largest Ozaki workspace any product of the factorization needs: the
@@ -378,9 +384,11 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
       w.ozb = oz_budget(m, n, b + pov);
       const int64_t mx = std::max(m, n);
       w.ozbS = std::max(gemm_oz_work_bytes(b, mx, b), gemm_oz_work_bytes(mx, b, b));   // the rotations
+      w.ozXb = gemm_oz_keep_bytes(mx, b + pov, mx, false);   // X^T (n_k x m_k) of the first step bounds all
       e = cudaMallocAsync(&w.ozT, w.ozb, s);
       if (e == cudaSuccess && uv) e = cudaMallocAsync(&w.ozU, w.ozb, s);
       if (e == cudaSuccess) e = cudaMallocAsync(&w.ozS, w.ozbS, s);
+      if (e == cudaSuccess && q > 0) e = cudaMallocAsync(&w.ozX, w.ozXb, s);
       for (void* oz : {w.ozT, w.ozU, w.ozS})
         if (e == cudaSuccess && oz) e = cudaMemsetAsync(oz, 0, gemm_oz_head_bytes(), s);
     }
@@ -390,6 +398,7 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
       if (w.ozT) cudaFreeAsync(w.ozT, s);
       if (w.ozU) cudaFreeAsync(w.ozU, s);
       if (w.ozS) cudaFreeAsync(w.ozS, s);
+      if (w.ozX) cudaFreeAsync(w.ozX, s);
       if (w.base) cudaFreeAsync(w.base, s);
       cudaStreamSynchronize(s);
       return e == cudaErrorMemoryAllocation ? RANDUTV_ENOMEM : RANDUTV_ECUDA;
@@ -455,10 +464,12 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
           RUTV_CK(cudaMemcpyAsync(opts.g_capture + g_off, G, kr * (b + pov) * sizeof(double),
                                   cudaMemcpyDeviceToDevice, sT));
         g_off += kr * (b + pov);
-        RUTV_CK(gT.run(sT, true, false, kc, wv, kr, 1.0, X, ldt, G, kr, 0.0, w.Y, kc));
+        // X^T is sliced once for X^T G and every X^T Z of the step (X does not change in between)
+        OzKeep kx{w.ozX, w.ozXb, false};
+        RUTV_CK(gT.run(sT, true, false, kc, wv, kr, 1.0, X, ldt, G, kr, 0.0, w.Y, kc, &kx));
         for (int j = 0; j < q; ++j) {
           RUTV_CK(gT.run(sT, false, false, kr, wv, kc, 1.0, X, ldt, w.Y, kc, 0.0, w.Z, kr));
-          RUTV_CK(gT.run(sT, true, false, kc, wv, kr, 1.0, X, ldt, w.Z, kr, 0.0, w.Y, kc));
+          RUTV_CK(gT.run(sT, true, false, kc, wv, kr, 1.0, X, ldt, w.Z, kr, 0.0, w.Y, kc, &kx));
         }
         double* Ysk = w.Y;   // the n_k x b matrix whose Householder QR gives VV
         if (pov > 0) {
@@ -575,6 +586,7 @@ done:
   if (w.ozT) cudaFreeAsync(w.ozT, s);
   if (w.ozU) cudaFreeAsync(w.ozU, s);
   if (w.ozS) cudaFreeAsync(w.ozS, s);
+  if (w.ozX) cudaFreeAsync(w.ozX, s);
   if (w.base) {
     cudaFreeAsync(w.base, s);
     cudaStreamSynchronize(s);

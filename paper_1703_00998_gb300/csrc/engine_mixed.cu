@@ -148,6 +148,8 @@ struct MWork {
       *red, *scal;
   void* oz = nullptr;   // workspace of the sliced sketch products (gemm_oz_sketch), or null
   size_t ozb = 0;
+  void* ozX = nullptr;  // the slices of X^T, shared by a step's X^T G and X^T Z (or null)
+  size_t ozXb = 0;
   int64_t gws_elems, gws64_elems;
   unsigned* flags;
   void* base;
@@ -345,10 +347,13 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
       }
       const int64_t mx = std::max(m, n);
       w.ozb = gemm_oz_sketch_work_bytes(mx, b, mx);   // bounds every sketch product of the factorization
+      w.ozXb = gemm_oz_keep_bytes(mx, b, mx, true);
       e = cudaMallocAsync(&w.oz, w.ozb, s);
       if (e == cudaSuccess) e = cudaMemsetAsync(w.oz, 0, gemm_oz_head_bytes(), s);
+      if (e == cudaSuccess && q > 0) e = cudaMallocAsync(&w.ozX, w.ozXb, s);
     }
     if (e != cudaSuccess) {
+      if (w.ozX) cudaFreeAsync(w.ozX, s);
       if (w.oz) cudaFreeAsync(w.oz, s);
       if (w.base) cudaFreeAsync(w.base, s);
       cudaStreamSynchronize(s);
@@ -417,10 +422,14 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
           // sliced sketch: the FP32 trailing block exactly, G / Y / Z to 35 bits, FP64 results
           const double* G64 = opts.g_inject ? opts.g_inject + g_off : w.G64;
           int* oz_err = reinterpret_cast<int*>(slot_of(w.flags, 3) + 2);
-          RUTV_MCK(gemm_oz_sketch(sT, true, false, kc, b, kr, X, ldt, G64, kr, w.Y64, kc, w.oz, w.ozb, oz_err));
+          // X^T is sliced once for X^T G and every X^T Z of the step (X does not change in between)
+          OzKeep kx{w.ozX, w.ozXb, false};
+          OzKeep* kxp = w.ozX ? &kx : nullptr;
+          RUTV_MCK(gemm_oz_sketch(sT, true, false, kc, b, kr, X, ldt, G64, kr, w.Y64, kc, w.oz, w.ozb, oz_err, kxp));
           for (int j = 0; j < q; ++j) {
             RUTV_MCK(gemm_oz_sketch(sT, false, false, kr, b, kc, X, ldt, w.Y64, kc, w.Z64, kr, w.oz, w.ozb, oz_err));
-            RUTV_MCK(gemm_oz_sketch(sT, true, false, kc, b, kr, X, ldt, w.Z64, kr, w.Y64, kc, w.oz, w.ozb, oz_err));
+            RUTV_MCK(gemm_oz_sketch(sT, true, false, kc, b, kr, X, ldt, w.Z64, kr, w.Y64, kc, w.oz, w.ozb, oz_err,
+                                    kxp));
           }
         } else {
           RUTV_MCK(gT.run(sT, kSketch, true, false, kc, b, kr, 1.f, X, ldt, w.G, kr, 0.f, w.Y, kc));
@@ -530,6 +539,7 @@ extern "C" int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_
 done:
   L.join(s);
   if (w.oz) cudaFreeAsync(w.oz, s);
+  if (w.ozX) cudaFreeAsync(w.ozX, s);
   if (w.base) {
     cudaFreeAsync(w.base, s);
     cudaStreamSynchronize(s);

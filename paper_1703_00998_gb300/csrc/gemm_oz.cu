@@ -112,65 +112,79 @@ template <> struct FBits<float> {
   __device__ static long long bits(float x) { return static_cast<long long>(__float_as_int(x)); }
 };
 
-// Slices of an R x K operand X (element (r, k) at X[r + k ldx], or at
-// X[k + r ldx] when kcontig), per K chunk: S[(j Rpad + r) Kpad + k] (BF16,
-// K contiguous) and e[c Rpad + r].  Rows r >= R and columns k >= K are zero.
-// One CTA of 128 threads per 32 rows x one chunk, staged through shared
-// memory so that both the reads and the BF16 writes are coalesced.
+// Column of the staging tile that holds k of a chunk: the low two bits of k
+// rotated by k / 16, so that the 32 lanes of a warp reading k = 4 lane + q
+// (q fixed) of one row hit 16 different 8-byte banks per 16 lanes.
+__device__ __forceinline__ int oz_swz(int kk) { return (kk & ~3) | (((kk & 3) + (kk >> 4)) & 3); }
+
+// Slices of an R x K operand X (element (r, k) at X[k + r ldx] when KC, the K
+// index contiguous, else at X[r + k ldx]), per K chunk: S[(j Rpad + r) Kpad +
+// k] (BF16, K contiguous) and e[c Rpad + r].  Rows r >= R and columns k >= K
+// are zero.  One CTA of 256 threads per 32 rows x one chunk; a warp owns a
+// row at a time and each lane 4 consecutive k of it, so the slices are
+// written 8 bytes per lane.  With K strided (column-major X) the chunk is
+// first staged through shared memory so that the reads are coalesced.
 // Integer arithmetic only (FP64 is the slow pipe here): the scale e is the
 // largest biased exponent of the row's chunk minus the bias (so |x| < 2^e),
 // and the slices are the 7-bit groups of the W-bit fixed-point magnitude
-// trunc(|x| 2^(W - e)), each with the sign of x.
-// With NS non-null it also writes NS[c Rpad + r] = sum_k (|s_0| + 1)^2 over
-// the chunk's entries (0 for an all-zero chunk): the chunk's squared
-// 2-norm is below NS 2^(2e - 14), since |x| < (|s_0| + 1) 2^(e - 7).
-template <int S, typename T>
-__global__ void __launch_bounds__(128)
-oz_slice_kernel(int64_t R, int64_t K, const T* __restrict__ X, int64_t ldx, bool kcontig, int64_t Rpad,
-                int64_t Kpad, __nv_bfloat16* __restrict__ Sl, int* __restrict__ E, int* __restrict__ NS) {
+// trunc(|x| 2^(W - e)), each with the sign of x.  With NS non-null it also
+// writes NS[c Rpad + r] = sum_k (|s_0| + 1)^2 over the chunk's entries (0 for
+// an all-zero chunk): the chunk's squared 2-norm is below NS 2^(2e - 14),
+// since |x| < (|s_0| + 1) 2^(e - 7).
+template <int S, typename T, bool KC>
+__global__ void __launch_bounds__(256)
+oz_slice_kernel(int64_t R, int64_t K, const T* __restrict__ X, int64_t ldx, int64_t Rpad, int64_t Kpad,
+                __nv_bfloat16* __restrict__ Sl, int* __restrict__ E, int* __restrict__ NS) {
   using F = FBits<T>;
   constexpr int W = 7 * S;
-  __shared__ long long tile[32][OZ_KC + 1];
-  __shared__ int s_e[32];
+  constexpr long long EMASK = (1ll << F::EB) - 1;
+  __shared__ long long tile[KC ? 1 : 32][KC ? 1 : OZ_KC + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 32;
   const int64_t k0 = static_cast<int64_t>(blockIdx.y) * OZ_KC;
-  for (int idx = tid; idx < 32 * OZ_KC; idx += 128) {
-    int i, kk;
-    if (kcontig) { kk = idx % OZ_KC; i = idx / OZ_KC; }
-    else { i = idx % 32; kk = idx / 32; }
-    const int64_t r = r0 + i, k = k0 + kk;
-    T v = T(0);
-    if (r < R && k < K) v = kcontig ? X[k + r * ldx] : X[r + k * ldx];
-    tile[i][kk] = F::bits(v);
+  if constexpr (!KC) {
+    for (int idx = tid; idx < 32 * OZ_KC; idx += 256) {
+      const int i = idx % 32, kk = idx / 32;
+      const int64_t r = r0 + i, k = k0 + kk;
+      T v = T(0);
+      if (r < R && k < K) v = X[r + k * ldx];
+      tile[i][oz_swz(kk)] = F::bits(v);
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  constexpr long long EMASK = (1ll << F::EB) - 1;
-  for (int i = warp; i < 32; i += 4) {
-    int be = 0;   // largest biased exponent of the row's chunk
-    for (int kk = lane; kk < OZ_KC; kk += 32) be = max(be, static_cast<int>((tile[i][kk] >> F::MB) & EMASK));
-    be = __reduce_max_sync(0xffffffffu, be);
-    if (lane == 0) s_e[i] = (be == 0) ? kOzZeroScale : be - F::EBIAS;
-  }
-  __syncthreads();
-  // a zero (or subnormal-only) chunk reports the scale kOzZeroScale, so that it never sets a row's
-  // largest scale; its slices are zero
-  if (tid < 32 && r0 + tid < Rpad) E[static_cast<int64_t>(blockIdx.y) * Rpad + r0 + tid] = s_e[tid];
-  // each warp writes 8 rows; a lane owns 4 consecutive k of a row
-  for (int i = warp; i < 32; i += 4) {
+  for (int i = warp; i < 32; i += 8) {
     const int64_t r = r0 + i;
     if (r >= Rpad) continue;
-    const int e = s_e[i] == kOzZeroScale ? 0 : s_e[i];
+    long long b[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int kk = lane * 4 + q;
+      if constexpr (KC) {
+        T v = T(0);
+        if (r < R && k0 + kk < K) v = X[k0 + kk + r * ldx];
+        b[q] = F::bits(v);
+      } else {
+        b[q] = tile[i][oz_swz(kk)];
+      }
+    }
+    int be = 0;   // largest biased exponent of the row's chunk
+#pragma unroll
+    for (int q = 0; q < 4; ++q) be = max(be, static_cast<int>((b[q] >> F::MB) & EMASK));
+    be = __reduce_max_sync(0xffffffffu, be);
+    // a zero (or subnormal-only) chunk reports the scale kOzZeroScale, so that it never sets a
+    // row's largest scale; its slices are zero
+    const bool zero = (be == 0);
+    if (lane == 0) E[static_cast<int64_t>(blockIdx.y) * Rpad + r] = zero ? kOzZeroScale : be - F::EBIAS;
+    const int e = zero ? 0 : be - F::EBIAS;
     int nsq = 0;
     unsigned long long mag[4];
     bool neg[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const long long b = tile[i][lane * 4 + q];
-      const int bexp = static_cast<int>((b >> F::MB) & EMASK);
-      neg[q] = (b >> (F::MB + F::EB)) & 1;
+      const int bexp = static_cast<int>((b[q] >> F::MB) & EMASK);
+      neg[q] = (b[q] >> (F::MB + F::EB)) & 1;
       const unsigned long long mant =
-          (static_cast<unsigned long long>(b) & ((1ull << F::MB) - 1)) | (bexp ? (1ull << F::MB) : 0ull);
+          (static_cast<unsigned long long>(b[q]) & ((1ull << F::MB) - 1)) | (bexp ? (1ull << F::MB) : 0ull);
       // |x| = mant 2^(max(bexp,1) - BM); magnitude in units of 2^(e - W)
       const int sh = max(bexp, 1) - (F::BM - W) - e;   // <= 3 (FP64) / 4 (FP32) because |x| < 2^e
       mag[q] = (sh >= 0) ? (mant << sh) : (sh > -64 ? (mant >> (-sh)) : 0ull);
@@ -193,9 +207,18 @@ oz_slice_kernel(int64_t R, int64_t K, const T* __restrict__ X, int64_t ldx, bool
     }
     if (NS) {
       nsq = __reduce_add_sync(0xffffffffu, nsq);
-      if (lane == 0) NS[static_cast<int64_t>(blockIdx.y) * Rpad + r] = (s_e[i] == kOzZeroScale) ? 0 : nsq;
+      if (lane == 0) NS[static_cast<int64_t>(blockIdx.y) * Rpad + r] = zero ? 0 : nsq;
     }
   }
+}
+
+// One slicing launch (S slices of T data; K contiguous or not).
+template <int S, typename T>
+void slice_launch(cudaStream_t s, int64_t R, int64_t K, const T* X, int64_t ldx, bool kcontig, int64_t Rpad,
+                  int64_t Kpad, int nch, __nv_bfloat16* Sl, int* E, int* NS) {
+  const dim3 g(static_cast<unsigned>(Rpad / 32), static_cast<unsigned>(nch));
+  if (kcontig) oz_slice_kernel<S, T, true><<<g, 256, 0, s>>>(R, K, X, ldx, Rpad, Kpad, Sl, E, NS);
+  else oz_slice_kernel<S, T, false><<<g, 256, 0, s>>>(R, K, X, ldx, Rpad, Kpad, Sl, E, NS);
 }
 
 // ============================================================ FP64 form
@@ -926,13 +949,12 @@ OxLayout ox_layout(int64_t m, int64_t n, int64_t k, int sm, int sn) {
 // Slices of an operand: FP64 (f32 = false) or FP32 data, `slices` of them.
 void launch_slices(cudaStream_t s, bool f32, int slices, int64_t R, int64_t K, const void* X, int64_t ldx,
                    bool kcontig, int64_t Rpad, int64_t Kpad, int nch, __nv_bfloat16* Sl, int* E, int* NS) {
-  const dim3 g(static_cast<unsigned>(Rpad / 32), static_cast<unsigned>(nch));
   if (!f32 && slices == 8)
-    oz_slice_kernel<8, double><<<g, 128, 0, s>>>(R, K, static_cast<const double*>(X), ldx, kcontig, Rpad, Kpad, Sl, E, NS);
+    slice_launch<8, double>(s, R, K, static_cast<const double*>(X), ldx, kcontig, Rpad, Kpad, nch, Sl, E, NS);
   else if (!f32 && slices == 5)
-    oz_slice_kernel<5, double><<<g, 128, 0, s>>>(R, K, static_cast<const double*>(X), ldx, kcontig, Rpad, Kpad, Sl, E, NS);
+    slice_launch<5, double>(s, R, K, static_cast<const double*>(X), ldx, kcontig, Rpad, Kpad, nch, Sl, E, NS);
   else
-    oz_slice_kernel<4, float><<<g, 128, 0, s>>>(R, K, static_cast<const float*>(X), ldx, kcontig, Rpad, Kpad, Sl, E, NS);
+    slice_launch<4, float>(s, R, K, static_cast<const float*>(X), ldx, kcontig, Rpad, Kpad, nch, Sl, E, NS);
   note_launch();
 }
 
@@ -955,9 +977,13 @@ cudaError_t launch_ozx(PerDeviceOnce& attr, unsigned grid, cudaStream_t s, const
 // holds FP32 data when a32 (b32), split into sm (sn) slices; the pairs
 // (slices, last group) supported are (8, 8 -> group 7), the FP64 products,
 // and (4 FP32, 5 FP64 -> group 5), the sketch of the mixed form.
+// keep (optional): a region that holds op(A)'s slices, scales and norm bounds
+// instead of the workspace; with keep->ready they are taken as they are (the
+// caller vouches that op(A) is unchanged since they were formed), otherwise
+// they are formed there and keep->ready is set.
 cudaError_t ozx_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const void* A,
                     int64_t lda, bool a32, int sm, const void* B, int64_t ldb, bool b32, int sn, double beta, double* D,
-                    int64_t ldd, void* work, size_t work_bytes, int* err) {
+                    int64_t ldd, void* work, size_t work_bytes, int* err, OzKeep* keep = nullptr) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   cudaError_t e = cudaSuccess;
   if (k <= 0) {
@@ -980,19 +1006,36 @@ cudaError_t ozx_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int6
   int* EA = reinterpret_cast<int*>(w + L.head + L.sa);
   auto* SB = reinterpret_cast<__nv_bfloat16*>(w + L.head + L.sa + L.ea);
   int* EB = reinterpret_cast<int*>(w + L.head + L.sa + L.ea + L.sb);
+  if (keep) {
+    // op(A)'s arrays in the caller's region, laid out as in the workspace
+    const size_t need = L.swap ? L.sb + L.eb : L.sa + L.ea;
+    if (!keep->base || keep->bytes < need) return cudaErrorInvalidValue;
+    char* kb = static_cast<char*>(keep->base);
+    if (L.swap) {
+      SB = reinterpret_cast<__nv_bfloat16*>(kb);
+      EB = reinterpret_cast<int*>(kb + L.sb);
+    } else {
+      SA = reinterpret_cast<__nv_bfloat16*>(kb);
+      EA = reinterpret_cast<int*>(kb + L.sa);
+    }
+  }
   int* NA = EA + static_cast<int64_t>(L.nch) * L.RApad;
   int* NB = EB + static_cast<int64_t>(L.nch) * L.RBpad;
   // op(A): rows = the m dimension, K contiguous when ta; op(B): columns = the n dimension, K contiguous when !tb
   const int64_t mpad = L.swap ? L.RBpad : L.RApad, npad = L.swap ? L.RApad : L.RBpad;
   {
-    // slicing: operands read once, slices, scales and norm bounds written (bytes of the launch)
+    // slicing: operands read once, slices, scales and norm bounds written (bytes of the launches)
+    const bool slice_a = !(keep && keep->ready);
     const ProfToken ts = prof_begin(s, kProfOzSlice);
-    launch_slices(s, a32, sm, m, k, A, lda, ta, mpad, L.Kpad, L.nch, L.swap ? SB : SA, L.swap ? EB : EA,
-                  L.swap ? NB : NA);
+    if (slice_a)
+      launch_slices(s, a32, sm, m, k, A, lda, ta, mpad, L.Kpad, L.nch, L.swap ? SB : SA, L.swap ? EB : EA,
+                    L.swap ? NB : NA);
     launch_slices(s, b32, sn, n, k, B, ldb, !tb, npad, L.Kpad, L.nch, L.swap ? SA : SB, L.swap ? EA : EB,
                   L.swap ? NA : NB);
-    prof_end(s, ts, 0.0, (a32 ? 4.0 : 8.0) * m * k + (b32 ? 4.0 : 8.0) * k * n + static_cast<double>(L.sa + L.sb) +
-                             static_cast<double>(L.ea + L.eb));
+    const double a_bytes = (a32 ? 4.0 : 8.0) * m * k + static_cast<double>(L.swap ? L.sb + L.eb : L.sa + L.ea);
+    const double b_bytes = (b32 ? 4.0 : 8.0) * k * n + static_cast<double>(L.swap ? L.sa + L.ea : L.sb + L.eb);
+    prof_end(s, ts, 0.0, (slice_a ? a_bytes : 0.0) + b_bytes);
+    if (keep) keep->ready = true;
   }
   e = cudaGetLastError();
   const ProfToken tok = prof_begin(s, kProfGemmOz);
@@ -1095,10 +1138,8 @@ cudaError_t oz32_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int
   auto* SB = reinterpret_cast<__nv_bfloat16*>(w + L.sa + L.ea);
   int* EB = reinterpret_cast<int*>(w + L.sa + L.ea + L.sb);
   float* part = L.nch > 1 ? reinterpret_cast<float*>(w + L.sa + L.ea + L.sb + L.eb) : nullptr;
-  oz_slice_kernel<C::S, float><<<dim3(static_cast<unsigned>(L.MApad / 32), static_cast<unsigned>(L.nch)), 128, 0, s>>>(
-      m, k, A, lda, ta, L.MApad, L.Kpad, SA, EA, nullptr);
-  oz_slice_kernel<C::S, float><<<dim3(static_cast<unsigned>(L.NBpad / 32), static_cast<unsigned>(L.nch)), 128, 0, s>>>(
-      n, k, B, ldb, !tb, L.NBpad, L.Kpad, SB, EB, nullptr);
+  slice_launch<C::S, float>(s, m, k, A, lda, ta, L.MApad, L.Kpad, L.nch, SA, EA, nullptr);
+  slice_launch<C::S, float>(s, n, k, B, ldb, !tb, L.NBpad, L.Kpad, L.nch, SB, EB, nullptr);
   note_launch(2);
   e = cudaGetLastError();
   CUtensorMap ma, mb;
@@ -1140,6 +1181,19 @@ size_t gemm_oz_sketch_work_bytes(int64_t m, int64_t n, int64_t k) {
   return ox_layout(m, n, k, 4, 5).total;
 }
 
+size_t gemm_oz_keep_bytes(int64_t m, int64_t n, int64_t k, bool sketch) {
+  if (m <= 0 || n <= 0 || k <= 0) return 0;
+  const OxLayout L = ox_layout(m, n, k, sketch ? 4 : 8, sketch ? 5 : 8);
+  return L.swap ? L.sb + L.eb : L.sa + L.ea;
+}
+
+cudaError_t gemm_oz_keep(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
+                         const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* D,
+                         int64_t ldd, void* work, size_t work_bytes, int* err, OzKeep* keep) {
+  return ozx_run(s, ta, tb, m, n, k, alpha, A, lda, false, 8, B, ldb, false, 8, beta, D, ldd, work, work_bytes, err,
+                 keep);
+}
+
 size_t gemm_oz_head_bytes() { return al256(OX_HEAD); }
 
 size_t gemm_oz32_work_bytes(int64_t m, int64_t n, int64_t k) {
@@ -1157,8 +1211,9 @@ cudaError_t gemm_oz(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int6
 
 cudaError_t gemm_oz_sketch(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, const float* A,
                            int64_t lda, const double* B, int64_t ldb, double* D, int64_t ldd, void* work,
-                           size_t work_bytes, int* err) {
-  return ozx_run(s, ta, tb, m, n, k, 1.0, A, lda, true, 4, B, ldb, false, 5, 0.0, D, ldd, work, work_bytes, err);
+                           size_t work_bytes, int* err, OzKeep* keep) {
+  return ozx_run(s, ta, tb, m, n, k, 1.0, A, lda, true, 4, B, ldb, false, 5, 0.0, D, ldd, work, work_bytes, err,
+                 keep);
 }
 
 cudaError_t gemm_oz32(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, float alpha,

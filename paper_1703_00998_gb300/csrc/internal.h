@@ -88,12 +88,26 @@ cudaError_t gemm_oz(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int6
                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* D, int64_t ldd,
                     void* work, size_t work_bytes, int* err);
 size_t gemm_oz_work_bytes(int64_t m, int64_t n, int64_t k);
+// A caller-held region for op(A)'s slices (see gemm_oz_keep): products that
+// share op(A) slice it once.  ready: the region holds op(A)'s slices.
+struct OzKeep {
+  void* base = nullptr;
+  size_t bytes = 0;
+  bool ready = false;
+};
+// gemm_oz with op(A)'s slices in keep (formed when !keep->ready, reused otherwise:
+// the caller vouches that op(A) has not changed); gemm_oz_keep_bytes is the
+// region's size for an m x n x k product (sketch: the gemm_oz_sketch form).
+cudaError_t gemm_oz_keep(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
+                         const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* D,
+                         int64_t ldd, void* work, size_t work_bytes, int* err, OzKeep* keep);
+size_t gemm_oz_keep_bytes(int64_t m, int64_t n, int64_t k, bool sketch);
 // D (m x n, FP64) = op(A) op(B) with op(A) FP32 data (split exactly into 4
 // slices) and op(B) FP64 data split into 5 slices (35 bits): the sketch
 // products of the mixed form, n <= 256 < m.  work: gemm_oz_sketch_work_bytes.
 cudaError_t gemm_oz_sketch(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, const float* A,
                            int64_t lda, const double* B, int64_t ldb, double* D, int64_t ldd, void* work,
-                           size_t work_bytes, int* err);
+                           size_t work_bytes, int* err, OzKeep* keep = nullptr);
 size_t gemm_oz_sketch_work_bytes(int64_t m, int64_t n, int64_t k);
 // Leading bytes of a gemm_oz workspace that must be zero before its first
 // use (the split-tile accumulators; every call leaves them zero again).
