@@ -79,7 +79,7 @@ def hbm_view(n, b, q, elem_bytes, seconds):
 # times its algorithmic bytes per launch.
 GEMM_TRAFFIC = {"5b25bb34a710a3c2": 0.926}
 # ncu dram bytes (read + write) / algorithmic bytes of gemm_ozx_kernel, by source hash (profiles/)
-OZ_TRAFFIC = {}
+OZ_TRAFFIC = {"4fff8438e965e148": 1.031}   # rank-128 update 1.002, long-K product 1.061 (profiles/)
 # DRAM traffic of the batched kernel per matrix from one ncu capture of a
 # 512-matrix batch of the same size law (dram read + write / 512), valid for
 # the kernel source with this sha256 prefix of csrc/batched.cu; a launch over

@@ -137,7 +137,7 @@ __device__ __forceinline__ Real jb_warp_sum(Real v) {
 // Returns whether a rotation was applied (identical in all lanes).
 template <typename Real, int NU>
 __device__ __forceinline__ bool jb_rotate(int p, int lane, Real* wi, Real* wj, Real* qi, Real* qj, Real* ni,
-                                          Real* nj, Real thr2, Real tol2) {
+                                          Real* nj, Real thr2, Real tol2, float* rho2) {
   Real x[NU], y[NU], q1[NU], q2[NU];
   Real g = 0;
 #pragma unroll
@@ -151,6 +151,8 @@ __device__ __forceinline__ bool jb_rotate(int p, int lane, Real* wi, Real* wj, R
   }
   const Real a = *ni, b = *nj;
   g = jb_warp_sum(g);   // identical in every lane
+  if (a > thr2 && b > thr2)   // the sweep's largest squared relative off-diagonal g^2 / (a b)
+    *rho2 = fmaxf(*rho2, static_cast<float>(g / a * (g / b)));
   if (g == Real(0) || a <= thr2 || b <= thr2 || !(g * g > tol2 * a * b)) return false;
   const Real tt = jb_angle(a, b, g);
   const Real c = jb_rsqrt(fma(tt, tt, Real(1)));
@@ -176,7 +178,11 @@ __device__ __forceinline__ bool jb_rotate(int p, int lane, Real* wi, Real* wj, R
 
 // The sweeps of the block-cyclic order on the seats of this CTA (buffer
 // *cur at entry and exit).  Returns whether the last sweep converged (the
-// same in every CTA).
+// same in every CTA).  Converged: a sweep applied no rotation, or the largest
+// relative off-diagonal rho = |w_i . w_j| / (||w_i|| ||w_j||) it met
+// satisfies rho^2 <= tol / 10: cyclic Jacobi converges quadratically, so the
+// next sweep would meet rho' ~ rho^2 <= tol / 10 and rotate nothing (the
+// confirming sweep is skipped).
 template <typename Real, int NU>
 __device__ bool jb_sweeps(const JbSeats<Real>& S, int* cur_io, int p, int cs, int rank, int max_sweeps, Real thr2,
                           Real tol2, int* s_flag) {
@@ -196,8 +202,9 @@ __device__ bool jb_sweeps(const JbSeats<Real>& S, int* cur_io, int p, int cs, in
       f = jb_warp_sum(f);
       if (lane == 0) *S.n(cur, e / bs, e % bs) = f;
     }
-    if (tid == 0) s_flag[sw & 1] = 0;
+    if (tid == 0) { s_flag[sw & 1] = 0; s_flag[2 + (sw & 1)] = 0; }
     bool rotated = false;
+    float rho2 = 0.0f;
     __syncthreads();
     for (int r = 0; r < P - 1; ++r) {
       if (r == 0 && bs > 1) {
@@ -209,7 +216,8 @@ __device__ bool jb_sweeps(const JbSeats<Real>& S, int* cur_io, int p, int cs, in
             rr_pair(bsp, sub, kp, &a, &b);
             if (b >= bs) continue;
             rotated |= jb_rotate<Real, NU>(p, lane, S.w(cur, seat, a), S.w(cur, seat, b), S.q(cur, seat, a),
-                                           S.q(cur, seat, b), S.n(cur, seat, a), S.n(cur, seat, b), thr2, tol2);
+                                           S.q(cur, seat, b), S.n(cur, seat, a), S.n(cur, seat, b), thr2, tol2,
+                                           &rho2);
           }
           __syncthreads();
         }
@@ -219,7 +227,7 @@ __device__ bool jb_sweeps(const JbSeats<Real>& S, int* cur_io, int p, int cs, in
         for (int i = warp; i < bs; i += JC_WARPS) {
           const int j = (i + sub) % bs;
           rotated |= jb_rotate<Real, NU>(p, lane, S.w(cur, 0, i), S.w(cur, 1, j), S.q(cur, 0, i), S.q(cur, 1, j),
-                                         S.n(cur, 0, i), S.n(cur, 1, j), thr2, tol2);
+                                         S.n(cur, 0, i), S.n(cur, 1, j), thr2, tol2, &rho2);
         }
         __syncthreads();
       }
@@ -250,12 +258,19 @@ __device__ bool jb_sweeps(const JbSeats<Real>& S, int* cur_io, int p, int cs, in
       cur = nx;
       cluster.sync();
     }
-    // a sweep without rotations anywhere in the cluster: converged
+    // a sweep without rotations anywhere in the cluster, or one whose largest relative
+    // off-diagonal already puts the next sweep below the tolerance: converged
     if (rotated) s_flag[sw & 1] = 1;   // benign race: every writer stores 1
+    if (lane == 0 && rho2 > 0.0f) atomicMax(&s_flag[2 + (sw & 1)], __float_as_int(rho2));   // non-negative floats
     cluster.sync();
     int any = 0;
-    for (int q = 0; q < cs; ++q) any |= *cluster.map_shared_rank(&s_flag[sw & 1], q);
-    converged = (any == 0);
+    float rmax = 0.0f;
+    for (int q = 0; q < cs; ++q) {
+      any |= *cluster.map_shared_rank(&s_flag[sw & 1], q);
+      rmax = fmaxf(rmax, __int_as_float(*cluster.map_shared_rank(&s_flag[2 + (sw & 1)], q)));
+    }
+    const float tol = sqrtf(static_cast<float>(tol2));
+    converged = (any == 0) || (rmax <= 0.1f * tol);
   }
   *cur_io = cur;
   return converged;
@@ -282,7 +297,7 @@ jacobi_block64_kernel(int p, const double* __restrict__ M, int64_t ldm, const do
   JbSeats<double> S{jsm, jsm + 8ull * bs * p, p, bs};
   __shared__ double s_part[JC_CLUSTER];
   __shared__ double s_fro;
-  __shared__ int s_flag[2];
+  __shared__ int s_flag[4];   // per sweep parity: rotated, largest rho^2 (float bits)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   // this CTA's two home blocks: rank (top) and 2 cs - 1 - rank (bottom)
@@ -310,7 +325,7 @@ jacobi_block64_kernel(int p, const double* __restrict__ M, int64_t ldm, const do
     f = warp_sum(f);
     if (lane == 0) s_part[rank] = f;
   }
-  if (tid < 2) s_flag[tid] = 0;
+  if (tid < 4) s_flag[tid] = 0;
   cluster.sync();
   if (tid == 0) {
     double f = 0.0;
@@ -401,7 +416,7 @@ jacobi_block32_kernel(int p, const double* __restrict__ M, int64_t ldm, double* 
   JbSeats<float> S{jsm32, jsm32 + 8ull * bs * p, p, bs};
   __shared__ double s_part[JC_CLUSTER];
   __shared__ double s_scale;
-  __shared__ int s_flag[2];
+  __shared__ int s_flag[4];   // per sweep parity: rotated, largest rho^2 (float bits)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   // ||M||_F^2 in FP64 over this CTA's rows of M, then the common scale
@@ -418,7 +433,7 @@ jacobi_block32_kernel(int p, const double* __restrict__ M, int64_t ldm, double* 
     f = warp_sum(f);
     if (lane == 0) s_part[rank] = f;
   }
-  if (tid < 2) s_flag[tid] = 0;
+  if (tid < 4) s_flag[tid] = 0;
   cluster.sync();
   if (tid == 0) {
     double f = 0.0;
