@@ -106,9 +106,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-t-only", action="store_true", help="skip the T-only (no U, V) FP64 timing")
-    ap.add_argument("--probe-oz", action="store_true",
-                    help="profiling aid: run two isolated Ozaki-scheme FP64 products (8192 x 8192 x 128 and "
-                         "8192 x 128 x 4096) once and exit")
+    ap.add_argument("--probe-oz", default=None, choices=["rank", "thin", "both"],
+                    help="isolated Ozaki-scheme products for profiling (rank-128 update, long-K product) and exit")
     ap.add_argument("--fp64-emulation", type=int, default=1, choices=[0, 1],
                     help="FP64 form: 1 Ozaki-scheme tensor-core GEMM, 0 FP64 DFMA GEMM")
     ap.add_argument("--overlap", type=int, default=1, choices=[0, 1],
@@ -599,26 +598,43 @@ def run_mixed(args, lib, native, A, Tst64, n, b, q, stream, dist):
     return out
 
 
-def probe_oz():
-    """Two isolated products through randutv_dgemm_oz (Gaussian operands, beta = 0): a rank-128 update
-    D = A B^T (8192 x 8192 x 128) and a long-K product (8192 x 128 x 4096)."""
+PROBE_SHAPES = {"rank": (8192, 8192, 128, False, True), "thin": (8192, 128, 8192, False, False)}
+
+
+def probe_oz(which):
+    """Isolated products through randutv_dgemm_oz (Gaussian operands): "rank" a rank-128 update
+    D = C - A B^T (8192 x 8192 x 128), "thin" a long-K product D = C - A B (8192 x 128 x 8192), "both"
+    both.  Each shape is called three times (the first builds and loads the kernels), and its CUDA-
+    event time per call (slicing + product kernels, from the library's profiling classes) printed."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_1703_00998_gb300 import native
     lib = native.lib()
     lib.randutv_set_stream(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
-    for m, n, k, ta, tb in ((8192, 8192, 128, False, True), (8192, 128, 4096, False, False)):
+    for name in (("rank", "thin") if which == "both" else (which,)):
+        m, n, k, ta, tb = PROBE_SHAPES[name]
         g = torch.Generator(device="cuda").manual_seed(m + n + k)
         A = torch.randn((k, m) if ta else (m, k), dtype=torch.float64, device="cuda", generator=g)
         B = torch.randn((n, k) if tb else (k, n), dtype=torch.float64, device="cuda", generator=g)
         Ac, Bc = A.t().contiguous(), B.t().contiguous()
-        C = torch.zeros((n, m), dtype=torch.float64, device="cuda")
-        native.check(lib.randutv_dgemm_oz(b"T" if ta else b"N", b"T" if tb else b"N", m, n, k, 1.0, Ac.data_ptr(),
-                                          A.shape[0], Bc.data_ptr(), B.shape[0], 0.0, C.data_ptr(), m),
-                     "randutv_dgemm_oz")
-    torch.cuda.synchronize()
-    print(json.dumps({"probe_oz": "ok"}), flush=True)
+        C = torch.randn((n, m), dtype=torch.float64, device="cuda", generator=g)
+
+        def call():
+            native.check(lib.randutv_dgemm_oz(b"T" if ta else b"N", b"T" if tb else b"N", m, n, k, -1.0,
+                                              Ac.data_ptr(), A.shape[0], Bc.data_ptr(), B.shape[0], 1.0,
+                                              C.data_ptr(), m), "randutv_dgemm_oz")
+        call()
+        lib.randutv_profile_enable(1)
+        lib.randutv_profile_reset()
+        for _ in range(2):
+            call()
+        torch.cuda.synchronize()
+        go, sl = native.profile_read(8), native.profile_read(10)
+        lib.randutv_profile_enable(0)
+        print(json.dumps({"probe_oz": name, "m": m, "n": n, "k": k, "product_ms": go["ms"] / 2,
+                          "slicing_ms": sl["ms"] / 2,
+                          "bf16_slice_tflops": go["flops"] / (go["ms"] * 1e-3) / 1e12}), flush=True)
     return 0
 
 
@@ -883,7 +899,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.probe_oz:
-        return probe_oz()
+        return probe_oz(args.probe_oz)
     if args.adjoint_only:
         import torch
         import __graft_entry__
