@@ -14,6 +14,7 @@ import ctypes
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -74,17 +75,18 @@ def hbm_view(n, b, q, elem_bytes, seconds):
 
 # DRAM traffic of the FP64 GEMM kernel from one ncu capture (n=4096, launches
 # 7-9 of the factorization): measured dram read+write / algorithmic bytes.
-# Valid only for the kernel source it was taken on (sha256 prefix of
-# csrc/gemm_f64.cu); the per-launch traffic of the bench run is this ratio
+# Valid only for the kernel source it was taken on (kernel_hash of
+# csrc/gemm_f64.cu: its code without comments); the per-launch traffic of the bench run is this ratio
 # times its algorithmic bytes per launch.
-GEMM_TRAFFIC = {"5b25bb34a710a3c2": 0.926}
-# ncu dram bytes (read + write) / algorithmic bytes of gemm_ozx_kernel, by source hash (profiles/)
-OZ_TRAFFIC = {"4fff8438e965e148": 1.031}   # rank-128 update 1.002, long-K product 1.061 (profiles/)
+GEMM_TRAFFIC = {"4b6a7761b9ca2e2b": 0.926}
+# ncu dram bytes (read + write) / algorithmic bytes of gemm_ozx_kernel, by kernel_hash of csrc/gemm_oz.cu
+OZ_TRAFFIC = {"7fa6e03422c5c52c": 1.031}   # rank-128 update 1.002, long-K product 1.061 (profiles/)
 # DRAM traffic of the batched kernel per matrix from one ncu capture of a
 # 512-matrix batch of the same size law (dram read + write / 512), valid for
-# the kernel source with this sha256 prefix of csrc/batched.cu; a launch over
-# the whole batch is scaled by its matrix count.
-BATCHED_TRAFFIC = {"438f06db0f444904": 7.227e9 / 512}
+# the kernel source with this kernel_hash of csrc/batched.cu (none: the
+# capture predates the current source); a launch over the whole batch is
+# scaled by its matrix count.
+BATCHED_TRAFFIC = {}
 
 
 def parse():
@@ -402,7 +404,13 @@ def gpu_index():
 
 
 def kernel_hash(path):
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    """sha256 prefix of a CUDA source's code: comments removed and whitespace collapsed, so that
+    an edit of a comment keeps a traffic measurement valid and any change of code voids it."""
+    src = open(path, encoding="utf-8").read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    src = " ".join(src.split())
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
 def cpu_sample(A, b, q, seconds):
@@ -712,6 +720,7 @@ def run_own(args):
     if args.overlap:
         opts.overlap = 0
         lib.randutv_profile_reset()
+        native.jacobi_sweeps(reset=True)
         lib.randutv_profile_enable(1)
         r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         r0.record(stream)
@@ -720,10 +729,12 @@ def run_own(args):
         torch.cuda.synchronize()
         lib.randutv_profile_enable(0)
         prof_r = {name: native.profile_read(i) for i, name in enumerate(native.PROF_NAMES)}
+        jsw = native.jacobi_sweeps(reset=True)
         ms_r, steps_r = r0.elapsed_time(r1), 1
         opts.overlap = args.overlap
     else:
         prof_r, ms_r, steps_r = prof, ms * args.steps, args.steps
+        jsw = None
 
     # verification of the last factorization (not timed)
     verify = {}
@@ -862,6 +873,9 @@ def run_own(args):
                      "serialised": {k: {"ms_per_step": v["ms"] / steps_r, "launches_per_step": v["launches"] / steps_r}
                                     for k, v in prof_r.items()},
                      "serialised_ms_per_step": ms_r / steps_r}
+    if jsw and jsw["svds"]:
+        breakdown["jacobi_sweeps_per_svd"] = {"fp32": jsw["fp32"] / jsw["svds"], "fp64": jsw["fp64"] / jsw["svds"],
+                                              "svds": jsw["svds"]}
 
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

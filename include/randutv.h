@@ -76,8 +76,11 @@ typedef struct randutv_opts {
                            core slice products, FP64-accurate); 0 = FP64
                            DFMA GEMM.  The Gram matrices of the compact-WY
                            factors and products too small for its tiles
-                           always use DFMA.  Needs about 24 n^2 bytes of
-                           scratch per lane (n = max(m, n)).                 */
+                           always use DFMA.  Needs about 17 n^2 bytes of
+                           scratch for each of the T and U/V lanes
+                           (n = max(m, n)), and 17 n^2 more when q > 0 for
+                           the slices of a step's X^T, which its products
+                           X^T G and X^T Z share.                           */
   int sketch_prec;      /* mixed form: how the sketch products (Section 4.3,
                            step 2) are formed; they decide which subspace a
                            step captures, not the backward error, but on
@@ -193,6 +196,12 @@ int randutv_profile_reset(void);
 int randutv_profile_read(int cls, double* ms, int64_t* launches, double* flops, double* bytes);
 /* Number of kernels this library has launched since it was loaded. */
 uint64_t randutv_launch_count(void);
+/* Sweeps of the small-SVD Jacobi kernels on the current device since the
+ * last reset: FP32 sweeps, FP64 sweeps, and the number of small SVDs (FP64
+ * sweep launches).  reset != 0 clears the counters after reading.  Waits for
+ * the device's pending work (a synchronous copy).  Any output pointer may be
+ * NULL.  Returns RANDUTV_ECUDA if the counters cannot be read. */
+int randutv_jacobi_sweeps(int64_t* fp32_sweeps, int64_t* fp64_sweeps, int64_t* svds, int reset);
 
 /* ---- Building blocks of one step, exposed so each kernel can be tested on
  * its own against the CPU oracle.  Same conventions as above. ---- */
@@ -244,13 +253,17 @@ int randutv_sgemm_tc(char transa, char transb, int64_t m, int64_t n, int64_t k, 
  * the paper.  Each row of op(A) and column of op(B) is split per K chunk of
  * 128 into a power-of-two scale and 8 slices of 7 bits (56 bits), the 36
  * slice-pair products with slice indices s + t <= 7 are summed exactly in
- * FP32 on the tensor cores, combined exactly in 64-bit integers and
- * rounded once to FP64 per chunk; chunks are summed in FP64.  Error per
- * chunk <= 128 * 2^-55 * max|op(A) row| * max|op(B) column| over the chunk
- * plus FP64 rounding.  k = 0 gives C = beta C.  Allocates its scratch
- * (about 16 (m + n) k bytes of slices, plus 8 m n per chunk when k > 128)
- * with cudaMallocAsync on the bound stream and synchronises it.  Negative
- * return: the position of the first invalid argument. */
+ * FP32 on the tensor cores and combined exactly in 64-bit integers; the
+ * chunks accumulate in a 64-bit fixed-point sum whose unit is set by bounds
+ * of the row and column 2-norms (it cannot overflow; the unit is below
+ * 2^-60 ||row|| ||column||), two roundings to that unit per chunk, and the
+ * result is rounded once to FP64.  Error <= 2 * 128 * 2^-55 * max|op(A)
+ * row| * max|op(B) column| per chunk plus one unit per chunk plus the final
+ * rounding: the accuracy class of an FP64 GEMM.  k = 0 gives C = beta C.
+ * Allocates its scratch (about 16 (m + n) k bytes of slices and 20 MB of
+ * split-tile accumulators) with cudaMallocAsync on the bound stream and
+ * synchronises it.  Negative return: the position of the first invalid
+ * argument. */
 int randutv_dgemm_oz(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
                      const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                      double* C, int64_t ldc);

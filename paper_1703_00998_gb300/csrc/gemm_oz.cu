@@ -30,8 +30,9 @@
 // The result is at least as accurate as an FP64 GEMM: the slices truncate
 // each operand after 56 bits of its chunk's scale (error <= 2 * 128 *
 // 2^-55 * max|a| * max|b| per chunk), the accumulator rounds each chunk
-// twice at 2^-62 |a| |b| (against the u sum |a_k| |b_k| <= 2^-53 |a| |b|
-// of an FP64 dot product), and the final value is rounded once.  Integer additions are associative, so a K range split over
+// twice to its unit, which is below 2^-60 |a| |b| (against the u sum
+// |a_k| |b_k| <= 2^-53 |a| |b| of an FP64 dot product), and the final value
+// is rounded once.  Integer additions are associative, so a K range split over
 // several CTAs (their accumulators added with integer atomics) gives
 // bit-identical results in any order.
 //

@@ -136,7 +136,8 @@ cudaError_t panel_qr(cudaStream_t s, int64_t k, int w, double* P, int64_t ldp, d
                      double* Vexp, double* R, double* part, unsigned* bar);
 int64_t panel_qr_part_elems(int64_t k, int w);
 // S (w x w, ld w) with H_1...H_w = I - Vexp S Vexp^T from the Gram matrix
-// Vexp^T Vexp (w x w, ld w) and tau: S = (striu(Gram) + diag(1/tau))^-1.
+// Vexp^T Vexp (w x w, ld w, the full symmetric matrix: its lower triangle is
+// read) and tau: S = (striu(Gram) + diag(1/tau))^-1.
 cudaError_t tfactor_from_gram(cudaStream_t s, int w, const double* gram, const double* tau,
                               double* S);
 

@@ -33,6 +33,10 @@
 namespace rutv {
 
 constexpr int JC_CLUSTER = 16;   // CTAs of the cluster (non-portable size, opt-in)
+
+// Sweep counters (diagnostics): FP32 sweeps, FP64 sweeps, FP64 launches; added
+// by CTA 0 of each launch, read and cleared by randutv_jacobi_sweeps.
+__device__ unsigned long long g_jb_sweeps[3];
 constexpr int JC_NT = 128;       // 4 warps per CTA, one pair per warp at a time
 constexpr int JC_WARPS = JC_NT / 32;
 constexpr int JC_MAXP = 256;
@@ -185,7 +189,7 @@ __device__ __forceinline__ bool jb_rotate(int p, int lane, Real* wi, Real* wj, R
 // confirming sweep is skipped).
 template <typename Real, int NU>
 __device__ bool jb_sweeps(const JbSeats<Real>& S, int* cur_io, int p, int cs, int rank, int max_sweeps, Real thr2,
-                          Real tol2, int* s_flag) {
+                          Real tol2, int* s_flag, int* sweeps_done) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -193,7 +197,8 @@ __device__ bool jb_sweeps(const JbSeats<Real>& S, int* cur_io, int p, int cs, in
   const int bsp = bs + (bs & 1);
   int cur = *cur_io;
   bool converged = false;
-  for (int sw = 0; sw < max_sweeps && !converged; ++sw) {
+  int sw = 0;
+  for (; sw < max_sweeps && !converged; ++sw) {
     // exact squared norms of this CTA's columns at the start of the sweep
     for (int e = warp; e < 2 * bs; e += JC_WARPS) {
       const Real* w = S.w(cur, e / bs, e % bs);
@@ -273,6 +278,7 @@ __device__ bool jb_sweeps(const JbSeats<Real>& S, int* cur_io, int p, int cs, in
     converged = (any == 0) || (rmax <= 0.1f * tol);
   }
   *cur_io = cur;
+  *sweeps_done = sw;
   return converged;
 }
 
@@ -338,8 +344,13 @@ jacobi_block64_kernel(int p, const double* __restrict__ M, int64_t ldm, const do
   const double pu = static_cast<double>(p) * 0x1p-53;
   const double thr2 = pu * pu * s_fro;
   int cur = 0;
-  const bool converged = jb_sweeps<double, NU>(S, &cur, p, cs, rank, max_sweeps, thr2, tol * tol, s_flag);
+  int nsw = 0;
+  const bool converged = jb_sweeps<double, NU>(S, &cur, p, cs, rank, max_sweeps, thr2, tol * tol, s_flag, &nsw);
   if (!converged && rank == 0 && tid == 0) atomicOr(err, kDevErrNoConv);
+  if (rank == 0 && tid == 0) {
+    atomicAdd(&g_jb_sweeps[1], static_cast<unsigned long long>(nsw));
+    atomicAdd(&g_jb_sweeps[2], 1ull);
+  }
 
   // every block is at its home seat again (buffer cur): exact norms
   for (int e = warp; e < 2 * bs; e += JC_WARPS) {
@@ -466,7 +477,9 @@ jacobi_block32_kernel(int p, const double* __restrict__ M, int64_t ldm, double* 
   }
   const float pu = static_cast<float>(p) * 0x1p-24f;
   int cur = 0;
-  jb_sweeps<float, NU>(S, &cur, p, cs, rank, max_sweeps, pu * pu * fro, pu * pu, s_flag);
+  int nsw = 0;
+  jb_sweeps<float, NU>(S, &cur, p, cs, rank, max_sweeps, pu * pu * fro, pu * pu, s_flag, &nsw);
+  if (rank == 0 && tid == 0) atomicAdd(&g_jb_sweeps[0], static_cast<unsigned long long>(nsw));
   for (int seat = 0; seat < 2; ++seat) {
     const int B = seat == 0 ? rank : 2 * cs - 1 - rank;
     for (int i = 0; i < bs; ++i) {
@@ -707,4 +720,25 @@ cudaError_t jacobi_svd(cudaStream_t s, int p, const double* M, int64_t ldm, doub
   return cudaGetLastError();
 }
 
+cudaError_t jacobi_sweep_counts(unsigned long long out[3], bool reset) {
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_jb_sweeps, sizeof(unsigned long long) * 3);
+  if (e == cudaSuccess && reset) {
+    const unsigned long long z[3] = {0, 0, 0};
+    e = cudaMemcpyToSymbol(g_jb_sweeps, z, sizeof(z));
+  }
+  return e;
+}
+
 }  // namespace rutv
+
+extern "C" int randutv_jacobi_sweeps(int64_t* fp32_sweeps, int64_t* fp64_sweeps, int64_t* svds, int reset) {
+  unsigned long long c[3] = {0, 0, 0};
+  if (rutv::jacobi_sweep_counts(c, reset != 0) != cudaSuccess) {
+    cudaGetLastError();
+    return RANDUTV_ECUDA;
+  }
+  if (fp32_sweeps) *fp32_sweeps = static_cast<int64_t>(c[0]);
+  if (fp64_sweeps) *fp64_sweeps = static_cast<int64_t>(c[1]);
+  if (svds) *svds = static_cast<int64_t>(c[2]);
+  return RANDUTV_OK;
+}

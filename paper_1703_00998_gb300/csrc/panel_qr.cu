@@ -196,7 +196,9 @@ cudaError_t panel_qr(cudaStream_t s, int64_t k, int w, double* P, int64_t ldp, d
 //   S(c,c) = tau_c,  S(i,c) = -tau_i * sum_{l=i+1..c} Gram(i,l) S(l,c)  (i < c),
 // which is the forward accumulation of H_1 ... H_w = I - V S V^T (the
 // recurrence of the block reflector, Section 2.4) with every column of S
-// solved independently: one warp per column.
+// solved independently: one warp per column.  Gram = V^T V is symmetric, so
+// Gram(i, l) is read as Gram(l, i): consecutive l across the lanes, one
+// coalesced segment per step instead of 32 scattered lines.
 constexpr int TF_WARPS = 8;
 
 __global__ void __launch_bounds__(TF_WARPS * 32)
@@ -212,7 +214,7 @@ tfactor_kernel(int w, const double* __restrict__ gram, const double* __restrict_
   __syncwarp();
   for (int i = c - 1; i >= 0; --i) {
     double s = 0.0;
-    for (int l = i + 1 + lane; l <= c; l += 32) s = fma(gram[i + static_cast<int64_t>(l) * w], x[l], s);
+    for (int l = i + 1 + lane; l <= c; l += 32) s = fma(gram[l + static_cast<int64_t>(i) * w], x[l], s);
     s = warp_sum(s);
     if (lane == 0) x[i] = -tau[i] * s;
     __syncwarp();

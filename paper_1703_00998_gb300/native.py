@@ -86,6 +86,7 @@ SIGNATURES = {
     "randutv_profile_read": (_i32, [_i32, ctypes.POINTER(_f64), ctypes.POINTER(_i64), ctypes.POINTER(_f64),
                                     ctypes.POINTER(_f64)]),
     "randutv_launch_count": (ctypes.c_uint64, []),
+    "randutv_jacobi_sweeps": (_i32, [ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64), _i32]),
     "randutv_small_svd_noalloc": (_i32, [_i64, _vp, _i64, _vp, _vp, _vp, _i32]),
     "randutv_batched_opts_default": (None, [ctypes.POINTER(BatchedOpts)]),
     "randutv_batched_plan_create": (_i32, [_i64, _vp, _vp, _i32, ctypes.POINTER(_vp)]),
@@ -113,6 +114,14 @@ def profile_read(cls):
     check(lib().randutv_profile_read(int(cls), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl),
                                      ctypes.byref(by)), "randutv_profile_read")
     return {"ms": ms.value, "launches": n.value, "flops": fl.value, "bytes": by.value}
+
+
+def jacobi_sweeps(reset=True):
+    """Small-SVD sweep counters: {"fp32": .., "fp64": .., "svds": ..} (cleared when reset)."""
+    a, b, c = _i64(), _i64(), _i64()
+    check(lib().randutv_jacobi_sweeps(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), int(bool(reset))),
+          "randutv_jacobi_sweeps")
+    return {"fp32": a.value, "fp64": b.value, "svds": c.value}
 
 
 def lib():

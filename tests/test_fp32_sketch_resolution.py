@@ -3,7 +3,7 @@ CPU.  Fig. 4's steps are run in FP64 with only the sketch Y = (X^T X)^q X^T G
 formed in FP32 (the one place where the batched form's precision changes
 which subspace a step captures): over the leading entries the resolution
 criterion keeps (2^-24 (d_{r0} / d_j)^(2q+1) <= 1e-3 within each block),
-|diag T| agrees with the FP64 oracle to 1e-4; on a block whose singular
+|diag T| agrees with the FP64 oracle to 1e-4 relative, entry by entry; on a block whose singular
 values span ~180 the entries beyond the prefix move by more than 1e-3."""
 import numpy as np
 import pytest
@@ -51,8 +51,7 @@ def test_resolved_entries_agree(m, n, r, b):
     do = np.abs(np.diag(To))
     d32 = _diag_fp32_sketch(A, b, 1, _g)
     kk = _resolved_prefix(do, b)
-    floor = len(do) * 2.0 ** -24 * do[0] / 1e-4
-    dr = np.abs(d32 - do) / (do + floor)
+    dr = np.abs(d32 - do) / do
     assert kk > 0
     assert dr[:kk].max() <= 1e-4, (kk, dr[:kk].max())
 
@@ -64,5 +63,4 @@ def test_unresolved_entries_move():
     d32 = _diag_fp32_sketch(A, 32, 1, _g)
     kk = _resolved_prefix(do, 32)
     assert kk < 32
-    floor = len(do) * 2.0 ** -24 * do[0] / 1e-4
-    assert (np.abs(d32 - do) / (do + floor))[kk:32].max() > 1e-3
+    assert (np.abs(d32 - do) / do)[kk:32].max() > 1e-3
