@@ -10,12 +10,16 @@
 // factorization, so HBM is read and written once.  Column j needs, from all
 // rows, ||x(2:)||^2 and x^T P(:, c) for c > j; every CTA adds its partial
 // sums into one accumulator vector per column with FP64 atomic reductions in
-// L2, one grid barrier follows, and every CTA reads the same sums (so all
-// hold identical beta, tau and v^T P) and updates its rows.  The partial sums
-// of column j+1 are formed right after the update of column j, so each
-// column costs one barrier and one L2 round trip.  (The order of the atomic
-// additions is not fixed, so results may differ between runs in the last
-// bits.)
+// L2, one grid barrier follows, and every thread reads the two sums that
+// define the reflector and evaluates beta, tau and the scale itself (all
+// agree bit for bit).  Per column, after the barrier: column j+1 is updated
+// first, then each group of 1-8 threads takes a column c > j+1, updates it
+// and, in the same pass over its rows, forms its dot product with the new
+// column j+1 (the next column's sums), so a column costs one barrier, one
+// L2 round trip and one __syncthreads.  The scaling of x(2:) to v is
+// deferred by one column (nobody reads it meanwhile).  (The order of the
+// atomic additions is not fixed, so results may differ between runs in the
+// last bits.)
 // Convention: LAPACK dlarfg (beta = -sign(alpha)||x||, tau = (beta-alpha)/beta,
 // v = x(2:)/(alpha-beta), tau = 0 when x(2:) = 0).
 #include <algorithm>
@@ -25,13 +29,28 @@
 namespace rutv {
 
 constexpr int PQ_NT = 256;
-constexpr int PQ_WARPS = PQ_NT / 32;
 constexpr int kMaxCoopBlocks = kNumSMs;
 // Preferred grid: 136 = 152 - 16, so the panel QR of the next step's Y runs
 // beside the previous step's small SVD (one 16-CTA cluster); a panel whose
 // rows do not fit 136 CTAs' shared memory takes up to 152.
 constexpr int kPreferredCoopBlocks = kNumSMs - 16;
 constexpr size_t kPqSmemBudget = 226 * 1024;   // of the 227 KB a CTA may use
+
+// Reflector j from its two sums: alpha = P(j, j) and xn2 = ||x(2:)||^2.
+// Every thread evaluates it from the same two values, so all agree bit for bit.
+struct PqRefl { double beta, tau, scale; };
+__device__ __forceinline__ PqRefl pq_reflector(double alpha, double xn2) {
+  PqRefl r{alpha, 0.0, 0.0};
+  if (xn2 != 0.0) {
+    const double nrm = sqrt(fma(alpha, alpha, xn2));
+    r.beta = -copysign(nrm, alpha);
+    // tau = (beta - alpha) / beta and scale = 1 / (alpha - beta) from one division
+    const double q = 1.0 / (r.beta * (alpha - r.beta));
+    r.tau = (r.beta - alpha) * ((alpha - r.beta) * q);
+    r.scale = r.beta * q;
+  }
+  return r;
+}
 
 __global__ void __launch_bounds__(PQ_NT, 1)
 panel_qr_kernel(int64_t k, int w, double* __restrict__ P, int64_t ldp, double* __restrict__ tau_out,
@@ -42,105 +61,144 @@ panel_qr_kernel(int64_t k, int w, double* __restrict__ P, int64_t ldp, double* _
   const int tid = threadIdx.x;
   const int64_t r_lo = static_cast<int64_t>(blockIdx.x) * rpb;
   const int nr = static_cast<int>(imax64(0, imin64(k, r_lo + rpb) - r_lo));
-  double* slice = sm;                         // rpb x w, column-major, ld rpb
-  double* vec = slice + static_cast<size_t>(rpb) * w;  // w: sums, then tau * v^T P(:, c)
-  double* rowj = vec + w;                     // w: row j of the panel
-  double* taus = rowj + w;                    // w: tau of every column
-  __shared__ double s_beta, s_tau, s_scale;
+  double* slice = sm;                                   // rpb x w, column-major, ld rpb
+  double* taus = slice + static_cast<size_t>(rpb) * w;  // w: the scale of each column, then its tau
   // part: acc (w x w, zeroed by the host) receives the partial sums of
   // column j at acc[j w + c] through FP64 atomic additions in L2; rowbuf
   // (w x w) row j of the panel at rowbuf[j w + c], stored by the owning CTA.
   double* acc = part;
   double* rowbuf = part + static_cast<size_t>(w) * w;
+  auto col = [&](int c) { return slice + static_cast<size_t>(c) * rpb; };
+  // local index of global row g in this CTA, or -1
+  auto own = [&](int64_t g) { return (g >= r_lo && g < r_lo + nr) ? static_cast<int>(g - r_lo) : -1; };
+  // Column groups: G threads (adjacent lanes, G a power of two <= 8) per
+  // column, each taking every G-th row; a group's sum is combined by
+  // shuffles among its own lanes (groups never straddle a warp and run
+  // their loop iterations together).
+  auto group_size = [&](int ncols) {
+    int g = 1;
+    while (g < 8 && 2 * g * ncols <= PQ_NT) g *= 2;
+    return g;
+  };
+  auto group_mask = [&](int G) { return ((1u << G) - 1u) << ((tid & 31) & ~(G - 1)); };
 
-  for (int64_t idx = tid; idx < static_cast<int64_t>(nr) * w; idx += PQ_NT) {
-    const int i = static_cast<int>(idx % nr), c = static_cast<int>(idx / nr);
-    slice[i + static_cast<size_t>(c) * rpb] = P[(r_lo + i) + c * ldp];
-  }
+  for (int c = 0; c < w; ++c)
+    for (int i = tid; i < nr; i += PQ_NT) col(c)[i] = P[(r_lo + i) + c * ldp];
   __syncthreads();
 
-  // This CTA's contribution to column j's sums over the rows below row j:
-  //   acc[j w + c] += sum_{i>j} P(i,j) P(i,c)  (c >= j; c = j gives ||x(2:)||^2)
-  // and, from the CTA owning row j, rowbuf[j w + c] = P(j, c).
-  auto partials = [&](int j) {
-    const int i0 = static_cast<int>(imax64(0, j + 1 - r_lo));
-    const double* xj = slice + static_cast<size_t>(j) * rpb;
-    if (i0 < nr) {
-      for (int c = j + tid; c < w; c += PQ_NT) {
-        const double* xc = slice + static_cast<size_t>(c) * rpb;
-        double s0 = 0.0, s1 = 0.0;
-        int i = i0;
-        for (; i + 1 < nr; i += 2) { s0 = fma(xj[i], xc[i], s0); s1 = fma(xj[i + 1], xc[i + 1], s1); }
-        if (i < nr) s0 = fma(xj[i], xc[i], s0);
-        atomicAdd(acc + static_cast<size_t>(j) * w + c, s0 + s1);
+  // Sums of column 0: acc[c] += sum_{i>0} P(i,0) P(i,c), rowbuf[c] = P(0, c).
+  {
+    const int G = group_size(w);
+    const int grp = tid / G, sub = tid % G;
+    const unsigned gm = group_mask(G);
+    const int i1 = static_cast<int>(imax64(0, 1 - r_lo));
+    const int l0 = own(0);
+    const double* x0 = col(0);
+    for (int c = grp; c < w; c += PQ_NT / G) {
+      const double* xc = col(c);
+      double s0 = 0.0;
+      for (int i = i1 + sub; i < nr; i += G) s0 = fma(x0[i], xc[i], s0);
+      for (int o = G / 2; o > 0; o >>= 1) s0 += __shfl_xor_sync(gm, s0, o, G);
+      if (sub == 0) {
+        if (i1 < nr) atomicAdd(acc + c, s0);
+        if (l0 >= 0) rowbuf[c] = xc[l0];
       }
     }
-    if (j >= r_lo && j < r_lo + nr)
-      for (int c = j + tid; c < w; c += PQ_NT)
-        rowbuf[static_cast<size_t>(j) * w + c] = slice[(j - r_lo) + static_cast<size_t>(c) * rpb];
-  };
-
-  partials(0);
-  for (int j = 0; j < w; ++j) {
-    if (!grid_barrier(gb, nb)) return;
-    for (int c = j + tid; c < w; c += PQ_NT) {
-      vec[c] = __ldcg(acc + static_cast<size_t>(j) * w + c);
-      rowj[c] = __ldcg(rowbuf + static_cast<size_t>(j) * w + c);
-    }
-    __syncthreads();
-    if (tid == 0) {
-      const double alpha = rowj[j], xn2 = vec[j];
-      double beta = alpha, t = 0.0, sc = 0.0;
-      if (xn2 != 0.0) {
-        const double nrm = sqrt(fma(alpha, alpha, xn2));
-        beta = -copysign(nrm, alpha);
-        // tau = (beta - alpha) / beta and scale = 1 / (alpha - beta) from one division
-        const double r = 1.0 / (beta * (alpha - beta));
-        t = (beta - alpha) * ((alpha - beta) * r);
-        sc = beta * r;
-      }
-      s_beta = beta; s_tau = t; s_scale = sc;
-      taus[j] = t;
-    }
-    __syncthreads();
-    const double t = s_tau, sc = s_scale;
-    // vec[c] <- tau * v^T P(:, c) = tau * (P(j, c) + scale * sum_{i>j} P(i,j) P(i,c))
-    for (int c = j + 1 + tid; c < w; c += PQ_NT) vec[c] = t * fma(sc, vec[c], rowj[c]);
-    const int i0 = static_cast<int>(imax64(0, j + 1 - r_lo));
-    double* xj = slice + static_cast<size_t>(j) * rpb;
-    for (int i = i0 + tid; i < nr; i += PQ_NT) xj[i] *= sc;   // x(2:) -> v(2:)
-    __syncthreads();
-    if (t != 0.0) {
-      const int ncols = w - j - 1;
-      const int nrows = nr - i0;
-      if (nrows > 0)
-        for (int64_t e = tid; e < static_cast<int64_t>(ncols) * nrows; e += PQ_NT) {
-          const int i = i0 + static_cast<int>(e % nrows);
-          const int c = j + 1 + static_cast<int>(e / nrows);
-          slice[i + static_cast<size_t>(c) * rpb] = fma(-xj[i], vec[c], slice[i + static_cast<size_t>(c) * rpb]);
-        }
-      if (j >= r_lo && j < r_lo + nr) {
-        const int il = static_cast<int>(j - r_lo);
-        for (int c = j + 1 + tid; c < w; c += PQ_NT) slice[il + static_cast<size_t>(c) * rpb] -= vec[c];
-      }
-    }
-    if (j >= r_lo && j < r_lo + nr && tid == 0) xj[j - r_lo] = s_beta;
-    __syncthreads();
-    if (j + 1 < w) partials(j + 1);
   }
 
+  for (int j = 0; j < w; ++j) {
+    if (!grid_barrier(gb, nb)) return;
+    const double* accj = acc + static_cast<size_t>(j) * w;
+    const double* rowj = rowbuf + static_cast<size_t>(j) * w;
+    const PqRefl h = pq_reflector(__ldcg(rowj + j), __ldcg(accj + j));
+    const int lj = own(j);                                        // local row of j (or -1)
+    const int i0 = static_cast<int>(imax64(0, j + 1 - r_lo));     // first local row below j
+    const double* xj = col(j);                                    // x(2:) of column j, unscaled
+    // Column j+1 first (the next reflector's column): for i > j
+    // P(i, j+1) -= v_i wc with v_i = scale x_i, wc = tau (P(j, j+1) + scale
+    // sum_{i>j} x_i P(i, j+1)), and P(j, j+1) -= wc.  Meanwhile x(2:) of
+    // column j-1 becomes v (nobody reads it any more).
+    if (j + 1 < w && h.tau != 0.0) {
+      const double wc = h.tau * fma(h.scale, __ldcg(accj + j + 1), __ldcg(rowj + j + 1));
+      const double ws = wc * h.scale;
+      double* xn = col(j + 1);
+      for (int i = i0 + tid; i < nr; i += PQ_NT) xn[i] = fma(-xj[i], ws, xn[i]);
+      if (lj >= 0 && tid == 0) xn[lj] -= wc;
+    }
+    if (j > 0) {
+      const double sp = taus[j - 1];
+      double* xp = col(j - 1);
+      for (int i = static_cast<int>(imax64(0, j - r_lo)) + tid; i < nr; i += PQ_NT) xp[i] *= sp;
+    }
+    __syncthreads();
+    if (tid == 0) taus[j] = h.scale;
+    // The columns c > j+1: update them, and in the same pass over the rows
+    // form the sums of column j+1 over rows > j+1:
+    //   acc[(j+1) w + c] += sum_{i>j+1} P(i, j+1) P(i, c)   (c = j+1: ||x(2:)||^2);
+    // the owner of row j+1 records that row (after the update) in rowbuf.
+    if (j + 1 < w) {
+      const int ncols = w - j - 1;
+      const int G = group_size(ncols);
+      const int grp = tid / G, sub = tid % G;
+      const unsigned gm = group_mask(G);
+      const int i1 = static_cast<int>(imax64(0, j + 2 - r_lo));   // first local row below j+1
+      const int ln = own(j + 1);
+      const double* xn = col(j + 1);
+      double* accn = acc + static_cast<size_t>(j + 1) * w;
+      double* rown = rowbuf + static_cast<size_t>(j + 1) * w;
+      for (int cc = grp; cc < ncols; cc += PQ_NT / G) {
+        const int c = j + 1 + cc;
+        double* xc = col(c);
+        double s0 = 0.0;
+        if (c > j + 1 && h.tau != 0.0) {
+          const double wc = h.tau * fma(h.scale, __ldcg(accj + c), __ldcg(rowj + c));
+          const double ws = wc * h.scale;
+          if (ln >= 0 && sub == 0) xc[ln] = fma(-xj[ln], ws, xc[ln]);   // row j+1: updated, not summed
+          for (int i = i1 + sub; i < nr; i += G) {
+            const double v = fma(-xj[i], ws, xc[i]);
+            xc[i] = v;
+            s0 = fma(xn[i], v, s0);
+          }
+          if (lj >= 0 && sub == 0) xc[lj] -= wc;
+        } else {
+          for (int i = i1 + sub; i < nr; i += G) s0 = fma(xn[i], xc[i], s0);
+        }
+        for (int o = G / 2; o > 0; o >>= 1) s0 += __shfl_xor_sync(gm, s0, o, G);
+        if (sub == 0) {
+          if (i1 < nr) atomicAdd(accn + c, s0);
+          if (ln >= 0) rown[c] = xc[ln];
+        }
+      }
+    }
+    if (lj >= 0 && tid == 0) col(j)[lj] = h.beta;
+  }
+  __syncthreads();
+  // the last column's x(2:) becomes v; then the scales in taus[] give way to tau
+  {
+    const double sp = taus[w - 1];
+    double* xp = col(w - 1);
+    for (int i = static_cast<int>(imax64(0, w - r_lo)) + tid; i < nr; i += PQ_NT) xp[i] *= sp;
+  }
+  __syncthreads();
+  for (int c = tid; c < w; c += PQ_NT)
+    taus[c] = pq_reflector(__ldcg(rowbuf + static_cast<size_t>(c) * w + c), __ldcg(acc + static_cast<size_t>(c) * w + c)).tau;
+  __syncthreads();
+
   // Write back: P (R above, vectors below), Vexp (explicit), R, tau.
-  for (int64_t idx = tid; idx < static_cast<int64_t>(nr) * w; idx += PQ_NT) {
-    const int i = static_cast<int>(idx % nr), c = static_cast<int>(idx / nr);
-    const int64_t gi = r_lo + i;
-    const double v = slice[i + static_cast<size_t>(c) * rpb];
-    P[gi + c * ldp] = v;
-    double e;
-    if (gi > c) e = v;
-    else if (gi == c) e = (taus[c] != 0.0) ? 1.0 : 0.0;
-    else e = 0.0;
-    Vexp[gi + c * k] = e;
-    if (gi < w) R[gi + static_cast<int64_t>(c) * w] = (gi <= c) ? v : 0.0;
+  for (int c = 0; c < w; ++c) {
+    const double tc = taus[c];
+    const double* xc = col(c);
+    for (int i = tid; i < nr; i += PQ_NT) {
+      const int64_t gi = r_lo + i;
+      const double v = xc[i];
+      P[gi + c * ldp] = v;
+      double e;
+      if (gi > c) e = v;
+      else if (gi == c) e = (tc != 0.0) ? 1.0 : 0.0;
+      else e = 0.0;
+      Vexp[gi + c * k] = e;
+      if (gi < w) R[gi + static_cast<int64_t>(c) * w] = (gi <= c) ? v : 0.0;
+    }
   }
   if (blockIdx.x == 0)
     for (int c = tid; c < w; c += PQ_NT) tau_out[c] = taus[c];
@@ -150,14 +208,14 @@ namespace {
 struct PqGeom { int rpb; int nb; size_t smem; };
 
 PqGeom pq_geometry(int64_t k, int w) {
-  const int64_t max_rows = static_cast<int64_t>(kPqSmemBudget / sizeof(double) - 3 * w) / w;
+  const int64_t max_rows = static_cast<int64_t>(kPqSmemBudget / sizeof(double) - w) / w;
   int64_t rpb = std::max<int64_t>(32, (k + kPreferredCoopBlocks - 1) / kPreferredCoopBlocks);
   rpb = std::min<int64_t>(rpb, std::max<int64_t>(1, max_rows));
   int64_t nb = (k + rpb - 1) / rpb;
   PqGeom g;
   g.rpb = static_cast<int>(rpb);
   g.nb = static_cast<int>(nb);
-  g.smem = (static_cast<size_t>(rpb) * w + 3 * static_cast<size_t>(w)) * sizeof(double);
+  g.smem = (static_cast<size_t>(rpb) * w + static_cast<size_t>(w)) * sizeof(double);
   return g;
 }
 }  // namespace
