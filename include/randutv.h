@@ -196,6 +196,17 @@ int randutv_profile_reset(void);
 int randutv_profile_read(int cls, double* ms, int64_t* launches, double* flops, double* bytes);
 /* Number of kernels this library has launched since it was loaded. */
 uint64_t randutv_launch_count(void);
+/* Self-test of the bounded device waits (no counterpart in the paper): one
+ * tiny launch on the legacy default stream whose wait nothing will end, an
+ * mbarrier no thread arrives at (kind 0) or a grid barrier sized for two
+ * CTAs in a launch of one (kind 1), with a limit of `seconds` (0 < seconds
+ * <= 2; the library's own waits use 2 s).  The kernel records the timeout
+ * and returns, so the call returns RANDUTV_ETIMEOUT (the expected result)
+ * after about `seconds`, and the CUDA context stays usable.  Returns -1 or
+ * -2 for an invalid kind or limit (before any CUDA call), RANDUTV_ECUDA if
+ * a CUDA call failed, RANDUTV_OK if the wait was not cut short (a fault of
+ * the self-test).  Calls that overlap on a device share its error word. */
+int randutv_selftest_wait(int kind, double seconds);
 /* Sweeps of the small-SVD Jacobi kernels on the current device since the
  * last reset: FP32 sweeps, FP64 sweeps, and the number of small SVDs (FP64
  * sweep launches).  reset != 0 clears the counters after reading.  Waits for

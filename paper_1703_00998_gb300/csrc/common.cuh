@@ -38,8 +38,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // last arriver does a single atomic and nobody resets anything.  Returns false
 // (in every thread of the CTA) when the wait ran out or another CTA reported
 // an error; the caller must then return without touching shared state.  The
-// wait gives up after ~2 s of wall time and sets kDevErrTimeout.
-__device__ __forceinline__ bool grid_barrier(const GridBarrier& g, unsigned nblocks) {
+// wait gives up after limit_ns of wall time (2 s by default) and sets
+// kDevErrTimeout.
+__device__ __forceinline__ bool grid_barrier(const GridBarrier& g, unsigned nblocks,
+                                             unsigned long long limit_ns = 2000000000ull) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -52,7 +54,7 @@ __device__ __forceinline__ bool grid_barrier(const GridBarrier& g, unsigned nblo
       unsigned spins = 0;
       while (static_cast<int>(ld_acquire_u32(g.count) - target) < 0) {
         if (++spins > 1024) __nanosleep(32);
-        if ((spins & 255u) == 0 && global_ns() - t0 > 2000000000ull) {
+        if ((spins & 255u) == 0 && global_ns() - t0 > limit_ns) {
           atomicOr(g.err, kDevErrTimeout);
           ok = 0;
           break;

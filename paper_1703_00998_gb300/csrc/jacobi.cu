@@ -122,6 +122,18 @@ __device__ __forceinline__ float jb_angle(float a, float b, float g) {
   return (fabsf(zf) > 0x1p60f) ? 0.5f / zf : copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)));
 }
 
+// rho^2 = g^2 / (a b) for the convergence test of a sweep (a heuristic
+// maximum, so FP32 accuracy suffices): FP64 divisions run on the slow FP64
+// pipe and every lane of the warp executes them, so the FP64 form scales
+// g^2 and a b by the same power of two (a b into [1, 2)) and divides in FP32.
+__device__ __forceinline__ float jb_ratio(double gg, double ab) {
+  const long long eb = (__double_as_longlong(ab) >> 52) & 0x7ff;
+  if (eb == 0 || eb >= 2046) return static_cast<float>(gg / ab);   // zero, subnormal, huge: rare
+  const double sc = __longlong_as_double(static_cast<long long>(2046 - eb) << 52);   // 2^(1023 - eb)
+  return __fdividef(static_cast<float>(gg * sc), static_cast<float>(ab * sc));
+}
+__device__ __forceinline__ float jb_ratio(float gg, float ab) { return __fdividef(gg, ab); }
+
 __device__ __forceinline__ double jb_rsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ float jb_rsqrt(float x) { return rsqrtf(x); }
 
@@ -155,9 +167,10 @@ __device__ __forceinline__ bool jb_rotate(int p, int lane, Real* wi, Real* wj, R
   }
   const Real a = *ni, b = *nj;
   g = jb_warp_sum(g);   // identical in every lane
-  if (a > thr2 && b > thr2)   // the sweep's largest squared relative off-diagonal g^2 / (a b)
-    *rho2 = fmaxf(*rho2, static_cast<float>(g / a * (g / b)));
-  if (g == Real(0) || a <= thr2 || b <= thr2 || !(g * g > tol2 * a * b)) return false;
+  const Real gg = g * g, ab = a * b;
+  const bool live = a > thr2 && b > thr2;
+  if (live) *rho2 = fmaxf(*rho2, jb_ratio(gg, ab));   // the sweep's largest g^2 / (a b)
+  if (g == Real(0) || !live || !(gg > tol2 * ab)) return false;
   const Real tt = jb_angle(a, b, g);
   const Real c = jb_rsqrt(fma(tt, tt, Real(1)));
   const Real sn = c * tt;

@@ -110,7 +110,17 @@ panel_qr_kernel(int64_t k, int w, double* __restrict__ P, int64_t ldp, double* _
     if (!grid_barrier(gb, nb)) return;
     const double* accj = acc + static_cast<size_t>(j) * w;
     const double* rowj = rowbuf + static_cast<size_t>(j) * w;
-    const PqRefl h = pq_reflector(__ldcg(rowj + j), __ldcg(accj + j));
+    // Every sum this thread needs for column j, loaded at once (one L2 round
+    // trip): the reflector's two, column j+1's two, and those of the first
+    // column of this thread's group in the pass below.
+    const int ncols = w - j - 1;
+    const int G = group_size(ncols > 0 ? ncols : 1);
+    const int grp = tid / G, sub = tid % G;
+    const double a_jj = __ldcg(accj + j), r_jj = __ldcg(rowj + j);
+    double a_n = 0.0, r_n = 0.0, a_c = 0.0, r_c = 0.0;
+    if (j + 1 < w) { a_n = __ldcg(accj + j + 1); r_n = __ldcg(rowj + j + 1); }
+    if (grp >= 1 && grp < ncols) { a_c = __ldcg(accj + j + 1 + grp); r_c = __ldcg(rowj + j + 1 + grp); }
+    const PqRefl h = pq_reflector(r_jj, a_jj);
     const int lj = own(j);                                        // local row of j (or -1)
     const int i0 = static_cast<int>(imax64(0, j + 1 - r_lo));     // first local row below j
     const double* xj = col(j);                                    // x(2:) of column j, unscaled
@@ -119,7 +129,7 @@ panel_qr_kernel(int64_t k, int w, double* __restrict__ P, int64_t ldp, double* _
     // sum_{i>j} x_i P(i, j+1)), and P(j, j+1) -= wc.  Meanwhile x(2:) of
     // column j-1 becomes v (nobody reads it any more).
     if (j + 1 < w && h.tau != 0.0) {
-      const double wc = h.tau * fma(h.scale, __ldcg(accj + j + 1), __ldcg(rowj + j + 1));
+      const double wc = h.tau * fma(h.scale, a_n, r_n);
       const double ws = wc * h.scale;
       double* xn = col(j + 1);
       for (int i = i0 + tid; i < nr; i += PQ_NT) xn[i] = fma(-xj[i], ws, xn[i]);
@@ -137,9 +147,6 @@ panel_qr_kernel(int64_t k, int w, double* __restrict__ P, int64_t ldp, double* _
     //   acc[(j+1) w + c] += sum_{i>j+1} P(i, j+1) P(i, c)   (c = j+1: ||x(2:)||^2);
     // the owner of row j+1 records that row (after the update) in rowbuf.
     if (j + 1 < w) {
-      const int ncols = w - j - 1;
-      const int G = group_size(ncols);
-      const int grp = tid / G, sub = tid % G;
       const unsigned gm = group_mask(G);
       const int i1 = static_cast<int>(imax64(0, j + 2 - r_lo));   // first local row below j+1
       const int ln = own(j + 1);
@@ -151,7 +158,8 @@ panel_qr_kernel(int64_t k, int w, double* __restrict__ P, int64_t ldp, double* _
         double* xc = col(c);
         double s0 = 0.0;
         if (c > j + 1 && h.tau != 0.0) {
-          const double wc = h.tau * fma(h.scale, __ldcg(accj + c), __ldcg(rowj + c));
+          if (cc != grp) { a_c = __ldcg(accj + c); r_c = __ldcg(rowj + c); }   // only when w > PQ_NT
+          const double wc = h.tau * fma(h.scale, a_c, r_c);
           const double ws = wc * h.scale;
           if (ln >= 0 && sub == 0) xc[ln] = fma(-xj[ln], ws, xc[ln]);   // row j+1: updated, not summed
           for (int i = i1 + sub; i < nr; i += G) {

@@ -22,8 +22,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
-// Bounded wait for the phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long t0) {
+// Bounded wait for the phase with the given parity; false once limit_ns of
+// wall time (from t0) have passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long t0,
+                                          unsigned long long limit_ns = 2000000000ull) {
   const uint32_t a = smem_u32(bar);
   for (uint32_t spin = 0;; ++spin) {
     uint32_t done;
@@ -33,7 +35,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsign
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
-    if ((spin & 1023u) == 1023u && global_ns() - t0 > 2000000000ull) return false;
+    if ((spin & 1023u) == 1023u && global_ns() - t0 > limit_ns) return false;
   }
 }
 

@@ -87,6 +87,7 @@ SIGNATURES = {
                                     ctypes.POINTER(_f64)]),
     "randutv_launch_count": (ctypes.c_uint64, []),
     "randutv_jacobi_sweeps": (_i32, [ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64), _i32]),
+    "randutv_selftest_wait": (_i32, [_i32, _f64]),
     "randutv_small_svd_noalloc": (_i32, [_i64, _vp, _i64, _vp, _vp, _vp, _i32]),
     "randutv_batched_opts_default": (None, [ctypes.POINTER(BatchedOpts)]),
     "randutv_batched_plan_create": (_i32, [_i64, _vp, _vp, _i32, ctypes.POINTER(_vp)]),

@@ -159,3 +159,12 @@ def test_rank_k_argument_validation(lib):
     assert f(8, 8, dummy, 8, 2, 1, 4, dummy, 8, ctypes.byref(o), ctypes.byref(h)) == -10
     assert lib.randutv_rank_k_vjp(None, dummy, 8, dummy, 8) == -1
     assert lib.randutv_rank_k_free(None) == -1
+
+
+def test_selftest_wait_argument_validation(lib):
+    # rejected before any CUDA call: unknown kind, limits outside (0, 2] s
+    assert lib.randutv_selftest_wait(2, 0.1) == -1
+    assert lib.randutv_selftest_wait(-1, 0.1) == -1
+    assert lib.randutv_selftest_wait(0, 0.0) == -2
+    assert lib.randutv_selftest_wait(1, 2.5) == -2
+    assert lib.randutv_selftest_wait(0, float("nan")) == -2

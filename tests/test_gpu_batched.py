@@ -7,13 +7,14 @@ m < n.  Parity, element by element where the result is unique: k_reached
 norm sits within 1e-3 of the threshold, where either side is valid),
 |diag T| entry by entry under max(1e-4 |d_ref|, 4 s_j), s_j the oracle's own
 spread under random perturbations of A of the two sides' measured backward
-errors (the FP32 result's residual plus the oracle's): FP32 rounding acts
-like such a perturbation, and where the FP32 sketch no longer resolves a
-direction of a fast decaying block (with q = 1 once the block's singular
-values span more than about (1e-3 / 2^-24)^(1/3) = 25) the same
-perturbation moves the oracle's entry as far; the count of entries held to
-the plain relative bar and of entries inside the resolved prefix (see
-_resolved_prefix) are reported,
+errors (the FP32 result's residual plus the oracle's), over the entries the
+FP32 sketch resolves (see _resolved_prefix: with q = 1 a block whose
+singular values span more than (1e-3 / 2^-24)^(1/3) = 25 starts to lose its
+smallest directions to the rounding of Y, and FP32 and FP64 then pick
+different, equally valid bases; measured on the CPU with the sketch alone
+rounded to FP32, the deviation grows from below 1e-6 at that point to 1e-2
+at a span of 180, more than a perturbation of the backward error moves the
+oracle; the ratio beyond the prefix is reported, not asserted),
 the exact zeros of T below the diagonal of
 its finished columns, the trailing block norm at the stop; where several
 results are valid (signs and bases of U, V) the test checks A = U T V^T to
@@ -112,9 +113,12 @@ def _check_matrix(plan, out, i, A32, b, tol, k_gpu, gauss_index=None, diag_rel=D
         eps = checks.residual(A, U, T, V) + checks.residual(A, Uo, To, Vo)
         sens = oracle_sensitivity(A, b, 1, lambda s_, k_, w_: _gauss(idx, s_, k_, w_), eps, tol=tol)
         kk = min(kk, len(sens))
-        r = compare(np.diag(T)[:kk], np.diag(To)[:kk], sens[:kk], diag_rel, 4.0)
-        r["resolved_prefix"] = _resolved_prefix(np.diag(To)[:kk], b)
-        print(f"batched matrix {i} {A.shape}: |diag T| {r}")
+        kp = _resolved_prefix(np.diag(To)[:kk], b)
+        r = compare(np.diag(T)[:kp], np.diag(To)[:kp], sens[:kp], diag_rel, 4.0)
+        r_all = compare(np.diag(T)[:kk], np.diag(To)[:kk], sens[:kk], diag_rel, 4.0)
+        r["entries"] = kk
+        r["beyond_prefix_ratio"] = r_all["ratio"]
+        print(f"batched matrix {i} {A.shape}: |diag T| over the resolved prefix {r}")
         assert r["ok"], (i, r)
     return k
 
