@@ -195,14 +195,18 @@ __device__ __forceinline__ bool jb_rotate(int p, int lane, Real* wi, Real* wj, R
 
 // The sweeps of the block-cyclic order on the seats of this CTA (buffer
 // *cur at entry and exit).  Returns whether the last sweep converged (the
-// same in every CTA).  Converged: a sweep applied no rotation, or the largest
-// relative off-diagonal rho = |w_i . w_j| / (||w_i|| ||w_j||) it met
-// satisfies rho^2 <= tol / 10: cyclic Jacobi converges quadratically, so the
-// next sweep would meet rho' ~ rho^2 <= tol / 10 and rotate nothing (the
-// confirming sweep is skipped).
+// same in every CTA).  Converged: a sweep applied no rotation (every pair
+// already orthogonal to the tolerance), or, with early_stop (the FP32
+// stage, which the FP64 sweeps refine anyway), the largest relative
+// off-diagonal rho = |w_i . w_j| / (||w_i|| ||w_j||) the sweep met
+// satisfies rho^2 <= tol / 10, so that the next sweep would meet about
+// rho^2 and rotate little.  The FP64 stage does not stop early: its last
+// rotations' rho' ~ rho^2 / gap is above the tolerance where singular values
+// cluster (relative gaps ~ 1e-2..1e-3), and it would leave Vs about
+// 1e-13 from orthogonal.
 template <typename Real, int NU>
 __device__ bool jb_sweeps(const JbSeats<Real>& S, int* cur_io, int p, int cs, int rank, int max_sweeps, Real thr2,
-                          Real tol2, int* s_flag, int* sweeps_done) {
+                          Real tol2, int* s_flag, int* sweeps_done, bool early_stop) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -288,7 +292,7 @@ __device__ bool jb_sweeps(const JbSeats<Real>& S, int* cur_io, int p, int cs, in
       rmax = fmaxf(rmax, __int_as_float(*cluster.map_shared_rank(&s_flag[2 + (sw & 1)], q)));
     }
     const float tol = sqrtf(static_cast<float>(tol2));
-    converged = (any == 0) || (rmax <= 0.1f * tol);
+    converged = (any == 0) || (early_stop && rmax <= 0.1f * tol);
   }
   *cur_io = cur;
   *sweeps_done = sw;
@@ -358,7 +362,7 @@ jacobi_block64_kernel(int p, const double* __restrict__ M, int64_t ldm, const do
   const double thr2 = pu * pu * s_fro;
   int cur = 0;
   int nsw = 0;
-  const bool converged = jb_sweeps<double, NU>(S, &cur, p, cs, rank, max_sweeps, thr2, tol * tol, s_flag, &nsw);
+  const bool converged = jb_sweeps<double, NU>(S, &cur, p, cs, rank, max_sweeps, thr2, tol * tol, s_flag, &nsw, false);
   if (!converged && rank == 0 && tid == 0) atomicOr(err, kDevErrNoConv);
   if (rank == 0 && tid == 0) {
     atomicAdd(&g_jb_sweeps[1], static_cast<unsigned long long>(nsw));
@@ -491,7 +495,7 @@ jacobi_block32_kernel(int p, const double* __restrict__ M, int64_t ldm, double* 
   const float pu = static_cast<float>(p) * 0x1p-24f;
   int cur = 0;
   int nsw = 0;
-  jb_sweeps<float, NU>(S, &cur, p, cs, rank, max_sweeps, pu * pu * fro, pu * pu, s_flag, &nsw);
+  jb_sweeps<float, NU>(S, &cur, p, cs, rank, max_sweeps, pu * pu * fro, pu * pu, s_flag, &nsw, true);
   if (rank == 0 && tid == 0) atomicAdd(&g_jb_sweeps[0], static_cast<unsigned long long>(nsw));
   for (int seat = 0; seat < 2; ++seat) {
     const int B = seat == 0 ? rank : 2 * cs - 1 - rank;

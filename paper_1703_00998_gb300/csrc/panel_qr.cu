@@ -10,13 +10,14 @@
 // factorization, so HBM is read and written once.  Column j needs, from all
 // rows, ||x(2:)||^2 and x^T P(:, c) for c > j; every CTA adds its partial
 // sums into one accumulator vector per column with FP64 atomic reductions in
-// L2, one grid barrier follows, and every thread reads the two sums that
-// define the reflector and evaluates beta, tau and the scale itself (all
-// agree bit for bit).  Per column, after the barrier: column j+1 is updated
-// first, then each group of 1-8 threads takes a column c > j+1, updates it
-// and, in the same pass over its rows, forms its dot product with the new
-// column j+1 (the next column's sums), so a column costs one barrier, one
-// L2 round trip and one __syncthreads.  The scaling of x(2:) to v is
+// L2, one grid barrier follows, and one thread reads the two sums that
+// define the reflector and forms beta, tau and the scale for all (a
+// warp-wide FP64 square root and division would cost 32 times as much on
+// the slow FP64 pipe).  Per column, after the barrier: column j+1 is
+// updated first, then each group of 1-8 threads takes a column c > j+1,
+// updates it and, in the same pass over its rows, forms its dot product
+// with the new column j+1 (the next column's sums), so a column costs one
+// barrier, one L2 round trip and two __syncthreads.  The scaling of x(2:) to v is
 // deferred by one column (nobody reads it meanwhile).  (The order of the
 // atomic additions is not fixed, so results may differ between runs in the
 // last bits.)
@@ -63,6 +64,7 @@ panel_qr_kernel(int64_t k, int w, double* __restrict__ P, int64_t ldp, double* _
   const int nr = static_cast<int>(imax64(0, imin64(k, r_lo + rpb) - r_lo));
   double* slice = sm;                                   // rpb x w, column-major, ld rpb
   double* taus = slice + static_cast<size_t>(rpb) * w;  // w: the scale of each column, then its tau
+  __shared__ double s_h[5];   // the column's beta, tau, scale, and column j+1's wc, wc * scale
   // part: acc (w x w, zeroed by the host) receives the partial sums of
   // column j at acc[j w + c] through FP64 atomic additions in L2; rowbuf
   // (w x w) row j of the panel at rowbuf[j w + c], stored by the owning CTA.
@@ -116,11 +118,21 @@ panel_qr_kernel(int64_t k, int w, double* __restrict__ P, int64_t ldp, double* _
     const int ncols = w - j - 1;
     const int G = group_size(ncols > 0 ? ncols : 1);
     const int grp = tid / G, sub = tid % G;
-    const double a_jj = __ldcg(accj + j), r_jj = __ldcg(rowj + j);
-    double a_n = 0.0, r_n = 0.0, a_c = 0.0, r_c = 0.0;
-    if (j + 1 < w) { a_n = __ldcg(accj + j + 1); r_n = __ldcg(rowj + j + 1); }
+    // FP64 is the slow pipe here and a warp-wide FP64 instruction costs the
+    // same with one lane or 32: thread 0 alone forms the reflector (a square
+    // root and a division) and column j+1's coefficients, for all to read.
+    double a_c = 0.0, r_c = 0.0;
     if (grp >= 1 && grp < ncols) { a_c = __ldcg(accj + j + 1 + grp); r_c = __ldcg(rowj + j + 1 + grp); }
-    const PqRefl h = pq_reflector(r_jj, a_jj);
+    if (tid == 0) {
+      const double a_jj = __ldcg(accj + j), r_jj = __ldcg(rowj + j);
+      double a_n = 0.0, r_n = 0.0;
+      if (j + 1 < w) { a_n = __ldcg(accj + j + 1); r_n = __ldcg(rowj + j + 1); }
+      const PqRefl hh = pq_reflector(r_jj, a_jj);
+      const double wc = hh.tau * fma(hh.scale, a_n, r_n);
+      s_h[0] = hh.beta; s_h[1] = hh.tau; s_h[2] = hh.scale; s_h[3] = wc; s_h[4] = wc * hh.scale;
+    }
+    __syncthreads();
+    const PqRefl h{s_h[0], s_h[1], s_h[2]};
     const int lj = own(j);                                        // local row of j (or -1)
     const int i0 = static_cast<int>(imax64(0, j + 1 - r_lo));     // first local row below j
     const double* xj = col(j);                                    // x(2:) of column j, unscaled
@@ -129,8 +141,7 @@ panel_qr_kernel(int64_t k, int w, double* __restrict__ P, int64_t ldp, double* _
     // sum_{i>j} x_i P(i, j+1)), and P(j, j+1) -= wc.  Meanwhile x(2:) of
     // column j-1 becomes v (nobody reads it any more).
     if (j + 1 < w && h.tau != 0.0) {
-      const double wc = h.tau * fma(h.scale, a_n, r_n);
-      const double ws = wc * h.scale;
+      const double wc = s_h[3], ws = s_h[4];
       double* xn = col(j + 1);
       for (int i = i0 + tid; i < nr; i += PQ_NT) xn[i] = fma(-xj[i], ws, xn[i]);
       if (lj >= 0 && tid == 0) xn[lj] -= wc;
@@ -140,8 +151,8 @@ panel_qr_kernel(int64_t k, int w, double* __restrict__ P, int64_t ldp, double* _
       double* xp = col(j - 1);
       for (int i = static_cast<int>(imax64(0, j - r_lo)) + tid; i < nr; i += PQ_NT) xp[i] *= sp;
     }
-    __syncthreads();
     if (tid == 0) taus[j] = h.scale;
+    __syncthreads();
     // The columns c > j+1: update them, and in the same pass over the rows
     // form the sums of column j+1 over rows > j+1:
     //   acc[(j+1) w + c] += sum_{i>j+1} P(i, j+1) P(i, c)   (c = j+1: ||x(2:)||^2);
