@@ -277,23 +277,44 @@ cudaError_t panel_qr(cudaStream_t s, int64_t k, int w, double* P, int64_t ldp, d
 // Gram(i, l) is read as Gram(l, i): consecutive l across the lanes, one
 // coalesced segment per step instead of 32 scattered lines.
 constexpr int TF_WARPS = 8;
+constexpr int TF_STAGED_MAX_W = 144;   // Gram block staged in shared memory up to this width
 
+// One warp per column c of S; the column's back-substitution is a chain of c
+// dependent steps, so its operands come from shared memory: the CTA first
+// copies tau and, when STAGED, the leading cm x cm block of the Gram matrix
+// that its columns c < cm need (coalesced), instead of an L2 round trip per
+// step.
+template <bool STAGED>
 __global__ void __launch_bounds__(TF_WARPS * 32)
 tfactor_kernel(int w, const double* __restrict__ gram, const double* __restrict__ tau, double* __restrict__ S) {
-  extern __shared__ double scol[];  // TF_WARPS columns of length w
+  extern __shared__ double tsm[];
+  double* scol = tsm;                                   // TF_WARPS columns of length w
+  double* ts = scol + static_cast<size_t>(TF_WARPS) * w;   // tau (w)
+  double* gs = ts + w;                                  // STAGED: Gram(0:cm, 0:cm), ld cm
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cm = min(w, (blockIdx.x + 1) * TF_WARPS);
+  for (int i = threadIdx.x; i < w; i += TF_WARPS * 32) ts[i] = tau[i];
+  if constexpr (STAGED) {
+    for (int i = warp; i < cm; i += TF_WARPS)
+      for (int l = lane; l < cm; l += 32) gs[l + i * cm] = gram[l + static_cast<int64_t>(i) * w];
+  }
+  __syncthreads();
   const int c = blockIdx.x * TF_WARPS + warp;
   if (c >= w) return;
   double* x = scol + static_cast<size_t>(warp) * w;
   for (int i = lane; i < w; i += 32) x[i] = 0.0;
   __syncwarp();
-  if (lane == 0) x[c] = tau[c];
+  if (lane == 0) x[c] = ts[c];
   __syncwarp();
   for (int i = c - 1; i >= 0; --i) {
-    double s = 0.0;
-    for (int l = i + 1 + lane; l <= c; l += 32) s = fma(gram[l + static_cast<int64_t>(i) * w], x[l], s);
-    s = warp_sum(s);
-    if (lane == 0) x[i] = -tau[i] * s;
+    double sum = 0.0;
+    if constexpr (STAGED) {
+      for (int l = i + 1 + lane; l <= c; l += 32) sum = fma(gs[l + i * cm], x[l], sum);
+    } else {
+      for (int l = i + 1 + lane; l <= c; l += 32) sum = fma(gram[l + static_cast<int64_t>(i) * w], x[l], sum);
+    }
+    sum = warp_sum(sum);
+    if (lane == 0) x[i] = -ts[i] * sum;
     __syncwarp();
   }
   for (int i = lane; i < w; i += 32) S[i + static_cast<int64_t>(c) * w] = x[i];
@@ -302,18 +323,26 @@ tfactor_kernel(int w, const double* __restrict__ gram, const double* __restrict_
 cudaError_t tfactor_from_gram(cudaStream_t s, int w, const double* gram, const double* tau, double* S) {
   if (w < 1 || w > 256) return cudaErrorInvalidValue;
   const int blocks = (w + TF_WARPS - 1) / TF_WARPS;
-  const size_t smem = static_cast<size_t>(TF_WARPS) * w * sizeof(double);
-  // the largest block (w = 256) bounds every launch: one attribute per device
+  const bool staged = w <= TF_STAGED_MAX_W;
+  const size_t smem = (static_cast<size_t>(TF_WARPS) * w + w + (staged ? static_cast<size_t>(w) * w : 0)) *
+                      sizeof(double);
+  // the largest launch of each form bounds every other: one attribute per device
   static PerDeviceOnce once;
-  if (smem > 48 * 1024) {
-    cudaError_t e = per_device_once(once, [] {
-      return cudaFuncSetAttribute(tfactor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(static_cast<size_t>(TF_WARPS) * 256 * sizeof(double)));
-    });
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = per_device_once(once, [] {
+    const size_t s1 = (static_cast<size_t>(TF_WARPS) * TF_STAGED_MAX_W + TF_STAGED_MAX_W +
+                       static_cast<size_t>(TF_STAGED_MAX_W) * TF_STAGED_MAX_W) * sizeof(double);
+    const size_t s0 = (static_cast<size_t>(TF_WARPS) * 256 + 256) * sizeof(double);
+    cudaError_t r = cudaFuncSetAttribute(tfactor_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(s1));
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(tfactor_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(s0));
+    return r;
+  });
+  if (e != cudaSuccess) return e;
   const ProfToken tok = prof_begin(s, kProfTfactor);
-  tfactor_kernel<<<blocks, TF_WARPS * 32, smem, s>>>(w, gram, tau, S);
+  if (staged) tfactor_kernel<true><<<blocks, TF_WARPS * 32, smem, s>>>(w, gram, tau, S);
+  else tfactor_kernel<false><<<blocks, TF_WARPS * 32, smem, s>>>(w, gram, tau, S);
   note_launch();
   prof_end(s, tok, w * static_cast<double>(w) * w / 3.0, 8.0 * 2.0 * w * w);
   return cudaGetLastError();
