@@ -163,6 +163,172 @@ __global__ void __launch_bounds__(HR_NT) hqr_reverse_kernel(int L, int w, const 
   }
 }
 
+// The same reverse over a cooperative grid: CTA b owns rows [b rpb, (b+1)
+// rpb) of the panel (rpb a multiple of 32; lane = row within each group of
+// 32, warp = a group of columns), so the FP64 work of a reflector is spread
+// over many SMs (one SM issues ~4 FP64 flop per clock here).  Each reflector
+// needs two sums over all rows: the products v^T P(:, c), v^T Pbar(:, c),
+// v^T v (pass 1) and the dlarfg cotangent's v^T Vbar part (pass 2); each CTA
+// adds its partial sums into `acc` (w x HG_ACC, zeroed by the host) with
+// FP64 atomics, and one bounded grid barrier follows each.  Scalar FP64
+// work (taubar's correction, the dlarfg derivative) runs in one thread and
+// is broadcast through shared memory.
+constexpr int HG_NT = 256;
+constexpr int HG_NW = HG_NT / 32;
+constexpr int HG_ACC = 2 * AD_MAXW + 2;   // per reflector: v^T P, v^T Pbar (w each), v^T v, the Vbar sum
+constexpr int HG_MAX_RPB = 256;
+
+__global__ void __launch_bounds__(HG_NT, 1)
+hqr_reverse_grid_kernel(int L, int w, const double* __restrict__ V, const double* __restrict__ tau,
+                        const double* __restrict__ R, int ldr, double* Vbar, const double* __restrict__ taubar,
+                        double* P, double* Pbar, double* acc, GridBarrier gb, int rpb) {
+  __shared__ double s_wn[AD_MAXW], s_db[AD_MAXW], s_wc[AD_MAXW];
+  __shared__ double s_sc[8];
+  __shared__ double red[HG_NW][HG_MAX_RPB];
+  __shared__ double s_part[HG_NW];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = gridDim.x;
+  const int r_lo = blockIdx.x * rpb;
+  const int nr = max(0, min(L, r_lo + rpb) - r_lo);
+  // the panel after all reflectors is [R; 0]; its cotangent is zero
+  for (int e = tid; e < nr * w; e += HG_NT) {
+    const int r = r_lo + e % nr, c = e / nr;
+    const int64_t o = r + static_cast<int64_t>(c) * L;
+    P[o] = (r <= c && r < w) ? R[r + static_cast<int64_t>(c) * ldr] : 0.0;
+    Pbar[o] = 0.0;
+  }
+  __syncthreads();
+  for (int j = w - 1; j >= 0; --j) {
+    const double t = tau[j], beta = R[j + static_cast<int64_t>(j) * ldr];
+    const double* vj = V + static_cast<int64_t>(j) * L;
+    double* aj = acc + static_cast<int64_t>(j) * HG_ACC;
+    const bool has = r_lo + nr > j;   // this CTA holds rows >= j
+    // pass 1: partial v^T P(:, c), v^T Pbar(:, c) (c > j) and v^T v over rows >= j
+    if (has) {
+      for (int c = j + 1 + warp; c < w; c += HG_NW) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int rl = lane; rl < nr; rl += 32) {
+          const int r = r_lo + rl;
+          if (r < j) continue;
+          const double v = (r == j) ? 1.0 : vj[r];
+          const int64_t o = r + static_cast<int64_t>(c) * L;
+          s1 = fma(v, P[o], s1);
+          s2 = fma(v, Pbar[o], s2);
+        }
+        s1 = wsum(s1);
+        s2 = wsum(s2);
+        if (lane == 0) {
+          atomicAdd(aj + c, s1);
+          atomicAdd(aj + AD_MAXW + c, s2);
+        }
+      }
+      if (warp == HG_NW - 1) {
+        double vv = 0.0;
+        for (int rl = lane; rl < nr; rl += 32) {
+          const int r = r_lo + rl;
+          if (r < j) continue;
+          const double v = (r == j) ? 1.0 : vj[r];
+          vv = fma(v, v, vv);
+        }
+        vv = wsum(vv);
+        if (lane == 0) atomicAdd(aj + 2 * AD_MAXW, vv);
+      }
+    }
+    if (!grid_barrier(gb, nb)) return;
+    if (tid > j && tid < w) {
+      s_wn[tid] = __ldcg(aj + tid);
+      s_db[tid] = __ldcg(aj + AD_MAXW + tid);
+    }
+    if (tid == 0) s_sc[0] = __ldcg(aj + 2 * AD_MAXW);
+    __syncthreads();
+    // w_c = v^T P_c before H_j = v^T P_c after it times (1 - tau v^T v)
+    if (tid > j && tid < w) s_wc[tid] = s_wn[tid] * (1.0 - t * s_sc[0]);
+    if (tid == 0) {
+      const double one = 1.0 - t * s_sc[0];
+      double tb = taubar[j];
+      for (int c = j + 1; c < w; ++c) tb -= s_db[c] * s_wn[c] * one;
+      s_sc[1] = tb;
+    }
+    __syncthreads();
+    // pass 2: the panel before H_j (columns c > j) and its cotangent; each
+    // thread's part of sum_c (Pbar w_c + P_c db_c) per row into red
+    for (int rl = lane; rl < nr; rl += 32) {
+      const int r = r_lo + rl;
+      double sab = 0.0;
+      if (r >= j) {
+        const double v = (r == j) ? 1.0 : vj[r];
+        for (int c = j + 1 + warp; c < w; c += HG_NW) {
+          const int64_t o = r + static_cast<int64_t>(c) * L;
+          const double cn = P[o], cbn = Pbar[o];
+          const double cc = cn - t * v * s_wn[c];
+          sab = fma(cbn, s_wc[c], sab);
+          sab = fma(cc, s_db[c], sab);
+          P[o] = cc;
+          Pbar[o] = cbn - t * v * s_db[c];
+        }
+      }
+      red[warp][rl] = sab;
+    }
+    __syncthreads();
+    double gp = 0.0;
+    for (int rl = tid; rl < nr; rl += HG_NT) {
+      const int r = r_lo + rl;
+      if (r > j) {
+        double sab = 0.0;
+#pragma unroll
+        for (int g = 0; g < HG_NW; ++g) sab += red[g][rl];
+        const int64_t o = r + static_cast<int64_t>(j) * L;
+        const double vb = Vbar[o] - t * sab;
+        Vbar[o] = vb;
+        gp = fma(vb, -t * beta * vj[r], gp);      // vb_r x_r with x_r = -tau beta v_r
+      }
+    }
+    gp = wsum(gp);
+    if (lane == 0) s_part[warp] = gp;
+    __syncthreads();
+    if (tid == 0 && has) {
+      double g = 0.0;
+      for (int i = 0; i < HG_NW; ++i) g += s_part[i];
+      atomicAdd(aj + 2 * AD_MAXW + 1, g);
+    }
+    if (!grid_barrier(gb, nb)) return;
+    // dlarfg derivative: x = beta (e_0 - tau v), alpha = beta (1 - tau)
+    if (tid == 0) {
+      const double gsum = __ldcg(aj + 2 * AD_MAXW + 1);
+      const double tb = s_sc[1];
+      const double alpha = beta * (1.0 - t);
+      const double nu = fabs(beta), sg = copysign(1.0, alpha);
+      double ab = 0.0, nub = 0.0, inv_ab = 0.0;
+      if (t != 0.0) {
+        inv_ab = 1.0 / (alpha - beta);
+        const double gg = -gsum * inv_ab * inv_ab;
+        const double bb = -gg + tb * alpha / (beta * beta);
+        nub = -sg * bb;
+        ab = gg - tb / beta + nub * alpha / nu;
+      }
+      s_sc[2] = ab;
+      s_sc[3] = inv_ab;
+      s_sc[4] = (t != 0.0) ? nub / nu : 0.0;
+      s_sc[5] = alpha;
+    }
+    __syncthreads();
+    for (int rl = tid; rl < nr; rl += HG_NT) {
+      const int r = r_lo + rl;
+      if (r < j) continue;
+      const int64_t o = r + static_cast<int64_t>(j) * L;
+      if (r == j) {
+        Pbar[o] = s_sc[2];
+        P[o] = s_sc[5];
+      } else {
+        const double x = -t * beta * vj[r];
+        Pbar[o] = (t != 0.0) ? Vbar[o] * s_sc[3] + s_sc[4] * x : 0.0;
+        P[o] = x;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // b x b part of the compact-WY adjoint (one CTA of 32 x 32 threads): from
 // VtQV = V^T Qbar V, S and tau, Nsym = N + N^T with N = striu(Mbar), Mbar =
 // triu(-S^T Sbar S^T), Sbar = triu(-VtQV), and taubar = -diag(Mbar) / tau^2.
@@ -227,6 +393,7 @@ struct randutv_rank_k_state {
   double *work = nullptr, *gram = nullptr, *pq = nullptr, *c1 = nullptr, *c2 = nullptr, *c3 = nullptr,
          *c4 = nullptr, *big1 = nullptr, *big2 = nullptr, *Tbar = nullptr, *Ubar = nullptr, *vbar = nullptr,
          *nsym = nullptr, *taub = nullptr, *pbar = nullptr, *pwork = nullptr;
+  double* hacc = nullptr;               // sums of the grid QR reverse (AD_MAXW x (2 AD_MAXW + 2))
   int64_t work_elems = 0;
   unsigned* flags = nullptr;
 };
@@ -288,9 +455,27 @@ cudaError_t wy_adjoint(State& S, cudaStream_t s, int64_t L, int w, const double*
 // Reverse of the Householder QR: S.vbar, S.taub -> Pbar (L x w, ld L).
 cudaError_t qr_reverse(State& S, cudaStream_t s, int64_t L, int w, const double* V, const double* tau, const double* R,
                        double* Pbar) {
-  hqr_reverse_kernel<<<1, HR_NT, 0, s>>>(static_cast<int>(L), w, V, tau, R, w, S.vbar, S.taub, S.pwork, Pbar);
+  // rows per CTA: a multiple of 32 with the grid within one wave of the SMs
+  int rpb = 32;
+  while (static_cast<int64_t>(rpb) * (kNumSMs - 4) < L && rpb < HG_MAX_RPB) rpb += 32;
+  const int nb = static_cast<int>((L + rpb - 1) / rpb);
+  if (static_cast<int64_t>(rpb) * nb < L || nb > kNumSMs) {
+    // too tall for one wave of row blocks: the one-CTA form
+    hqr_reverse_kernel<<<1, HR_NT, 0, s>>>(static_cast<int>(L), w, V, tau, R, w, S.vbar, S.taub, S.pwork, Pbar);
+    note_launch();
+    return cudaGetLastError();
+  }
+  AD_CK(cudaMemsetAsync(S.hacc, 0, sizeof(double) * AD_MAXW * HG_ACC, s));
+  AD_CK(cudaMemsetAsync(S.flags, 0, 2 * sizeof(unsigned), s));
+  GridBarrier gb{S.flags, S.flags + 1, reinterpret_cast<int*>(S.flags + 2)};
+  int Li = static_cast<int>(L), ldr = w;
+  const double* taub = S.taub;
+  double *vbar = S.vbar, *pw = S.pwork, *acc = S.hacc;
+  void* args[] = {&Li, &w, &V, &tau, &R, &ldr, &vbar, &taub, &pw, &Pbar, &acc, &gb, &rpb};
+  cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(hqr_reverse_grid_kernel), dim3(nb),
+                                              dim3(HG_NT), args, 0, s);
   note_launch();
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t add(cudaStream_t s, int64_t m, int64_t n, const double* X, int64_t ldx, double* Y, int64_t ldy) {
@@ -510,6 +695,7 @@ int randutv_rank_k(int64_t m, int64_t n, const double* A, int64_t lda, int b, in
   items.push_back({&S->Ubar, m * m});
   items.push_back({&S->nsym, b * b});
   items.push_back({&S->taub, b});
+  items.push_back({&S->hacc, 32 * 66});
   size_t total = 0;
   for (auto& it : items) total += (static_cast<size_t>(it.second) * sizeof(double) + 255) & ~static_cast<size_t>(255);
   total += 256;
@@ -554,8 +740,12 @@ int randutv_rank_k_vjp(randutv_rank_k_state* state, const double* Fbar, int64_t 
   if (ldab < state->m) return -5;
   cudaStream_t s = current_stream();
   cudaError_t e = reverse(*state, s, Fbar, ldfb, Abar, ldab);
+  unsigned herr[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(herr, state->flags, sizeof(herr), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  return ad_status(e, "randutv_rank_k_vjp");
+  const int st = ad_status(e, "randutv_rank_k_vjp");
+  if (st == RANDUTV_OK && (herr[2] & kDevErrTimeout)) return RANDUTV_ETIMEOUT;
+  return st;
 }
 
 int randutv_rank_k_free(randutv_rank_k_state* state) {
