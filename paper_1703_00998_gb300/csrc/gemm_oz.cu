@@ -228,6 +228,7 @@ constexpr int OX_A_BYTES = OZ_BM * OZ_KB * 2;             // 16 KB: one A slice,
 constexpr int OX_BST = 2;                                 // B ring stages
 constexpr int OX_TILE = OZ_BM * 64;                       // outputs of the largest tile (128 x 64)
 constexpr int OX_SPLIT_TILES = 2 * kNumSMs;               // tiles whose K range may be split between CTAs
+constexpr int kOzWaveCTAs = kNumSMs - 16;                 // CTAs of a one-wave (stream-K) launch
 
 // Tile shapes of the FP64 kernel: 128 x BN outputs.  BN = 64 with 8 epilogue
 // warps (32 columns each) for long K, where the products dominate and the
@@ -1068,8 +1069,10 @@ cudaError_t ozx_run(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int6
     const int64_t W = static_cast<int64_t>(p.ntiles) * L.nch;
     int64_t grid;
     if (L.nch >= 2 && p.ntiles <= OX_SPLIT_TILES && p.ntiles < 2 * kNumSMs) {
-      // few tiles, long K: the (tile, chunk) units spread evenly over one wave, tiles split between CTAs
-      grid = std::min<int64_t>(W, kNumSMs);
+      // few tiles, long K: the (tile, chunk) units spread evenly over one wave, tiles split between CTAs.
+      // The wave is 136 CTAs, not 152: the factorization's small SVD holds a 16-CTA cluster for
+      // milliseconds on its own lane, and a one-wave kernel with CTAs left over would wait for it.
+      grid = std::min<int64_t>(W, kOzWaveCTAs);
       p.upc = static_cast<int>((W + grid - 1) / grid);
     } else {
       // whole tiles per CTA, up to 8, in as few waves as that allows
