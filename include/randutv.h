@@ -437,7 +437,9 @@ int randutv_batched_gaussian(uint64_t seed, int64_t index, int64_t step, int64_t
  * for any number of cotangents Fbar (m x n, ld ldfb); randutv_rank_k_free
  * releases the state.  A state serves one call at a time (its scratch is
  * reused by every randutv_rank_k_vjp).  b <= 32 (EUNSUPPORTED above; also
- * when k >= min(m, n)); opts->p must be 0. */
+ * when k >= min(m, n)); opts->p must be 0.  The large products of both
+ * passes use the Ozaki-scheme GEMM when opts->fp64_emulation is set (the
+ * default; its workspace is part of the state), else FP64 DFMA. */
 typedef struct randutv_rank_k_state randutv_rank_k_state;
 
 int randutv_rank_k(int64_t m, int64_t n, const double* A, int64_t lda, int b, int q, int64_t k,

@@ -394,6 +394,8 @@ struct randutv_rank_k_state {
          *c4 = nullptr, *big1 = nullptr, *big2 = nullptr, *Tbar = nullptr, *Ubar = nullptr, *vbar = nullptr,
          *nsym = nullptr, *taub = nullptr, *pbar = nullptr, *pwork = nullptr;
   double* hacc = nullptr;               // sums of the grid QR reverse (AD_MAXW x (2 AD_MAXW + 2))
+  double* oz = nullptr;                 // Ozaki-scheme GEMM workspace (null: every product on DFMA)
+  size_t ozb = 0;
   int64_t work_elems = 0;
   unsigned* flags = nullptr;
 };
@@ -409,8 +411,14 @@ using State = randutv_rank_k_state;
     if (e_ != cudaSuccess) return e_;                            \
   } while (0)
 
+// The products go through the Ozaki-scheme GEMM (FP64-accurate, BF16 tensor
+// cores) when the options ask for it and the product fills its tiles, else
+// through the FP64 DFMA GEMM, as in the factorization.
 cudaError_t g64(State& S, cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
                 const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc) {
+  if (S.oz && m >= 64 && n >= 32 && k >= 32 && gemm_oz_work_bytes(m, n, k) <= S.ozb)
+    return gemm_oz(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, S.oz, S.ozb,
+                   reinterpret_cast<int*>(S.flags + 2));
   return gemm_f64(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, S.work, S.work_elems);
 }
 
@@ -696,6 +704,12 @@ int randutv_rank_k(int64_t m, int64_t n, const double* A, int64_t lda, int b, in
   items.push_back({&S->nsym, b * b});
   items.push_back({&S->taub, b});
   items.push_back({&S->hacc, 32 * 66});
+  if (o.fp64_emulation && gemm_oz_supported()) {
+    // the largest products: m x n x k (the first forward product), mx x mx x b and thin mx x b x mx
+    S->ozb = std::max({gemm_oz_work_bytes(m, n, std::max<int64_t>(m, k)), gemm_oz_work_bytes(mx, mx, b),
+                       gemm_oz_work_bytes(mx, b, mx), gemm_oz_work_bytes(b, mx, mx), gemm_oz_work_bytes(mx, mx, mx)});
+    items.push_back({&S->oz, static_cast<int64_t>((S->ozb + 7) / 8)});
+  }
   size_t total = 0;
   for (auto& it : items) total += (static_cast<size_t>(it.second) * sizeof(double) + 255) & ~static_cast<size_t>(255);
   total += 256;
@@ -712,6 +726,7 @@ int randutv_rank_k(int64_t m, int64_t n, const double* A, int64_t lda, int b, in
   }
   S->flags = reinterpret_cast<unsigned*>(p);
   e = cudaMemsetAsync(S->flags, 0, 256, s);
+  if (e == cudaSuccess && S->oz) e = cudaMemsetAsync(S->oz, 0, gemm_oz_head_bytes(), s);   // split-tile head
   S->seed = o.seed;
   if (e == cudaSuccess && o.g_inject)
     e = cudaMemcpyAsync(S->gin, o.g_inject, sizeof(double) * gtot, cudaMemcpyDeviceToDevice, s);

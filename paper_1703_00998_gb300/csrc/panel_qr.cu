@@ -277,27 +277,66 @@ cudaError_t panel_qr(cudaStream_t s, int64_t k, int w, double* P, int64_t ldp, d
 // Gram(i, l) is read as Gram(l, i): consecutive l across the lanes, one
 // coalesced segment per step instead of 32 scattered lines.
 constexpr int TF_WARPS = 8;
-constexpr int TF_STAGED_MAX_W = 144;   // Gram block staged in shared memory up to this width
+constexpr int TF_STAGED_MAX_W = 128;   // the right-looking form below, up to this width
+constexpr int TF_RL_WARPS = 4;         // one warp per SMSP: a warp alone on its FP64 pipe
 
-// One warp per column c of S; the column's back-substitution is a chain of c
-// dependent steps, so its operands come from shared memory: the CTA first
-// copies tau and, when STAGED, the leading cm x cm block of the Gram matrix
-// that its columns c < cm need (coalesced), instead of an L2 round trip per
-// step.
-template <bool STAGED>
+// Right-looking back-substitution for column c of S, one warp per column
+// and one warp per SMSP (FP64 issues at 0.5 lanes per clock per SMSP, so a
+// warp-wide FP64 instruction takes 64 cycles and a second warp on the SMSP
+// would halve the rate).  With x_c = tau_c, for l = c, c-1, .., 1: every
+// lane adds Gram(i, l) x_l into its partial sums acc_i (i < l, lane i mod
+// 32, at most 4 per lane), and the owner of i = l-1 forms x_{l-1} = -tau_{l-1}
+// acc_{l-1}: a chain of one FMA, one multiply and a shared-memory broadcast
+// per step, instead of a 5-step warp reduction in FP64.  The Gram block the
+// CTA's columns need (Gram(0:cm, 0:cm), column-major, read down columns) and
+// tau are staged in shared memory first.
+__global__ void __launch_bounds__(TF_RL_WARPS * 32)
+tfactor_rl_kernel(int w, const double* __restrict__ gram, const double* __restrict__ tau, double* __restrict__ S) {
+  extern __shared__ double tsm[];
+  double* ts = tsm;                                   // tau (w)
+  double* xs = ts + w;                                // TF_RL_WARPS columns of x (w each)
+  double* gs = xs + static_cast<size_t>(TF_RL_WARPS) * w;   // Gram(0:cm, 0:cm), ld cm
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cm = min(w, (blockIdx.x + 1) * TF_RL_WARPS);
+  for (int i = threadIdx.x; i < w; i += TF_RL_WARPS * 32) ts[i] = tau[i];
+  for (int l = warp; l < cm; l += TF_RL_WARPS)
+    for (int i = lane; i < cm; i += 32) gs[i + l * cm] = gram[i + static_cast<int64_t>(l) * w];
+  __syncthreads();
+  const int c = blockIdx.x * TF_RL_WARPS + warp;
+  if (c >= w) return;
+  double* x = xs + static_cast<size_t>(warp) * w;
+  double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;   // i = lane + 32 k, k = 0..3
+  if (lane == 0) x[c] = ts[c];
+  __syncwarp();
+  for (int l = c; l >= 1; --l) {
+    const double xl = x[l];
+    const double* gl = gs + l * cm;
+    // rows i < l; the k-th block of 32 rows takes part while 32 k < l
+    if (lane < l) acc0 = fma(gl[lane], xl, acc0);
+    if (l > 32 && lane + 32 < l) acc1 = fma(gl[lane + 32], xl, acc1);
+    if (l > 64 && lane + 64 < l) acc2 = fma(gl[lane + 64], xl, acc2);
+    if (l > 96 && lane + 96 < l) acc3 = fma(gl[lane + 96], xl, acc3);
+    const int i = l - 1;
+    if (lane == (i & 31)) {
+      const int k = i >> 5;
+      const double a = k == 0 ? acc0 : (k == 1 ? acc1 : (k == 2 ? acc2 : acc3));
+      x[i] = -ts[i] * a;
+    }
+    __syncwarp();
+  }
+  for (int i = lane; i < w; i += 32) S[i + static_cast<int64_t>(c) * w] = (i <= c) ? x[i] : 0.0;
+}
+
+// The same column by column as a left-looking solve (one warp reduction per
+// step) for wider blocks: x_i = -tau_i sum_{l=i+1..c} Gram(l, i) x_l, with
+// Gram(l, i) read down the lower triangle (coalesced).
 __global__ void __launch_bounds__(TF_WARPS * 32)
 tfactor_kernel(int w, const double* __restrict__ gram, const double* __restrict__ tau, double* __restrict__ S) {
   extern __shared__ double tsm[];
   double* scol = tsm;                                   // TF_WARPS columns of length w
   double* ts = scol + static_cast<size_t>(TF_WARPS) * w;   // tau (w)
-  double* gs = ts + w;                                  // STAGED: Gram(0:cm, 0:cm), ld cm
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int cm = min(w, (blockIdx.x + 1) * TF_WARPS);
   for (int i = threadIdx.x; i < w; i += TF_WARPS * 32) ts[i] = tau[i];
-  if constexpr (STAGED) {
-    for (int i = warp; i < cm; i += TF_WARPS)
-      for (int l = lane; l < cm; l += 32) gs[l + i * cm] = gram[l + static_cast<int64_t>(i) * w];
-  }
   __syncthreads();
   const int c = blockIdx.x * TF_WARPS + warp;
   if (c >= w) return;
@@ -308,11 +347,7 @@ tfactor_kernel(int w, const double* __restrict__ gram, const double* __restrict_
   __syncwarp();
   for (int i = c - 1; i >= 0; --i) {
     double sum = 0.0;
-    if constexpr (STAGED) {
-      for (int l = i + 1 + lane; l <= c; l += 32) sum = fma(gs[l + i * cm], x[l], sum);
-    } else {
-      for (int l = i + 1 + lane; l <= c; l += 32) sum = fma(gram[l + static_cast<int64_t>(i) * w], x[l], sum);
-    }
+    for (int l = i + 1 + lane; l <= c; l += 32) sum = fma(gram[l + static_cast<int64_t>(i) * w], x[l], sum);
     sum = warp_sum(sum);
     if (lane == 0) x[i] = -ts[i] * sum;
     __syncwarp();
@@ -322,27 +357,28 @@ tfactor_kernel(int w, const double* __restrict__ gram, const double* __restrict_
 
 cudaError_t tfactor_from_gram(cudaStream_t s, int w, const double* gram, const double* tau, double* S) {
   if (w < 1 || w > 256) return cudaErrorInvalidValue;
-  const int blocks = (w + TF_WARPS - 1) / TF_WARPS;
-  const bool staged = w <= TF_STAGED_MAX_W;
-  const size_t smem = (static_cast<size_t>(TF_WARPS) * w + w + (staged ? static_cast<size_t>(w) * w : 0)) *
-                      sizeof(double);
-  // the largest launch of each form bounds every other: one attribute per device
   static PerDeviceOnce once;
   cudaError_t e = per_device_once(once, [] {
-    const size_t s1 = (static_cast<size_t>(TF_WARPS) * TF_STAGED_MAX_W + TF_STAGED_MAX_W +
+    const size_t s1 = (static_cast<size_t>(TF_STAGED_MAX_W) * (1 + TF_RL_WARPS) +
                        static_cast<size_t>(TF_STAGED_MAX_W) * TF_STAGED_MAX_W) * sizeof(double);
     const size_t s0 = (static_cast<size_t>(TF_WARPS) * 256 + 256) * sizeof(double);
-    cudaError_t r = cudaFuncSetAttribute(tfactor_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t r = cudaFuncSetAttribute(tfactor_rl_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(s1));
     if (r == cudaSuccess)
-      r = cudaFuncSetAttribute(tfactor_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               static_cast<int>(s0));
+      r = cudaFuncSetAttribute(tfactor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(s0));
     return r;
   });
   if (e != cudaSuccess) return e;
   const ProfToken tok = prof_begin(s, kProfTfactor);
-  if (staged) tfactor_kernel<true><<<blocks, TF_WARPS * 32, smem, s>>>(w, gram, tau, S);
-  else tfactor_kernel<false><<<blocks, TF_WARPS * 32, smem, s>>>(w, gram, tau, S);
+  if (w <= TF_STAGED_MAX_W) {
+    const int blocks = (w + TF_RL_WARPS - 1) / TF_RL_WARPS;
+    const size_t smem = (static_cast<size_t>(w) * (1 + TF_RL_WARPS) + static_cast<size_t>(w) * w) * sizeof(double);
+    tfactor_rl_kernel<<<blocks, TF_RL_WARPS * 32, smem, s>>>(w, gram, tau, S);
+  } else {
+    const int blocks = (w + TF_WARPS - 1) / TF_WARPS;
+    const size_t smem = (static_cast<size_t>(TF_WARPS) * w + w) * sizeof(double);
+    tfactor_kernel<<<blocks, TF_WARPS * 32, smem, s>>>(w, gram, tau, S);
+  }
   note_launch();
   prof_end(s, tok, w * static_cast<double>(w) * w / 3.0, 8.0 * 2.0 * w * w);
   return cudaGetLastError();
