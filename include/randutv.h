@@ -430,9 +430,10 @@ int randutv_batched_gaussian(uint64_t seed, int64_t index, int64_t step, int64_t
  *
  * randutv_rank_k writes A_k (m x n, ld ldf, device) and, when state is
  * non-NULL, keeps on the device what the reverse pass needs: T and U as
- * they enter each step (m n + m^2 doubles per step) and a copy of the
- * injected Gaussians; the reverse pass forms each step's sketch,
- * reflectors and WY factors again from them;
+ * they enter each step (m n + m^2 doubles per step), each step's Gaussian,
+ * sketches, reflectors and WY factors (about (q + 4) max(m, n) b doubles
+ * per step) and a copy of the injected Gaussians; the reverse pass forms
+ * the T between each step's two block-reflector applications again;
  * randutv_rank_k_vjp then writes Abar = (dA_k/dA)^T Fbar (m x n, ld ldab)
  * for any number of cotangents Fbar (m x n, ld ldfb); randutv_rank_k_free
  * releases the state.  A state serves one call at a time (its scratch is

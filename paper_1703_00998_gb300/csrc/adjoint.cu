@@ -15,9 +15,10 @@
 // then step by step backwards through the two block-reflector applications
 // (Q = I - V S V^T: Cbar <- Cbar Q^T or Q Cbar, and the products Qbar V,
 // Qbar^T V formed from thin factors; each step's Gaussian, sketches,
-// reflectors, WY factors and intermediate T are formed again from the
-// step's checkpointed T and U when the reverse pass reaches it, instead of
-// being stored), the compact-WY factor (S^-1 =
+// reflectors and WY factors are kept from the forward pass, O((m + n) b)
+// per step, and the T between the step's two applications is formed again
+// from the step's checkpointed T when the reverse pass reaches it, instead
+// of being stored), the compact-WY factor (S^-1 =
 // striu(V^T V) + diag(1/tau): Sbar = triu(-V^T Qbar V), Mbar = triu(-S^T
 // Sbar S^T), Vbar += V (N + N^T) with N = striu(Mbar), taubar = -diag(Mbar)
 // / tau^2), the Householder QR reflector by reflector (the intermediate
@@ -383,12 +384,14 @@ struct randutv_rank_k_state {
     double *Tprev, *Uprev;
   };
   std::vector<Step> st;
-  // one step's factors, formed in the forward and formed again from the
-  // checkpoint when the reverse pass reaches the step
+  // each step's factors, kept from the forward (O((m + n) b) per step); the
+  // reverse pass forms T after the step's right application again from the
+  // checkpoint (one block-reflector application) instead of storing it
   struct Factors {
-    double *T1, *G, *Ys, *Zs, *Vv, *tv, *Rv, *Sv, *Vu, *tu, *Ru, *Su;
-  } f;
-  double *recT = nullptr, *recU = nullptr;   // the step's T and U while its factors are formed again
+    double *G, *Ys, *Zs, *Vv, *tv, *Rv, *Sv, *Vu, *tu, *Ru, *Su;
+  };
+  std::vector<Factors> fs;
+  double* recT = nullptr;                // the step's T after its right application, formed again
   // scratch
   double *work = nullptr, *gram = nullptr, *pq = nullptr, *c1 = nullptr, *c2 = nullptr, *c3 = nullptr,
          *c4 = nullptr, *big1 = nullptr, *big2 = nullptr, *Tbar = nullptr, *Ubar = nullptr, *vbar = nullptr,
@@ -495,12 +498,11 @@ cudaError_t add(cudaStream_t s, int64_t m, int64_t n, const double* X, int64_t l
 }
 
 // Step i of the map on T (m x n) and U (m x m), both in place; the step's
-// Gaussian, sketches, reflectors, factors and T after the right application
-// go to S.f.
+// Gaussian, sketches, reflectors and factors go to S.fs[i - 1].
 cudaError_t step_forward(State& S, cudaStream_t s, int i, double* T, double* U) {
   const int64_t m = S.m, n = S.n;
   const int b = S.b, q = S.q;
-  auto& P = S.f;
+  auto& P = S.fs[i - 1];
   const int64_t r0 = static_cast<int64_t>(b) * (i - 1), kr = m - r0, kc = n - r0;
   if (S.gin) {
     int64_t goff = 0;
@@ -519,7 +521,6 @@ cudaError_t step_forward(State& S, cudaStream_t s, int i, double* T, double* U) 
   }
   AD_CK(qr_panel(S, s, kc, b, P.Ys + q * kc * b, kc, P.Vv, P.tv, P.Rv, P.Sv));
   AD_CK(wy_apply(S, s, true, false, m, kc, b, P.Vv, P.Sv, T + r0 * m, m));
-  AD_CK(copy_matrix(s, m, n, T, m, P.T1, m));
   AD_CK(qr_panel(S, s, kr, b, T + r0 + r0 * m, m, P.Vu, P.tu, P.Ru, P.Su));
   AD_CK(wy_apply(S, s, true, false, m, kr, b, P.Vu, P.Su, U + r0 * m, m));
   return wy_apply(S, s, false, false, kc, kr, b, P.Vu, P.Su, T + r0 + r0 * m, m);
@@ -555,11 +556,14 @@ cudaError_t reverse(State& S, cudaStream_t s, const double* Fb, int64_t ldfb, do
   AD_CK(g64(S, s, false, false, m, k, n, 1.0, S.A, m, S.big2, n, 1.0, Ub, m));
   AD_CK(cudaMemsetAsync(Tb, 0, sizeof(double) * m * n, s));
   for (int i = S.s; i >= 1; --i) {
-    // the step's factors again, from its checkpoint (per-block recomputation)
-    AD_CK(copy_matrix(s, m, n, S.st[i - 1].Tprev, m, S.recT, m));
-    AD_CK(copy_matrix(s, m, m, S.st[i - 1].Uprev, m, S.recU, m));
-    AD_CK(step_forward(S, s, i, S.recT, S.recU));
-    const auto& P = S.f;
+    // the step's factors from the forward; T after its right application
+    // formed again from the checkpoint (bit for bit: the same products)
+    const auto& P = S.fs[i - 1];
+    {
+      const int64_t kc0 = n - static_cast<int64_t>(b) * (i - 1);
+      AD_CK(copy_matrix(s, m, n, S.st[i - 1].Tprev, m, S.recT, m));
+      AD_CK(wy_apply(S, s, true, false, m, kc0, b, P.Vv, P.Sv, S.recT + static_cast<int64_t>(b) * (i - 1) * m, m));
+    }
     const double* Tprev = S.st[i - 1].Tprev;
     const double* Uprev = S.st[i - 1].Uprev;
     const int64_t r0 = static_cast<int64_t>(b) * (i - 1), kr = m - r0, kc = n - r0;
@@ -567,7 +571,7 @@ cudaError_t reverse(State& S, cudaStream_t s, const double* Fb, int64_t ldfb, do
     AD_CK(copy_matrix(s, kr, kc, Tb + r0 + r0 * m, m, T2b, kr));
     double* Ubb = S.big1;                                 // Ubar(:, r0:) after the step (m x kr, ld m)
     AD_CK(copy_matrix(s, m, kr, Ub + r0 * m, m, Ubb, m));
-    const double* T1b = P.T1 + r0 + r0 * m;               // T(r0:, r0:) before the left application
+    const double* T1b = S.recT + r0 + r0 * m;             // T(r0:, r0:) before the left application
     const double* Uo = Uprev + r0 * m;                    // U(:, r0:) before the right application
     // (left application of Qu^T to T and right application of Qu to U)
     AD_CK(wy_apply(S, s, false, true, kc, kr, b, P.Vu, P.Su, Tb + r0 + r0 * m, m));   // Qu Tbar_blk
@@ -674,22 +678,23 @@ int randutv_rank_k(int64_t m, int64_t n, const double* A, int64_t lda, int b, in
     items.push_back({&S->st[i].Tprev, m * n});
     items.push_back({&S->st[i].Uprev, m * m});
   }
-  // factors of one step, sized for the first (largest) one
-  auto& P = S->f;
-  items.push_back({&P.T1, m * n});
-  items.push_back({&P.G, m * b});
-  items.push_back({&P.Ys, (q + 1) * n * b});
-  items.push_back({&P.Zs, std::max<int64_t>(1, q * m * b)});
-  items.push_back({&P.Vv, n * b});
-  items.push_back({&P.tv, b});
-  items.push_back({&P.Rv, b * b});
-  items.push_back({&P.Sv, b * b});
-  items.push_back({&P.Vu, m * b});
-  items.push_back({&P.tu, b});
-  items.push_back({&P.Ru, b * b});
-  items.push_back({&P.Su, b * b});
+  // every step's factors, each sized for the first (largest) step
+  S->fs.resize(S->s);
+  for (int i = 0; i < S->s; ++i) {
+    auto& P = S->fs[i];
+    items.push_back({&P.G, m * b});
+    items.push_back({&P.Ys, (q + 1) * n * b});
+    items.push_back({&P.Zs, std::max<int64_t>(1, q * m * b)});
+    items.push_back({&P.Vv, n * b});
+    items.push_back({&P.tv, b});
+    items.push_back({&P.Rv, b * b});
+    items.push_back({&P.Sv, b * b});
+    items.push_back({&P.Vu, m * b});
+    items.push_back({&P.tu, b});
+    items.push_back({&P.Ru, b * b});
+    items.push_back({&P.Su, b * b});
+  }
   items.push_back({&S->recT, m * n});
-  items.push_back({&S->recU, m * m});
   int64_t gtot = 0;
   for (int i = 0; i < S->s; ++i) gtot += (m - static_cast<int64_t>(b) * i) * b;
   if (o.g_inject) items.push_back({&S->gin, gtot});
