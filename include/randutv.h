@@ -429,11 +429,11 @@ int randutv_batched_gaussian(uint64_t seed, int64_t index, int64_t step, int64_t
  * steps), so A_k is a smooth function of A at fixed G.
  *
  * randutv_rank_k writes A_k (m x n, ld ldf, device) and, when state is
- * non-NULL, keeps on the device what the reverse pass needs: T and U as
- * they enter each step (m n + m^2 doubles per step), each step's Gaussian,
- * sketches, reflectors and WY factors (about (q + 4) max(m, n) b doubles
- * per step) and a copy of the injected Gaussians; the reverse pass forms
- * the T between each step's two block-reflector applications again;
+ * non-NULL, keeps on the device what the reverse pass needs: A, the final
+ * T and U, each step's Gaussian, sketches, reflectors and WY factors (about
+ * (q + 4) max(m, n) b doubles per step) and a copy of the injected
+ * Gaussians; the reverse pass walks T and U back step by step with the
+ * kept reflectors (no per-step copies of T or U);
  * randutv_rank_k_vjp then writes Abar = (dA_k/dA)^T Fbar (m x n, ld ldab)
  * for any number of cotangents Fbar (m x n, ld ldfb); randutv_rank_k_free
  * releases the state.  A state serves one call at a time (its scratch is

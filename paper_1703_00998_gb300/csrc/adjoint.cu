@@ -16,9 +16,10 @@
 // (Q = I - V S V^T: Cbar <- Cbar Q^T or Q Cbar, and the products Qbar V,
 // Qbar^T V formed from thin factors; each step's Gaussian, sketches,
 // reflectors and WY factors are kept from the forward pass, O((m + n) b)
-// per step, and the T between the step's two applications is formed again
-// from the step's checkpointed T when the reverse pass reaches it, instead
-// of being stored), the compact-WY factor (S^-1 =
+// per step, and T and U entering each step, and T between its two
+// applications, are walked back from the final T and U with those
+// reflectors when the reverse pass reaches the step, instead of being
+// stored), the compact-WY factor (S^-1 =
 // striu(V^T V) + diag(1/tau): Sbar = triu(-V^T Qbar V), Mbar = triu(-S^T
 // Sbar S^T), Vbar += V (N + N^T) with N = striu(Mbar), taubar = -diag(Mbar)
 // / tau^2), the Householder QR reflector by reflector (the intermediate
@@ -242,13 +243,15 @@ hqr_reverse_grid_kernel(int L, int w, const double* __restrict__ V, const double
     }
     if (tid == 0) s_sc[0] = __ldcg(aj + 2 * AD_MAXW);
     __syncthreads();
-    // w_c = v^T P_c before H_j = v^T P_c after it times (1 - tau v^T v)
+    // w_c = v^T P_c before H_j = v^T P_c after it times (1 - tau v^T v);
+    // taubar_j - sum_c db_c w_c by one warp (a chain of FP64 steps in one
+    // thread would cost 64 cycles of the FP64 pipe per step)
     if (tid > j && tid < w) s_wc[tid] = s_wn[tid] * (1.0 - t * s_sc[0]);
-    if (tid == 0) {
+    if (warp == 0) {
       const double one = 1.0 - t * s_sc[0];
-      double tb = taubar[j];
-      for (int c = j + 1; c < w; ++c) tb -= s_db[c] * s_wn[c] * one;
-      s_sc[1] = tb;
+      double d = (lane > j && lane < w) ? s_db[lane] * s_wn[lane] * one : 0.0;
+      d = wsum(d);
+      if (lane == 0) s_sc[1] = taubar[j] - d;
     }
     __syncthreads();
     // pass 2: the panel before H_j (columns c > j) and its cotangent; each
@@ -379,11 +382,7 @@ struct randutv_rank_k_state {
   uint64_t seed = 0;
   double *A = nullptr, *U = nullptr, *W = nullptr;
   double* gin = nullptr;                // copy of the injected Gaussian streams (or null: drawn from seed)
-  // checkpoints: T and U before each step
-  struct Step {
-    double *Tprev, *Uprev;
-  };
-  std::vector<Step> st;
+  double* Tfin = nullptr;                // T after the last step of the forward pass
   // each step's factors, kept from the forward (O((m + n) b) per step); the
   // reverse pass forms T after the step's right application again from the
   // checkpoint (one block-reflector application) instead of storing it
@@ -391,7 +390,10 @@ struct randutv_rank_k_state {
     double *G, *Ys, *Zs, *Vv, *tv, *Rv, *Sv, *Vu, *tu, *Ru, *Su;
   };
   std::vector<Factors> fs;
-  double* recT = nullptr;                // the step's T after its right application, formed again
+  // the reverse pass walks T and U back step by step with the kept
+  // reflectors: recP holds T entering the step, recT T between its two
+  // applications, recU U entering it
+  double *recT = nullptr, *recP = nullptr, *recU = nullptr;
   // scratch
   double *work = nullptr, *gram = nullptr, *pq = nullptr, *c1 = nullptr, *c2 = nullptr, *c3 = nullptr,
          *c4 = nullptr, *big1 = nullptr, *big2 = nullptr, *Tbar = nullptr, *Ubar = nullptr, *vbar = nullptr,
@@ -532,11 +534,8 @@ cudaError_t forward(State& S, cudaStream_t s, const double* A, int64_t lda, doub
   double* T = S.big1;                    // the running T (m x n)
   AD_CK(copy_matrix(s, m, n, A, lda, T, m));
   AD_CK(set_identity(s, m, S.U, m));
-  for (int i = 1; i <= S.s; ++i) {
-    AD_CK(copy_matrix(s, m, n, T, m, S.st[i - 1].Tprev, m));
-    AD_CK(copy_matrix(s, m, m, S.U, m, S.st[i - 1].Uprev, m));
-    AD_CK(step_forward(S, s, i, T, S.U));
-  }
+  for (int i = 1; i <= S.s; ++i) AD_CK(step_forward(S, s, i, T, S.U));
+  AD_CK(copy_matrix(s, m, n, T, m, S.Tfin, m));
   // W = U_k^T A, F = U_k W
   AD_CK(g64(S, s, true, false, S.k, n, m, 1.0, S.U, m, S.A, m, 0.0, S.W, S.k));
   return g64(S, s, false, false, m, n, S.k, 1.0, S.U, m, S.W, S.k, 0.0, F, ldf);
@@ -555,17 +554,23 @@ cudaError_t reverse(State& S, cudaStream_t s, const double* Fb, int64_t ldfb, do
   AD_CK(g64(S, s, true, false, n, k, m, 1.0, Fb, ldfb, S.U, m, 0.0, S.big2, n));
   AD_CK(g64(S, s, false, false, m, k, n, 1.0, S.A, m, S.big2, n, 1.0, Ub, m));
   AD_CK(cudaMemsetAsync(Tb, 0, sizeof(double) * m * n, s));
+  AD_CK(copy_matrix(s, m, n, S.Tfin, m, S.recP, m));
+  AD_CK(copy_matrix(s, m, m, S.U, m, S.recU, m));
   for (int i = S.s; i >= 1; --i) {
-    // the step's factors from the forward; T after its right application
-    // formed again from the checkpoint (bit for bit: the same products)
+    // T and U entering the step, and T between its two applications, walked
+    // back from those after it with the step's own reflectors (orthogonal:
+    // the inverse of C Q is C Q^T, of Q^T C is Q C)
     const auto& P = S.fs[i - 1];
     {
-      const int64_t kc0 = n - static_cast<int64_t>(b) * (i - 1);
-      AD_CK(copy_matrix(s, m, n, S.st[i - 1].Tprev, m, S.recT, m));
-      AD_CK(wy_apply(S, s, true, false, m, kc0, b, P.Vv, P.Sv, S.recT + static_cast<int64_t>(b) * (i - 1) * m, m));
+      const int64_t q0 = static_cast<int64_t>(b) * (i - 1), kr0 = m - q0, kc0 = n - q0;
+      AD_CK(copy_matrix(s, m, n, S.recP, m, S.recT, m));
+      AD_CK(wy_apply(S, s, false, true, kc0, kr0, b, P.Vu, P.Su, S.recT + q0 + q0 * m, m));   // Qu T(r0:, r0:)
+      AD_CK(copy_matrix(s, m, n, S.recT, m, S.recP, m));
+      AD_CK(wy_apply(S, s, true, true, m, kc0, b, P.Vv, P.Sv, S.recP + q0 * m, m));           // T(:, r0:) Qv^T
+      AD_CK(wy_apply(S, s, true, true, m, kr0, b, P.Vu, P.Su, S.recU + q0 * m, m));           // U(:, r0:) Qu^T
     }
-    const double* Tprev = S.st[i - 1].Tprev;
-    const double* Uprev = S.st[i - 1].Uprev;
+    const double* Tprev = S.recP;
+    const double* Uprev = S.recU;
     const int64_t r0 = static_cast<int64_t>(b) * (i - 1), kr = m - r0, kc = n - r0;
     double* T2b = S.big2;                                 // Tbar(r0:, r0:) after the step (kr x kc, ld kr)
     AD_CK(copy_matrix(s, kr, kc, Tb + r0 + r0 * m, m, T2b, kr));
@@ -673,11 +678,7 @@ int randutv_rank_k(int64_t m, int64_t n, const double* A, int64_t lda, int b, in
   items.push_back({&S->A, m * n});
   items.push_back({&S->U, m * m});
   items.push_back({&S->W, k * n});
-  S->st.resize(S->s);
-  for (int i = 0; i < S->s; ++i) {
-    items.push_back({&S->st[i].Tprev, m * n});
-    items.push_back({&S->st[i].Uprev, m * m});
-  }
+  items.push_back({&S->Tfin, m * n});
   // every step's factors, each sized for the first (largest) step
   S->fs.resize(S->s);
   for (int i = 0; i < S->s; ++i) {
@@ -695,6 +696,8 @@ int randutv_rank_k(int64_t m, int64_t n, const double* A, int64_t lda, int b, in
     items.push_back({&P.Su, b * b});
   }
   items.push_back({&S->recT, m * n});
+  items.push_back({&S->recP, m * n});
+  items.push_back({&S->recU, m * m});
   int64_t gtot = 0;
   for (int i = 0; i < S->s; ++i) gtot += (m - static_cast<int64_t>(b) * i) * b;
   if (o.g_inject) items.push_back({&S->gin, gtot});
