@@ -80,7 +80,7 @@ def hbm_view(n, b, q, elem_bytes, seconds):
 # times its algorithmic bytes per launch.
 GEMM_TRAFFIC = {"4b6a7761b9ca2e2b": 0.926}
 # ncu dram bytes (read + write) / algorithmic bytes of gemm_ozx_kernel, by kernel_hash of csrc/gemm_oz.cu
-OZ_TRAFFIC = {"a72219d471f54b9a": 1.027}   # rank-128 update 1.003, long-K product 1.050 (profiles/)
+OZ_TRAFFIC = {"0ccfe3e7f56bf92f": 1.025}   # rank-128 update 1.003, long-K product 1.047 (profiles/)
 # DRAM traffic of the batched kernel per matrix from one ncu capture of a
 # 512-matrix batch of the same size law (dram read + write / 512), valid for
 # the kernel source with this kernel_hash of csrc/batched.cu (none: the

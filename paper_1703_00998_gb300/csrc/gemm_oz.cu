@@ -121,7 +121,8 @@ __device__ __forceinline__ int oz_swz(int kk) { return (kk & ~3) | (((kk & 3) + 
 // Slices of an R x K operand X (element (r, k) at X[k + r ldx] when KC, the K
 // index contiguous, else at X[r + k ldx]), per K chunk: S[(j Rpad + r) Kpad +
 // k] (BF16, K contiguous) and e[c Rpad + r].  Rows r >= R and columns k >= K
-// are zero.  One CTA of 256 threads per 32 rows x one chunk; a warp owns a
+// are zero.  One CTA of 256 threads per one chunk x 32 rows (grid x = chunk,
+// y = row block); a warp owns a
 // row at a time and each lane 4 consecutive k of it, so the slices are
 // written 8 bytes per lane.  With K strided (column-major X) the chunk is
 // first staged through shared memory so that the reads are coalesced.
@@ -141,8 +142,8 @@ oz_slice_kernel(int64_t R, int64_t K, const T* __restrict__ X, int64_t ldx, int6
   constexpr long long EMASK = (1ll << F::EB) - 1;
   __shared__ long long tile[KC ? 1 : 32][KC ? 1 : OZ_KC + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 32;
-  const int64_t k0 = static_cast<int64_t>(blockIdx.y) * OZ_KC;
+  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * 32;
+  const int64_t k0 = static_cast<int64_t>(blockIdx.x) * OZ_KC;
   if constexpr (!KC) {
     for (int idx = tid; idx < 32 * OZ_KC; idx += 256) {
       const int i = idx % 32, kk = idx / 32;
@@ -175,7 +176,7 @@ oz_slice_kernel(int64_t R, int64_t K, const T* __restrict__ X, int64_t ldx, int6
     // a zero (or subnormal-only) chunk reports the scale kOzZeroScale, so that it never sets a
     // row's largest scale; its slices are zero
     const bool zero = (be == 0);
-    if (lane == 0) E[static_cast<int64_t>(blockIdx.y) * Rpad + r] = zero ? kOzZeroScale : be - F::EBIAS;
+    if (lane == 0) E[static_cast<int64_t>(blockIdx.x) * Rpad + r] = zero ? kOzZeroScale : be - F::EBIAS;
     const int e = zero ? 0 : be - F::EBIAS;
     int nsq = 0;
     unsigned long long mag[4];
@@ -208,7 +209,7 @@ oz_slice_kernel(int64_t R, int64_t K, const T* __restrict__ X, int64_t ldx, int6
     }
     if (NS) {
       nsq = __reduce_add_sync(0xffffffffu, nsq);
-      if (lane == 0) NS[static_cast<int64_t>(blockIdx.y) * Rpad + r] = zero ? 0 : nsq;
+      if (lane == 0) NS[static_cast<int64_t>(blockIdx.x) * Rpad + r] = zero ? 0 : nsq;
     }
   }
 }
@@ -217,7 +218,9 @@ oz_slice_kernel(int64_t R, int64_t K, const T* __restrict__ X, int64_t ldx, int6
 template <int S, typename T>
 void slice_launch(cudaStream_t s, int64_t R, int64_t K, const T* X, int64_t ldx, bool kcontig, int64_t Rpad,
                   int64_t Kpad, int nch, __nv_bfloat16* Sl, int* E, int* NS) {
-  const dim3 g(static_cast<unsigned>(Rpad / 32), static_cast<unsigned>(nch));
+  // chunks vary fastest: CTAs in flight together slice consecutive chunks of
+  // the same rows, so each slice row is written as one contiguous run
+  const dim3 g(static_cast<unsigned>(nch), static_cast<unsigned>(Rpad / 32));
   if (kcontig) oz_slice_kernel<S, T, true><<<g, 256, 0, s>>>(R, K, X, ldx, Rpad, Kpad, Sl, E, NS);
   else oz_slice_kernel<S, T, false><<<g, 256, 0, s>>>(R, K, X, ldx, Rpad, Kpad, Sl, E, NS);
 }
