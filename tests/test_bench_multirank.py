@@ -72,3 +72,18 @@ def test_algorithmic_bytes_floor():
     assert bench.algorithmic_elems(n, b, q) == ref
     v = bench.hbm_view(8000, 128, 1, 8, 0.694)
     assert 150 < v["achieved_gbs"] < 250 and 0 < v["frac"] < 0.05
+
+
+def test_kernel_hash_ignores_comments_only(tmp_path):
+    """A traffic ratio stays keyed to a source while only its comments change,
+    and is dropped when its code changes."""
+    sys.path.insert(0, ROOT)
+    import bench
+    a = tmp_path / "a.cu"
+    b = tmp_path / "b.cu"
+    c = tmp_path / "c.cu"
+    a.write_text("// header\n__global__ void k(int* x) {\n  x[0] = 1;  // store\n}\n")
+    b.write_text("/* another\n   header */\n__global__   void k(int* x)\n{ x[0] = 1; }\n")
+    c.write_text("// header\n__global__ void k(int* x) {\n  x[0] = 2;  // store\n}\n")
+    assert bench.kernel_hash(str(a)) == bench.kernel_hash(str(b))
+    assert bench.kernel_hash(str(a)) != bench.kernel_hash(str(c))
