@@ -160,12 +160,14 @@ def test_n4000_b128_against_oracle(R, kind, q):
     assert r["ok"]
 
 
-def test_n8000_b128_q1_full_size(R):
-    """The benchmark workload: properties at full size and the first block
-    against the oracle's first step (the diagonal block of step 1 is final)."""
+@pytest.mark.parametrize("kind", ["exp200", "gauss"])
+def test_n8000_b128_q1_full_size(R, kind):
+    """The benchmark workload (and an iid Gaussian matrix of the same size):
+    properties at full size and the first block against the oracle's first
+    step (the diagonal block of step 1 is final)."""
     import torch
     n, b = 8000, 128
-    A = synth.make_matrix("exp200", n, n, 1703002, device="cuda")
+    A = synth.make_matrix(kind, n, n, 1703002 + ["exp200", "inv", "gauss"].index(kind), device="cuda")
     Ah = host(A)
     out = R.factor(A, b=b, q=1, seed=SEED)
     U, T, V = out.U, out.T, out.V
