@@ -115,7 +115,11 @@ def parse():
     ap.add_argument("--overlap", type=int, default=1, choices=[0, 1],
                     help="1: U/V accumulation on a second, low-priority stream")
     ap.add_argument("--tensor-cores", type=int, default=1, choices=[0, 1],
-                    help="mixed form: 0 CUDA cores only, 1 sketch products on the tcgen05 tensor cores")
+                    help="mixed form with --sketch-prec 1 or 2: 0 sketch products on the CUDA cores, 1 on the "
+                         "tcgen05 tensor cores")
+    ap.add_argument("--sketch-prec", type=int, default=0, choices=[0, 1, 2],
+                    help="mixed form's sketch: 0 FP64 results from BF16 slice products (default), 1 3xTF32, "
+                         "2 one TF32 product")
     ap.add_argument("--forms", default="fp64,mixed", help="fp64, mixed or both (the FP64 form carries the line)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form leg")
     ap.add_argument("--batched-only", action="store_true",
@@ -550,6 +554,7 @@ def run_mixed(args, lib, native, A, Tst64, n, b, q, stream, dist):
     Vst = torch.empty((n, n), dtype=torch.float32, device="cuda")
     opts = native.default_opts()
     opts.tensor_cores = args.tensor_cores
+    opts.sketch_prec = args.sketch_prec
     opts.overlap = args.overlap
     kr = ctypes.c_int64(0)
 
@@ -578,6 +583,7 @@ def run_mixed(args, lib, native, A, Tst64, n, b, q, stream, dist):
     world = dist.get_world_size() if dist else 1
     out = {"value": whole_job_rate(world, total_flops(n, q), ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
            "dtype": "f32 storage and products, f64 panel QR and small SVD", "tensor_cores": args.tensor_cores,
+           "sketch_prec": args.sketch_prec,
            "breakdown": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
                          for k, v in prof.items()}}
     g = prof["gemm32"]
